@@ -1,0 +1,324 @@
+/*
+ * FP64 CPU oracle: plain, slow, step-by-step restatement of the paper's
+ * method.  TEST INFRASTRUCTURE ONLY (see oracle.h): nothing on the product
+ * path links or calls this file.
+ *
+ * Paper passages followed:
+ *   Eq. (1)            the NLSE, G(z) = -gamma + (e^{z_a gamma}-1) sum delta(z - z_k)
+ *   text after Eq. (1) Fourier transform with exp(+i omega t); interaction
+ *                      picture A_hat = psi_hat exp(i beta + int G); beta(omega, z)
+ *   Eq. (2)            integral equation for psi_hat
+ *   MPA steps 1-7      Picard iteration over one interval [z0, z0+L]
+ *   Eq. (6)            trapezoidal discretisation of the iteration
+ *   Eq. (4)            composite (Strang) split-step
+ */
+#include "oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#define ORACLE_MAX_THREADS() omp_get_max_threads()
+#else
+#define ORACLE_MAX_THREADS() 1
+#endif
+
+typedef double complex cplx;
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* ------------------------------------------------------------------ FFT */
+
+static int is_pow2(long n) { return n >= 2 && (n & (n - 1)) == 0; }
+
+/* Iterative radix-2 Cooley-Tukey, decimation in time: bit-reverse the
+ * input, then log2(N) butterfly stages.  Twiddles exp(sign 2 pi i m/N) are
+ * evaluated directly with libm for every m (no recurrences). */
+static int fft_c(cplx* x, long N, int sign) {
+    if (!is_pow2(N)) return 1;
+    for (long i = 1, j = 0; i < N; i++) {
+        long bit = N >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            cplx t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+    long half_n = N / 2;
+    cplx* tw = (cplx*)malloc(sizeof(cplx) * (size_t)half_n);
+    if (!tw) return 3;
+    for (long m = 0; m < half_n; m++) {
+        double a = TWO_PI * (double)m / (double)N;
+        tw[m] = cos(a) + I * (sign > 0 ? sin(a) : -sin(a));
+    }
+    for (long len = 2; len <= N; len <<= 1) {
+        long half = len / 2, step = N / len;
+        for (long i = 0; i < N; i += len) {
+            for (long m = 0; m < half; m++) {
+                cplx w = tw[m * step];
+                cplx u = x[i + m];
+                cplx v = x[i + m + half] * w;
+                x[i + m] = u + v;
+                x[i + m + half] = u - v;
+            }
+        }
+    }
+    free(tw);
+    if (sign < 0) {
+        double s = 1.0 / (double)N;
+        for (long i = 0; i < N; i++) x[i] *= s;
+    }
+    return 0;
+}
+
+int oracle_fft(double* x, long N, int sign) { return fft_c((cplx*)x, N, sign); }
+
+/* ------------------------------------------------------------ fiber map */
+
+typedef struct {
+    const double* rows; /* n_seg x {length, beta2, beta3, sigma} */
+    int n_seg;
+    double gamma, z_a;
+    int n_periods;
+    double period;
+} fmap;
+
+static fmap make_map(const double* rows, int n_seg, double gamma, double z_a, int n_periods) {
+    fmap m = {rows, n_seg, gamma, z_a, n_periods, 0.0};
+    for (int s = 0; s < n_seg; s++) m.period += rows[4 * s];
+    return m;
+}
+
+/* int_za^zb of coefficient column col (1 = beta2, 2 = beta3, 3 = sigma):
+ * sum over every segment copy of coefficient x overlap length. */
+static double integrate(const fmap* m, double za, double zb, int col) {
+    if (zb <= za) return 0.0;
+    double acc = 0.0;
+    long p0 = (long)floor(za / m->period) - 1, p1 = (long)floor(zb / m->period) + 1;
+    for (long p = p0; p <= p1; p++) {
+        double off = (double)p * m->period;
+        for (int s = 0; s < m->n_seg; s++) {
+            double a = off, b = off + m->rows[4 * s];
+            off = b;
+            double lo = a > za ? a : za, hi = b < zb ? b : zb;
+            if (hi > lo) acc += m->rows[4 * s + col] * (hi - lo);
+        }
+    }
+    return acc;
+}
+
+/* Coefficient value just left (side < 0) or right (side > 0) of z. */
+static double coef_side(const fmap* m, double z, int col, int side) {
+    double eps = 1e-9 * m->period;
+    double zz = z + (side > 0 ? eps : -eps);
+    double u = zz - floor(zz / m->period) * m->period;
+    double off = 0.0;
+    for (int s = 0; s < m->n_seg; s++) {
+        double b = off + m->rows[4 * s];
+        if (u < b || s == m->n_seg - 1) return m->rows[4 * s + col];
+        off = b;
+    }
+    return m->rows[4 * (m->n_seg - 1) + col];
+}
+
+/* Number of amplifiers z_k = k z_a (k >= 1) with za < z_k <= zb. */
+static long n_amps(const fmap* m, double za, double zb) {
+    if (m->z_a <= 0.0) return 0;
+    double tol = 1e-9 * m->z_a;
+    long ka = (long)floor((za + tol) / m->z_a), kb = (long)floor((zb + tol) / m->z_a);
+    if (ka < 0) ka = 0;
+    return kb > ka ? kb - ka : 0;
+}
+
+static double omega_of(long k, long N, double T) {
+    long kp = k < N / 2 ? k : k - N;
+    return TWO_PI * (double)kp / T;
+}
+
+/* beta(omega, za, zb) of the text after Eq. (2), evaluated in FP64. */
+static double beta_of(double w, double I2, double I3) { return 0.5 * w * w * I2 + w * w * w * I3 / 6.0; }
+
+/* Exact linear flow over [za, zb] on a spectrum (the sigma = 0 solution of
+ * Eq. (2), continued across amplifiers). */
+static void linear_flow(const fmap* m, cplx* X, long N, double T, double za, double zb) {
+    double I2 = integrate(m, za, zb, 1), I3 = integrate(m, za, zb, 2);
+    double g = exp(-m->gamma * (zb - za) + (double)n_amps(m, za, zb) * m->z_a * m->gamma);
+    for (long k = 0; k < N; k++) {
+        double b = beta_of(omega_of(k, N, T), I2, I3);
+        X[k] *= g * (cos(b) + I * sin(b));
+    }
+}
+
+static int check_span(const fmap* m, double z_from, double z_to) {
+    if (!(z_to >= z_from) || z_from < -1e-12) return 2;
+    if (z_to > m->period * m->n_periods * (1.0 + 1e-12) + 1e-9) return 2;
+    return 0;
+}
+
+/* ----------------------------------------------------------------- MPA */
+
+/* One interval of the MPA (steps 1-6 of the algorithm, Eq. (6)): returns
+ * psi^{(n_tot)} at node M.  psi0 is the spectrum A_hat(z0) in natural order. */
+static int mpa_interval(const fmap* m, long N, double T, double z0, double L, int M, int n_tot,
+                        const cplx* psi0, cplx* psiM, int n_threads) {
+    double dz = L / (double)M;
+    size_t nn = (size_t)(M + 1) * (size_t)N;
+    cplx* psi = (cplx*)malloc(sizeof(cplx) * nn);
+    cplx* V = (cplx*)malloc(sizeof(cplx) * nn);
+    double* I2 = (double*)malloc(sizeof(double) * (size_t)(M + 1));
+    double* I3 = (double*)malloc(sizeof(double) * (size_t)(M + 1));
+    double* sig = (double*)malloc(sizeof(double) * (size_t)(M + 1));
+    double* loss = (double*)malloc(sizeof(double) * (size_t)(M + 1));
+    if (!psi || !V || !I2 || !I3 || !sig || !loss) {
+        free(psi); free(V); free(I2); free(I3); free(sig); free(loss);
+        return 3;
+    }
+    /* per-node quantities: z_j = z0 + j dz, beta relative to z0, the loss
+     * factor exp(int_{z0}^{z_j} G) = exp(-gamma (z_j - z0)) and sigma(z_j)
+     * (average of the one-sided values where a segment boundary falls on an
+     * interior node, the inner one-sided value at the interval ends). */
+    for (int j = 0; j <= M; j++) {
+        double zj = z0 + dz * (double)j;
+        I2[j] = integrate(m, z0, zj, 1);
+        I3[j] = integrate(m, z0, zj, 2);
+        loss[j] = exp(-m->gamma * (zj - z0));
+        if (j == 0) sig[j] = coef_side(m, zj, 3, +1);
+        else if (j == M) sig[j] = coef_side(m, zj, 3, -1);
+        else sig[j] = 0.5 * (coef_side(m, zj, 3, -1) + coef_side(m, zj, 3, +1));
+    }
+    /* step 1: copy psi(z0) to every node */
+    for (int j = 0; j <= M; j++) memcpy(psi + (size_t)j * N, psi0, sizeof(cplx) * (size_t)N);
+
+    int err = 0;
+    for (int it = 0; it < n_tot; it++) {
+        /* steps 2-4 at every node, independently (one node per task) */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : ORACLE_MAX_THREADS())
+        for (int j = 0; j <= M; j++) {
+            cplx* a = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+            if (!a) { err = 3; continue; }
+            const cplx* pj = psi + (size_t)j * N;
+            for (long k = 0; k < N; k++) {
+                double b = beta_of(omega_of(k, N, T), I2[j], I3[j]);
+                a[k] = pj[k] * (cos(b) + I * sin(b)) * loss[j];            /* step 2 */
+            }
+            fft_c(a, N, -1);                                                 /* step 3 */
+            for (long n = 0; n < N; n++) {
+                double p = creal(a[n]) * creal(a[n]) + cimag(a[n]) * cimag(a[n]);
+                a[n] *= p;                                                   /* |A|^2 A */
+            }
+            fft_c(a, N, +1);                                                 /* step 4 */
+            cplx* vj = V + (size_t)j * N;
+            for (long k = 0; k < N; k++) {
+                double b = beta_of(omega_of(k, N, T), I2[j], I3[j]);
+                /* V_j = sigma(z_j) F[|A_j|^2 A_j] dz exp(-i beta - int G), Eq. (6) */
+                vj[k] = sig[j] * dz * a[k] * (cos(b) - I * sin(b)) / loss[j];
+            }
+            free(a);
+        }
+        if (err) break;
+        /* step 5: trapezoidal rule with every partial integral saved,
+         * psi_l = psi_0 + i (V_0/2 + sum_{j=1}^{l-1} V_j + V_l/2), l = 1..M */
+        for (long k = 0; k < N; k++) {
+            cplx run = 0.5 * V[k];
+            for (int l = 1; l <= M; l++) {
+                cplx vl = V[(size_t)l * N + k];
+                psi[(size_t)l * N + k] = psi0[k] + I * (run + 0.5 * vl);
+                run += vl;
+            }
+        }
+        /* step 6: the next iteration starts again at step 2 */
+    }
+    if (!err) memcpy(psiM, psi + (size_t)M * N, sizeof(cplx) * (size_t)N);
+    free(psi); free(V); free(I2); free(I3); free(sig); free(loss);
+    return err;
+}
+
+int oracle_mpa_interval(const double* seg_rows, int n_seg, double gamma, double z_a, int n_periods,
+                        long N, double T, double z0, double L, int M, int n_tot,
+                        const double* psi0, double* psiM, int n_threads) {
+    if (!is_pow2(N)) return 1;
+    if (M < 1 || n_tot < 1 || !(L > 0.0) || !(T > 0.0) || n_seg < 1) return 4;
+    fmap m = make_map(seg_rows, n_seg, gamma, z_a, n_periods);
+    return mpa_interval(&m, N, T, z0, L, M, n_tot, (const cplx*)psi0, (cplx*)psiM, n_threads);
+}
+
+int oracle_mpa(const double* seg_rows, int n_seg, double gamma, double z_a, int n_periods,
+               long N, double T, double z_from, double z_to, double L, int M, int n_tot,
+               double* field, int n_threads, int* threads_used) {
+    if (!is_pow2(N)) return 1;
+    if (M < 1 || n_tot < 1 || !(L > 0.0) || !(T > 0.0) || n_seg < 1) return 4;
+    fmap m = make_map(seg_rows, n_seg, gamma, z_a, n_periods);
+    if (check_span(&m, z_from, z_to)) return 2;
+    double cnt = (z_to - z_from) / L;
+    long n_int = lround(cnt);
+    if (fabs(cnt - (double)n_int) > 1e-9 * (cnt > 1.0 ? cnt : 1.0)) return 2;
+    /* amplifiers may only sit at interval ends */
+    for (long q = 0; q < n_int; q++) {
+        double a = z_from + L * (double)q, b = z_from + L * (double)(q + 1);
+        if (n_amps(&m, a, b - 1e-6 * L) != 0) return 2;
+    }
+    if (threads_used) {
+        *threads_used = n_threads > 0 ? n_threads : ORACLE_MAX_THREADS();
+    }
+    cplx* X = (cplx*)field;
+    cplx* psiM = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    if (!psiM) return 3;
+    fft_c(X, N, +1); /* A_hat(z_from) = psi_hat(z0) of the first interval */
+    int err = 0;
+    for (long q = 0; q < n_int && !err; q++) {
+        double z0 = z_from + L * (double)q;
+        err = mpa_interval(&m, N, T, z0, L, M, n_tot, X, psiM, n_threads);
+        if (err) break;
+        /* step 7: A_hat(z0 + L) = psi_M exp(i beta(omega, z0 + L) + int G),
+         * then the lumped gain when z0 + L is an amplifier location */
+        double I2 = integrate(&m, z0, z0 + L, 1), I3 = integrate(&m, z0, z0 + L, 2);
+        double g = exp(-m.gamma * L + (double)n_amps(&m, z0, z0 + L) * m.z_a * m.gamma);
+        for (long k = 0; k < N; k++) {
+            double b = beta_of(omega_of(k, N, T), I2, I3);
+            X[k] = psiM[k] * (cos(b) + I * sin(b)) * g;
+        }
+    }
+    free(psiM);
+    fft_c(X, N, -1);
+    return err;
+}
+
+/* ------------------------------------------------------------------ SS */
+
+int oracle_ss(const double* seg_rows, int n_seg, double gamma, double z_a, int n_periods,
+              long N, double T, double z_from, double z_to, double dz, double* field) {
+    if (!is_pow2(N)) return 1;
+    if (!(dz > 0.0) || !(T > 0.0) || n_seg < 1) return 4;
+    fmap m = make_map(seg_rows, n_seg, gamma, z_a, n_periods);
+    if (check_span(&m, z_from, z_to)) return 2;
+    double cnt = (z_to - z_from) / dz;
+    long K = lround(cnt);
+    if (K < 1 || fabs(cnt - (double)K) > 1e-9 * (cnt > 1.0 ? cnt : 1.0)) return 2;
+    cplx* X = (cplx*)field;
+    fft_c(X, N, +1);
+    /* Eq. (4): exp(iL dz/2) Q^K exp(-iL dz/2), Q = exp(iN dz) exp(iL dz):
+     * half linear step, then K nonlinear kicks at the step midpoints
+     * z_k + dz/2 separated by full linear steps, and a final half step. */
+    double za = z_from, zb = z_from + 0.5 * dz;
+    linear_flow(&m, X, N, T, za, zb);
+    for (long k = 0; k < K; k++) {
+        double zk = z_from + dz * (double)k;
+        double s = integrate(&m, zk, zk + dz, 3); /* int sigma over the step */
+        fft_c(X, N, -1);
+        for (long n = 0; n < N; n++) {
+            double p = creal(X[n]) * creal(X[n]) + cimag(X[n]) * cimag(X[n]);
+            double ph = s * p;
+            X[n] *= cos(ph) + I * sin(ph); /* exp(i sigma |A|^2 dz) A */
+        }
+        fft_c(X, N, +1);
+        za = zb;
+        zb = (k == K - 1) ? z_to : zb + dz;
+        linear_flow(&m, X, N, T, za, zb);
+    }
+    fft_c(X, N, -1);
+    return 0;
+}
