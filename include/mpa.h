@@ -1,0 +1,155 @@
+/*
+ * mpa.h -- C ABI of the GB300 (sm_103a) implementation of the massively
+ * parallel algorithm (MPA) for the dispersion-managed WDM nonlinear
+ * Schroedinger equation (Korotkevich & Lushnikov, arXiv:1101.0086), with the
+ * symmetric split-step (SS) method of Eq. (4) on the same GPU.
+ *
+ * Physics (Eq. (1)):
+ *   i A_z - beta2(z)/2 A_tt - i beta3(z)/6 A_ttt + sigma(z)|A|^2 A = i G(z) A,
+ *   G(z) = -gamma + (exp(z_a gamma) - 1) sum_k delta(z - k z_a).
+ * Units: t in ps, z in km, beta2 in ps^2/km, beta3 in ps^3/km,
+ * sigma in 1/(W km), |A|^2 in W, gamma (amplitude loss) in 1/km.
+ *
+ * Fourier convention (text after Eq. (1)): A_hat(w) = int A(t) exp(+i w t) dt,
+ * discretised as F[x]_k = sum_n x_n exp(+2 pi i k n/N) with
+ * w_k = 2 pi k'/T, k' = k (k < N/2) or k - N (k >= N/2).
+ *
+ * Field layout: A(t_n), t_n = n T/N, n = 0..N-1, interleaved (re, im):
+ * complex64 (float2) for MPA_FP32, complex128 (double2) for MPA_FP64.
+ * All field and workspace pointers are DEVICE pointers owned by the caller;
+ * the library allocates no device memory: scratch and tables live in the
+ * caller's workspace.
+ * Streams are cudaStream_t values passed as void* (NULL = legacy default
+ * stream).  Calls are stream-ordered and asynchronous unless stated.
+ *
+ * Errors: every entry point returns an int status (MPA_OK = 0).  Argument
+ * and grid checks are synchronous; a CUDA launch or copy failure returns
+ * MPA_ERR_CUDA.  Nothing aborts or throws across the ABI.
+ */
+#ifndef MPA_H
+#define MPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MPA_API __attribute__((visibility("default")))
+#else
+#define MPA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MPA_OK = 0,
+    MPA_ERR_INVALID_ARG = 1,   /* NULL pointer, non-positive size, bad enum */
+    MPA_ERR_UNSUPPORTED_N = 2, /* N not a power of two in [2^8, 2^25] (2^24 for FP64) */
+    MPA_ERR_WORKSPACE = 3,     /* workspace missing or smaller than required */
+    MPA_ERR_CUDA = 4,          /* a CUDA call failed (see mpa_last_cuda_error) */
+    MPA_ERR_GRID = 5,          /* z-grid inconsistent with the fiber map (see each call) */
+    MPA_ERR_NONFINITE = 6      /* a NaN/Inf was produced (mpa_plan_status) */
+};
+
+enum { MPA_FP32 = 0, MPA_FP64 = 1 };
+
+typedef void* mpa_stream; /* cudaStream_t */
+
+/* One piece of the dispersion-management period with constant coefficients. */
+typedef struct {
+    double length_km;
+    double beta2_ps2_per_km;
+    double beta3_ps3_per_km;
+    double sigma_per_W_km;
+} mpa_segment;
+
+/* Periodic fiber map (Eq. (1): beta2, beta3 periodic in z; sigma per segment).
+ * segments[0..n_segments) form one period, repeated n_periods times.
+ * Lumped amplifiers at z_k = k z_a_km, k >= 1, multiply the field by
+ * exp(z_a gamma) when the propagation crosses z_k (z_k in (z_from, z_to]).
+ * z_a_km <= 0 disables amplifiers.  The map is copied by the calls that take
+ * it; the caller keeps ownership of `segments`. */
+typedef struct {
+    const mpa_segment* segments;
+    int32_t n_segments;
+    double gamma_per_km;
+    double z_a_km;
+    int32_t n_periods;
+} mpa_fiber_map;
+
+/* MPA discretisation (MPA steps 1-7 and Eq. (6)): intervals of length L_km,
+ * each with M+1 equally spaced nodes and n_iter Picard iterations. */
+typedef struct {
+    int64_t N;         /* Fourier modes, power of two */
+    double T_ps;       /* time window */
+    double L_km;       /* interval length; must divide the DM period or be a multiple of it */
+    int32_t M;         /* intervals of the z-quadrature per interval (M+1 nodes) */
+    int32_t n_iter;    /* n_tot, Picard iterations per interval (>= 1) */
+    int32_t precision; /* MPA_FP32 (FFT/nonlinearity in FP32, phase exact, Kahan sums, FP64 state) or MPA_FP64 */
+} mpa_plan_params;
+
+typedef struct mpa_plan mpa_plan;
+
+/* Create a plan (host only, no CUDA call).  Validates N, T, L, M, n_iter
+ * and the map; precomputes on the host, for every distinct interval start
+ * within the DM period, the per-node constants of Eq. (6): the exact
+ * fixed-point phase coefficients of beta(w, z_j), the loss factor
+ * exp(int G) and the trapezoid weight sigma(z_j) dz.  *out receives the plan. */
+MPA_API int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* params, mpa_plan** out);
+
+/* Bytes of device workspace the plan needs (caller allocates, >= 256-B aligned). */
+MPA_API int mpa_plan_workspace_size(const mpa_plan* plan, size_t* bytes);
+
+/* Attach caller-owned device workspace and upload the node tables
+ * (synchronous).  The workspace must stay valid while the plan is used. */
+MPA_API int mpa_plan_set_workspace(mpa_plan* plan, void* workspace, size_t bytes);
+
+/* MPA propagation (MPA steps 1-7 per interval, interval marching of the text
+ * before step 1): the time-domain field is propagated in place from
+ * z_from_km to z_to_km.  z_from must be a multiple of L; (z_to - z_from)/L
+ * whole; no amplifier strictly inside an interval (else MPA_ERR_GRID).
+ * The lumped gain of an amplifier at an interval end is applied after
+ * step 7.  Asynchronous on `stream`. */
+MPA_API int mpa_propagate(mpa_plan* plan, void* field, double z_from_km, double z_to_km, mpa_stream stream);
+
+/* One interval of the MPA without step 7: from the spectrum psi0 (N
+ * complex128, natural frequency order, = A_hat(z0)) compute
+ * psi^{(n_iter)} at node M (complex128) for the interval starting at z0_km
+ * (a multiple of L).  Exposed for step-level parity checks. */
+MPA_API int mpa_interval(mpa_plan* plan, const void* psi0, void* psiM, double z0_km, mpa_stream stream);
+
+/* Returns MPA_ERR_NONFINITE if any propagate since the last call produced a
+ * NaN/Inf (synchronises the stream), else MPA_OK; clears the flag. */
+MPA_API int mpa_plan_status(mpa_plan* plan, mpa_stream stream);
+
+MPA_API void mpa_plan_destroy(mpa_plan* plan);
+
+/* Symmetric split-step of Eq. (4) on the GPU: half linear step, then
+ * (nonlinear phase rotation exp(i sigma |A|^2 dz), linear step) repeated,
+ * the last linear step halved.  Linear steps are exact Fourier multipliers
+ * exp(i beta(w; za, zb) + int G) (amplifier gains included); the nonlinear
+ * step uses int sigma over the step.  (z_to - z_from)/dz must be whole.
+ * The field (precision's complex type) is updated in place. */
+MPA_API int ss_workspace_size(int64_t N, int32_t precision, size_t* bytes);
+MPA_API int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision,
+                 void* field, double z_from_km, double z_to_km, void* workspace, size_t ws_bytes,
+                 mpa_stream stream);
+
+/* Discrete Fourier transform of N values in place, in the convention above:
+ * sign = +1: F (no scaling), sign = -1: F^-1 (scaled by 1/N).  The MPA uses
+ * these transforms in steps 3 and 4.  Workspace: ss_workspace_size bytes. */
+MPA_API int mpa_fft(int64_t N, int32_t precision, int32_t sign, void* data, void* workspace, size_t ws_bytes,
+            mpa_stream stream);
+
+/* Human-readable status; the last CUDA error string for MPA_ERR_CUDA. */
+MPA_API const char* mpa_status_string(int status);
+MPA_API const char* mpa_last_cuda_error(void);
+
+/* Number of this library's kernels launched since load (all threads). */
+MPA_API int64_t mpa_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPA_H */

@@ -1,0 +1,280 @@
+// Device building blocks of the MPA node transform and the split-step step:
+// complex arithmetic, fixed-size DFTs in registers, the exact fixed-point
+// dispersion phase, and a batched self-sorting (Stockham) FFT over shared
+// memory.
+//
+// Fourier convention (text after Eq. (1)): forward F uses exp(+2 pi i kn/N)
+// (sign S = +1), the inverse exp(-2 pi i kn/N) (S = -1, 1/N applied by the
+// caller).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpa {
+
+template <typename T> struct cx_of;
+template <> struct cx_of<float> { typedef float2 type; };
+template <> struct cx_of<double> { typedef double2 type; };
+template <typename T> using cx = typename cx_of<T>::type;
+
+__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+    return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class C> __device__ __forceinline__ C cconj(C a) { return mkc(a.x, -a.y); }
+template <class C, class T> __device__ __forceinline__ C cscale(C a, T s) { return mkc(a.x * s, a.y * s); }
+// a * (S i)
+template <int S, class C> __device__ __forceinline__ C mul_si(C a) {
+    return S > 0 ? mkc(-a.y, a.x) : mkc(a.y, -a.x);
+}
+// a * exp(S i theta) given c = (cos, sin) of theta
+template <int S, class C> __device__ __forceinline__ C mul_dir(C a, C w) {
+    return S > 0 ? cmul(a, w) : cmul(a, cconj(w));
+}
+
+// ------------------------------------------------------------------ DFTs
+// cos and sin of multiples of 2 pi/16 (closed forms: cos(pi/8) =
+// sqrt(2+sqrt(2))/2, cos(pi/4) = sqrt(2)/2, sin(pi/8) = sqrt(2-sqrt(2))/2).
+#define MPA_COS_PI_8 0.92387953251128675613
+#define MPA_SIN_PI_8 0.38268343236508977173
+#define MPA_COS_PI_4 0.70710678118654752440
+
+// v * exp(S 2 pi i K/R), R <= 16, 0 <= K < R/2 (compile-time special cases)
+template <int R, int K, int S, class C> __device__ __forceinline__ C tw_const(C v) {
+    typedef decltype(v.x) T;
+    constexpr int K16 = K * (16 / R);
+    if constexpr (K16 == 0) {
+        return v;
+    } else if constexpr (K16 == 4) {
+        return mul_si<S>(v);
+    } else if constexpr (K16 == 2 || K16 == 6) {
+        const T c = (T)MPA_COS_PI_4;
+        constexpr T re = (K16 == 2) ? T(1) : T(-1);
+        // (re + S i) c
+        return mkc(c * (re * v.x - T(S) * v.y), c * (re * v.y + T(S) * v.x));
+    } else {
+        const T a = (T)MPA_COS_PI_8, b = (T)MPA_SIN_PI_8;
+        // K16 = 1: (a, b); 3: (b, a); 5: (-b, a); 7: (-a, b)
+        const T cr = (K16 == 1) ? a : (K16 == 3) ? b : (K16 == 5) ? -b : -a;
+        const T ci = (K16 == 1 || K16 == 7) ? b : a;
+        const T si = T(S) * ci;
+        return mkc(v.x * cr - v.y * si, v.x * si + v.y * cr);
+    }
+}
+
+template <int R, int S, int K, class C> __device__ __forceinline__ void dft_combine(C* x, const C* e, const C* o) {
+    if constexpr (K < R / 2) {
+        const C t = tw_const<R, K, S>(o[K]);
+        x[K] = cadd(e[K], t);
+        x[K + R / 2] = csub(e[K], t);
+        dft_combine<R, S, K + 1>(x, e, o);
+    }
+}
+
+// In-register DFT of R points (power of two <= 16): X_k = sum_r x_r W^{rk},
+// W = exp(S 2 pi i / R), by even/odd splitting.
+template <int R, int S, class C> struct Dft {
+    static __device__ __forceinline__ void run(C* x) {
+        C e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = x[2 * i];
+            o[i] = x[2 * i + 1];
+        }
+        Dft<R / 2, S, C>::run(e);
+        Dft<R / 2, S, C>::run(o);
+        dft_combine<R, S, 0>(x, e, o);
+    }
+};
+template <int S, class C> struct Dft<1, S, C> {
+    static __device__ __forceinline__ void run(C*) {}
+};
+template <int S, class C> struct Dft<2, S, C> {
+    static __device__ __forceinline__ void run(C* x) {
+        const C a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    }
+};
+
+// --------------------------------------------------------- exact phase
+// Per-node (or per-linear-step) constants.  The dispersion phase
+// beta(w_k, z) = w^2/2 I2 + w^3/6 I3 with w = 2 pi k'/T is, in turns,
+//   theta = k'^2 a + k'^3 b,  a = pi I2 / T^2,  b = 2 pi^2 I3 / (3 T^3).
+// The host stores a mod 1 and b mod 1 as 128-bit binary fractions (exact
+// for the FP64 values of a and b); the device reduces theta mod 1 exactly in
+// 64-bit integer arithmetic, so no FP64 arithmetic and no large-argument
+// range reduction is needed however large beta grows.
+struct NodeC {
+    unsigned long long a_hi, a_lo, b_hi, b_lo;
+    double pre;  // MPA: exp(int_{z0}^{z_j} G) = exp(-gamma (z_j - z0)); SS: linear-step gain
+    double post; // MPA: sigma(z_j) dz / pre (weight of V_j in Eq. (6))
+};
+
+// frac(k'^2 a + k'^3 b) as an unsigned Q0.64 number of turns (error < 3 ulp).
+// frac(k'^3 b) = frac(k' frac(k'^2 b)) since k'^3 b - k' frac(k'^2 b) is an
+// integer multiple of k'.
+__device__ __forceinline__ unsigned long long phase_q64(long long kp, const NodeC& c) {
+    const unsigned long long ak = (unsigned long long)(kp < 0 ? -kp : kp);
+    const unsigned long long u = ak * ak;  // < 2^50 for N <= 2^25
+    const unsigned long long ta = u * c.a_hi + __umul64hi(u, c.a_lo);
+    const unsigned long long f_lo = u * c.b_lo;
+    const unsigned long long f_hi = u * c.b_hi + __umul64hi(u, c.b_lo);
+    unsigned long long tb = ak * f_hi + __umul64hi(ak, f_lo);
+    if (kp < 0) tb = 0ull - tb;  // odd power of k'
+    return ta + tb;
+}
+
+// exp(2 pi i theta) for theta a Q0.64 fraction of a turn: reinterpret as a
+// signed fraction in [-1/2, 1/2) and evaluate sin/cos of pi * (2 theta).
+template <typename T> __device__ __forceinline__ cx<T> expi_turns(unsigned long long th);
+template <> __device__ __forceinline__ float2 expi_turns<float>(unsigned long long th) {
+    const float x = __ll2float_rn((long long)th) * 1.0842021724855044e-19f;  // 2^-63
+    float s, c;
+    sincospif(x, &s, &c);
+    return make_float2(c, s);
+}
+template <> __device__ __forceinline__ double2 expi_turns<double>(unsigned long long th) {
+    const double x = __ll2double_rn((long long)th) * 1.0842021724855044e-19;  // 2^-63
+    double s, c;
+    sincospi(x, &s, &c);
+    return make_double2(c, s);
+}
+
+// exp(2 pi i e / n) for an integer e (|e| small enough to be exact in T
+// after reduction to [-n/2, n/2)), n a power of two given by log2.
+template <typename T> __device__ __forceinline__ cx<T> expi_ratio(long long e, int log2n) {
+    const long long n = 1ll << log2n;
+    e &= (n - 1);
+    if (e >= (n >> 1)) e -= n;
+    const T x = (T)e * (T)2 / (T)n;  // exact: |e| <= 2^24 (FP32) or 2^52 (FP64)
+    T s, c;
+    if constexpr (sizeof(T) == 4) sincospif(x, &s, &c);
+    else sincospi(x, &s, &c);
+    return mkc(c, s);
+}
+
+// ------------------------------------------------- shared-memory Stockham
+// Padding of the shared-memory tile: one extra element per 2^PSH elements
+// keeps every pass free of bank conflicts (PSH = log2 of the largest radix).
+template <int PSH> __device__ __forceinline__ int phys(int i) { return i + (i >> PSH); }
+
+// Tile layouts of G independent transforms of length L:
+//   COL: element (l, g) at l*G + g  (a tile of G columns of an N2 x N1 matrix)
+//   ROW: element (l, g) at g*L + l  (G contiguous rows)
+enum { LAYOUT_COL = 0, LAYOUT_ROW = 1 };
+
+template <int LAYOUT, int L, int G> __device__ __forceinline__ int eidx(int l, int g) {
+    return LAYOUT == LAYOUT_COL ? l * G + g : g * L + l;
+}
+
+// Two-level table of W_L^e = exp(2 pi i e/L): hi[e >> SH] * lo[e & (2^SH-1)].
+template <int L> struct TwDims {
+    static constexpr int logL = (L >= 16384) ? 14 : (L >= 8192) ? 13 : (L >= 4096) ? 12 : (L >= 2048) ? 11
+                              : (L >= 1024) ? 10 : (L >= 512) ? 9 : (L >= 256) ? 8 : (L >= 128) ? 7
+                              : (L >= 64) ? 6 : (L >= 32) ? 5 : (L >= 16) ? 4 : (L >= 8) ? 3 : (L >= 4) ? 2 : 1;
+    static constexpr int SH = (logL + 1) / 2;
+    static constexpr int NLO = 1 << SH;
+    static constexpr int NHI = L >> SH;
+};
+
+template <typename T, int L> __device__ __forceinline__ void tw_init(cx<T>* hi, cx<T>* lo, int tid, int nt) {
+    typedef TwDims<L> D;
+    for (int i = tid; i < D::NLO + D::NHI; i += nt) {
+        if (i < D::NLO) lo[i] = expi_ratio<T>(i, D::logL);
+        else hi[i - D::NLO] = expi_ratio<T>((long long)(i - D::NLO) << D::SH, D::logL);
+    }
+}
+
+template <typename T, int L> __device__ __forceinline__ cx<T> tw_get(const cx<T>* hi, const cx<T>* lo, int e) {
+    typedef TwDims<L> D;
+    if constexpr (D::NHI == 1) return lo[e];
+    else return cmul(hi[e >> D::SH], lo[e & (D::NLO - 1)]);
+}
+
+// v[r] *= W_L^{S r e1} for r = 1..R-1, from table powers w1, w2, w4, w8
+// (each a table lookup) combined in at most three products.
+template <typename T, int L, int R, int S>
+__device__ __forceinline__ void twiddle_row(cx<T>* v, int e1, const cx<T>* hi, const cx<T>* lo) {
+    typedef cx<T> C;
+    C w[R];
+    w[1] = tw_get<T, L>(hi, lo, e1);
+    if constexpr (R > 2) w[2] = tw_get<T, L>(hi, lo, 2 * e1);
+    if constexpr (R > 4) w[4] = tw_get<T, L>(hi, lo, 4 * e1);
+    if constexpr (R > 8) w[8] = tw_get<T, L>(hi, lo, 8 * e1);
+    if constexpr (R > 2) w[3] = cmul(w[1], w[2]);
+    if constexpr (R > 4) {
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+    }
+    if constexpr (R > 8) {
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = mul_dir<S>(v[r], w[r]);
+}
+
+// One radix-R Stockham pass over the tile (in place, barrier-separated
+// read and write phases).  Butterfly j of transform g reads elements
+// j + r L/R, applies W_{NS R}^{S r (j mod NS)}, does the R-point DFT and
+// writes to (j - j mod NS) R + j mod NS + r NS.
+template <typename T, int L, int G, int NT, int R, int NS, int S, int LAYOUT, int PSH>
+__device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
+    typedef cx<T> C;
+    constexpr int NB = (L / R) * G;
+    static_assert(NB % NT == 0, "butterflies must divide among threads");
+    constexpr int Q = NB / NT;
+    C v[Q][R];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = threadIdx.x + q * NT;
+        const int j = LAYOUT == LAYOUT_COL ? b / G : b % (L / R);
+        const int g = LAYOUT == LAYOUT_COL ? b % G : b / (L / R);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = s[phys<PSH>(eidx<LAYOUT, L, G>(j + r * (L / R), g))];
+        if constexpr (NS > 1) twiddle_row<T, L, R, S>(v[q], (j & (NS - 1)) * (L / (NS * R)), hi, lo);
+        Dft<R, S, C>::run(v[q]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = threadIdx.x + q * NT;
+        const int j = LAYOUT == LAYOUT_COL ? b / G : b % (L / R);
+        const int g = LAYOUT == LAYOUT_COL ? b % G : b / (L / R);
+        const int k = j & (NS - 1);
+        const int dst = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(dst + r * NS, g))] = v[q][r];
+    }
+    __syncthreads();
+}
+
+// Full transform: radix-RMAX passes, the last one of radix L/NS.
+template <typename T, int L, int G, int NT, int RMAX, int NS, int S, int LAYOUT, int PSH>
+__device__ __forceinline__ void stockham(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
+    if constexpr (NS < L) {
+        constexpr int R = (L / NS) < RMAX ? (L / NS) : RMAX;
+        stockham_pass<T, L, G, NT, R, NS, S, LAYOUT, PSH>(s, hi, lo);
+        stockham<T, L, G, NT, RMAX, NS * R, S, LAYOUT, PSH>(s, hi, lo);
+    }
+}
+
+// Precision-dependent tiling: elements per thread E, largest radix, the
+// padding shift, the minimum column-tile width (64-byte row segments) and
+// the target tile size in elements.
+template <typename T> struct Tiling;
+template <> struct Tiling<float> {
+    static constexpr int E = 32, RMAX = 16, PSH = 4, CMIN = 8, TE = 8192;
+};
+template <> struct Tiling<double> {
+    static constexpr int E = 16, RMAX = 8, PSH = 3, CMIN = 4, TE = 4096;
+};
+
+}  // namespace mpa

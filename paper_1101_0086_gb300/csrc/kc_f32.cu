@@ -1,0 +1,65 @@
+// Column-pass launchers, float.
+#include "launch.h"
+
+namespace mpa {
+
+template <int L, int MODE>
+static cudaError_t kc_one(const KCParams<float>& p, cudaStream_t st) {
+    typedef KCGeom<float, L> Gm;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kc_kernel<float, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Gm::smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long nblk = (p.ncols + Gm::G - 1) / Gm::G;
+    if (nblk <= 0) return cudaSuccess;
+    kc_kernel<float, L, MODE><<<(unsigned)nblk, Gm::NT, Gm::smem_bytes, st>>>(p);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t kc_mode(int mode, const KCParams<float>& p, cudaStream_t st) {
+    switch (mode) {
+        case KC_MPA_PRE: return kc_one<L, KC_MPA_PRE>(p, st);
+        case KC_MPA_POST: return kc_one<L, KC_MPA_POST>(p, st);
+        case KC_SS_STEP: return kc_one<L, KC_SS_STEP>(p, st);
+        case KC_FWD: return kc_one<L, KC_FWD>(p, st);
+        case KC_INV: return kc_one<L, KC_INV>(p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <>
+cudaError_t kc_launch<float>(int mode, int logL, const KCParams<float>& p, cudaStream_t st) {
+    switch (logL) {
+        case 4: return kc_mode<16>(mode, p, st);
+        case 5: return kc_mode<32>(mode, p, st);
+        case 6: return kc_mode<64>(mode, p, st);
+        case 7: return kc_mode<128>(mode, p, st);
+        case 8: return kc_mode<256>(mode, p, st);
+        case 9: return kc_mode<512>(mode, p, st);
+        case 10: return kc_mode<1024>(mode, p, st);
+        case 11: return kc_mode<2048>(mode, p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <>
+long long kc_blocks<float>(int logL, long long ncols) {
+    switch (logL) {
+        case 4: return (ncols + KCGeom<float, 16>::G - 1) / KCGeom<float, 16>::G;
+        case 5: return (ncols + KCGeom<float, 32>::G - 1) / KCGeom<float, 32>::G;
+        case 6: return (ncols + KCGeom<float, 64>::G - 1) / KCGeom<float, 64>::G;
+        case 7: return (ncols + KCGeom<float, 128>::G - 1) / KCGeom<float, 128>::G;
+        case 8: return (ncols + KCGeom<float, 256>::G - 1) / KCGeom<float, 256>::G;
+        case 9: return (ncols + KCGeom<float, 512>::G - 1) / KCGeom<float, 512>::G;
+        case 10: return (ncols + KCGeom<float, 1024>::G - 1) / KCGeom<float, 1024>::G;
+        case 11: return (ncols + KCGeom<float, 2048>::G - 1) / KCGeom<float, 2048>::G;
+    }
+    return -1;
+}
+
+}  // namespace mpa

@@ -1,0 +1,355 @@
+// Kernels of the MPA node transform (MPA steps 2-5) and of the split-step
+// comparator, on the four-step factorisation N = N1 * N2.
+//
+// A spectrum in natural order, k = k1 + N1 k2, is viewed as an N2 x N1
+// row-major matrix.  The inverse transform is a column pass (length-N2 DFTs
+// over k2, then the factor W_N^{-n2 k1}) followed by a row pass (length-N1
+// DFTs over k1); row n2 then holds A(t) at t-index N2 n1 + n2 for
+// n1 = 0..N1-1.  Because |A|^2 A (MPA step 4) and the split-step rotation
+// are pointwise, the row pass forms them right there and starts the forward
+// transform (length-N1 DFTs over n1, factor W_N^{+n2 k1}) without any
+// transpose; the next column pass finishes it (length-N2 DFTs over n2) and
+// leaves the spectrum in natural order again.
+//
+//   KC (column pass)  modes: MPA_PRE  phase exp(i beta_j) * exp(int G) -> inverse
+//                             MPA_POST forward -> exp(-i beta_j) * sigma dz / exp(int G)  (V_j of Eq. (6))
+//                             SS_STEP  forward -> linear step of Eq. (4) -> inverse
+//                             FWD      forward only        INV  inverse only
+//   KR (row pass)     modes: MPA  inverse -> 1/N -> |A|^2 A -> forward
+//                             SS   inverse -> 1/N -> A exp(i s |A|^2) -> forward
+//                             FWD  forward only        INV  inverse -> 1/N
+//   SCAN              Eq. (6) trapezoid partial sums over the nodes for
+//                     every frequency, fused with step 7 on the last iteration.
+#pragma once
+
+#include "device.cuh"
+
+namespace mpa {
+
+enum { KC_MPA_PRE = 0, KC_MPA_POST = 1, KC_SS_STEP = 2, KC_FWD = 3, KC_INV = 4 };
+enum { KR_MPA = 0, KR_SS = 1, KR_FWD = 2, KR_INV = 3 };
+
+template <typename T> struct KCParams {
+    const cx<T>* src;
+    long long src_stride;  // elements between consecutive nodes of the source (0: shared source)
+    cx<T>* dst;
+    long long dst_stride;
+    long long N;
+    int logN;
+    int N1, logN1;
+    long long ncols;     // nodes * N1 columns in this launch
+    const NodeC* nodes;  // MPA: constants of the launch's node 0, 1, ...
+    NodeC flow;          // SS: constants of the linear step
+};
+
+template <typename T> struct KRParams {
+    cx<T>* data;  // nrows contiguous rows of length N1
+    long long nrows;
+    long long N;
+    int logN;
+    int N2;
+    T inv_n;  // 1/N
+    T rot;    // SS: int sigma over the step
+};
+
+// Column pass geometry for column length L: G columns per tile, NT threads.
+template <typename T, int L> struct KCGeom {
+    typedef Tiling<T> P;
+    static constexpr int G = (P::TE / L) > P::CMIN ? (P::TE / L) : P::CMIN;
+    static constexpr int TE = G * L;
+    static constexpr int NT = TE / P::E;
+    static constexpr int OSH = 5;  // outer-factor two-level split of n2
+    static constexpr int OLO = L < 32 ? L : 32;
+    static constexpr int OHI = L > 32 ? L / 32 : 1;
+    static constexpr size_t smem_elems = (size_t)TE + (TE >> P::PSH) + 1 + TwDims<L>::NLO + TwDims<L>::NHI +
+                                         (size_t)G * (OLO + OHI);
+    static constexpr size_t smem_bytes = smem_elems * sizeof(cx<T>);
+};
+
+template <typename T, int L> struct KRGeom {
+    typedef Tiling<T> P;
+    static constexpr int G = (P::TE / L) > 1 ? (P::TE / L) : 1;
+    static constexpr int TE = G * L;
+    static constexpr int NT = TE / P::E;
+    static constexpr int OSH = 7;  // outer-factor split of k1
+    static constexpr int OLO = L < 128 ? L : 128;
+    static constexpr int OHI = L > 128 ? L / 128 : 1;
+    static constexpr size_t smem_elems = (size_t)TE + (TE >> P::PSH) + 1 + TwDims<L>::NLO + TwDims<L>::NHI +
+                                         (size_t)G * (OLO + OHI);
+    static constexpr size_t smem_bytes = smem_elems * sizeof(cx<T>);
+};
+
+__device__ __forceinline__ long long signed_k(long long k, long long N) { return k < (N >> 1) ? k : k - N; }
+
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(KCGeom<T, L>::NT) kc_kernel(const KCParams<T> p) {
+    typedef cx<T> C;
+    typedef KCGeom<T, L> Gm;
+    typedef Tiling<T> P;
+    constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
+    constexpr bool FWD = (MODE == KC_MPA_POST || MODE == KC_SS_STEP || MODE == KC_FWD);
+    constexpr bool INV = (MODE == KC_MPA_PRE || MODE == KC_SS_STEP || MODE == KC_INV);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    C* olo = tlo + TwDims<L>::NLO;  // [G][OLO]
+    C* ohi = olo + G * Gm::OLO;     // [G][OHI]
+    const int tid = threadIdx.x;
+    const long long col0 = (long long)blockIdx.x * G;
+    const int N1m = p.N1 - 1;
+
+    tw_init<T, L>(thi, tlo, tid, NT);
+    if constexpr (INV) {
+        // W_N^{-n2 k1} for the tile's columns: olo[g][m] = W^{-k1 m}, ohi[g][h] = W^{-k1 32 h}
+        for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
+            const int g = i / (Gm::OLO + Gm::OHI), m = i % (Gm::OLO + Gm::OHI);
+            const long long k1 = (col0 + g) & N1m;
+            if (m < Gm::OLO) olo[g * Gm::OLO + m] = expi_ratio<T>(-k1 * m, p.logN);
+            else ohi[g * Gm::OHI + (m - Gm::OLO)] = expi_ratio<T>(-k1 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+        }
+    }
+
+    // load the tile (element (l, g) = row l of column col0 + g)
+#pragma unroll 4
+    for (int i = tid; i < TE; i += NT) {
+        const int l = i / G, g = i % G;
+        const long long col = col0 + g;
+        C v = mkc(T(0), T(0));
+        if (col < p.ncols) {
+            const long long node = col >> p.logN1;
+            const long long c = col & N1m;
+            v = p.src[node * p.src_stride + (long long)l * p.N1 + c];
+            if constexpr (MODE == KC_MPA_PRE) {
+                // MPA step 2: A_hat_j = psi_j exp(i beta(w, z_j) + int G)
+                const NodeC nc = p.nodes[node];
+                const long long k = c + (long long)l * p.N1;
+                const C ph = expi_turns<T>(phase_q64(signed_k(k, p.N), nc));
+                v = cscale(cmul(v, ph), (T)nc.pre);
+            }
+        }
+        s[phys<P::PSH>(i)] = v;
+    }
+    __syncthreads();
+
+    if constexpr (FWD) stockham<T, L, G, NT, P::RMAX, 1, +1, LAYOUT_COL, P::PSH>(s, thi, tlo);
+
+    if constexpr (MODE == KC_SS_STEP) {
+        // exact linear step exp(i beta(w; za, zb) + int G) between the kicks
+        for (int i = tid; i < TE; i += NT) {
+            const int l = i / G, g = i % G;
+            const long long c = (col0 + g) & N1m;
+            const long long k = c + (long long)l * p.N1;
+            C v = s[phys<P::PSH>(i)];
+            const C ph = expi_turns<T>(phase_q64(signed_k(k, p.N), p.flow));
+            s[phys<P::PSH>(i)] = cscale(cmul(v, ph), (T)p.flow.pre);
+        }
+        __syncthreads();
+    }
+
+    if constexpr (INV) stockham<T, L, G, NT, P::RMAX, 1, -1, LAYOUT_COL, P::PSH>(s, thi, tlo);
+
+    // store
+#pragma unroll 4
+    for (int i = tid; i < TE; i += NT) {
+        const int l = i / G, g = i % G;
+        const long long col = col0 + g;
+        if (col >= p.ncols) continue;
+        const long long node = col >> p.logN1;
+        const long long c = col & N1m;
+        C v = s[phys<P::PSH>(i)];
+        if constexpr (INV) {
+            // four-step factor W_N^{-n2 k1}, n2 = l
+            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+            if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
+            v = cmul(v, w);
+        }
+        if constexpr (MODE == KC_MPA_POST) {
+            // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
+            const NodeC nc = p.nodes[node];
+            const long long k = c + (long long)l * p.N1;
+            const C ph = expi_turns<T>(phase_q64(signed_k(k, p.N), nc));
+            v = cscale(cmul(v, cconj(ph)), (T)nc.post);
+        }
+        p.dst[node * p.dst_stride + (long long)l * p.N1 + c] = v;
+    }
+}
+
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(KRGeom<T, L>::NT) kr_kernel(const KRParams<T> p) {
+    typedef cx<T> C;
+    typedef KRGeom<T, L> Gm;
+    typedef Tiling<T> P;
+    constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
+    constexpr bool INV = (MODE != KR_FWD);
+    constexpr bool FWD = (MODE != KR_INV);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    C* olo = tlo + TwDims<L>::NLO;  // [G][OLO]
+    C* ohi = olo + G * Gm::OLO;     // [G][OHI]
+    const int tid = threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * G;
+
+    tw_init<T, L>(thi, tlo, tid, NT);
+    if constexpr (FWD) {
+        // W_N^{+n2 k1} for the tile's rows: olo[g][m] = W^{n2 m}, ohi[g][h] = W^{n2 128 h}
+        for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
+            const int g = i / (Gm::OLO + Gm::OHI), m = i % (Gm::OLO + Gm::OHI);
+            const long long n2 = (row0 + g) % p.N2;
+            if (m < Gm::OLO) olo[g * Gm::OLO + m] = expi_ratio<T>(n2 * m, p.logN);
+            else ohi[g * Gm::OHI + (m - Gm::OLO)] = expi_ratio<T>(n2 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+        }
+    }
+
+    C* base = p.data + row0 * L;
+    const long long lim = (p.nrows - row0) * L;  // elements of this tile that exist
+#pragma unroll 4
+    for (int i = tid; i < TE; i += NT) s[phys<P::PSH>(i)] = (i < lim) ? base[i] : mkc(T(0), T(0));
+    __syncthreads();
+
+    if constexpr (INV) {
+        stockham<T, L, G, NT, P::RMAX, 1, -1, LAYOUT_ROW, P::PSH>(s, thi, tlo);
+        if constexpr (MODE != KR_INV) {
+            for (int i = tid; i < TE; i += NT) {
+                C a = cscale(s[phys<P::PSH>(i)], p.inv_n);  // A(t) (MPA step 3 / SS inverse)
+                const T pw = a.x * a.x + a.y * a.y;
+                if constexpr (MODE == KR_MPA) {
+                    a = cscale(a, pw);  // |A|^2 A (MPA step 4)
+                } else {
+                    T sn, cs;  // A exp(i s |A|^2), the nonlinear step of Eq. (4)
+                    if constexpr (sizeof(T) == 4) sincosf(p.rot * pw, &sn, &cs);
+                    else sincos(p.rot * pw, &sn, &cs);
+                    a = cmul(a, mkc(cs, sn));
+                }
+                s[phys<P::PSH>(i)] = a;
+            }
+            __syncthreads();
+        }
+    }
+    if constexpr (FWD) stockham<T, L, G, NT, P::RMAX, 1, +1, LAYOUT_ROW, P::PSH>(s, thi, tlo);
+
+#pragma unroll 4
+    for (int i = tid; i < TE; i += NT) {
+        if (i >= lim) continue;
+        C v = s[phys<P::PSH>(i)];
+        if constexpr (FWD) {
+            const int g = i / L, l = i % L;  // l = k1
+            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+            if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
+            v = cmul(v, w);
+        } else {
+            v = cscale(v, p.inv_n);
+        }
+        base[i] = v;
+    }
+}
+
+// Eq. (6) for every frequency k: running trapezoid sum over nodes j = 1..M
+//   psi^{(n+1)}_l = psi_0 + i (V_0/2 + sum_{j=1}^{l-1} V_j + V_l/2),
+// with V_j stored in psi[j] (node 0 holds V_0).  FP32 sums are Kahan-
+// compensated; the final value at node M is formed in FP64.
+//   mode 0: write psi^{(n+1)}_j into psi[j] (next iteration)
+//   mode 1: step 7: state <- psi_M exp(i beta(w, z0+L) + int G) * gain, psi0c <- state
+//   mode 2: out <- psi_M (FP64, no step 7)
+template <typename T> struct ScanParams {
+    cx<T>* psi;
+    long long N;
+    int M;
+    const cx<T>* psi0c;  // psi_0 in the working precision
+    double2* state;      // FP64 psi_0 in, A_hat(z0+L) out (mode 1)
+    cx<T>* psi0c_out;    // mode 1: working-precision copy of the new state
+    double2* out;        // mode 2
+    int mode;
+    NodeC nodeM;
+    double gain;
+    unsigned int* err;
+};
+
+template <typename T> __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
+    typedef cx<T> C;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.N) return;
+    const C v0 = p.psi[k];
+    T rx = T(0.5) * v0.x, ry = T(0.5) * v0.y, cxx = T(0), cyy = T(0);
+    const C p0 = p.psi0c[k];
+    C vl = v0;
+    for (int j = 1; j <= p.M; ++j) {
+        C* q = p.psi + (long long)j * p.N + k;
+        vl = *q;
+        if (p.mode == 0) {
+            // psi_0 + i (R + V_j/2), R = running sum (compensation removed)
+            const T sx = (rx - cxx) + T(0.5) * vl.x, sy = (ry - cyy) + T(0.5) * vl.y;
+            *q = mkc(p0.x - sy, p0.y + sx);
+        }
+        if constexpr (sizeof(T) == 4) {
+            kahan_add(rx, cxx, vl.x);
+            kahan_add(ry, cyy, vl.y);
+        } else {
+            rx += vl.x;
+            ry += vl.y;
+        }
+    }
+    if (p.mode == 0) return;
+    // psi_M = psi_0 + i (R_M - V_M/2) in FP64
+    const double sx = ((double)rx - (double)cxx) - 0.5 * (double)vl.x;
+    const double sy = ((double)ry - (double)cyy) - 0.5 * (double)vl.y;
+    const double2 s0 = p.state[k];
+    const double2 psiM = make_double2(s0.x - sy, s0.y + sx);
+    if (p.mode == 2) {
+        p.out[k] = psiM;
+        return;
+    }
+    // step 7 and the lumped gain
+    const double2 ph = expi_turns<double>(phase_q64(signed_k(k, p.N), p.nodeM));
+    const double g = p.nodeM.pre * p.gain;
+    const double2 a = make_double2(g * (psiM.x * ph.x - psiM.y * ph.y), g * (psiM.x * ph.y + psiM.y * ph.x));
+    p.state[k] = a;
+    p.psi0c_out[k] = mkc((T)a.x, (T)a.y);
+    if (!(isfinite(a.x) && isfinite(a.y))) atomicOr(p.err, 1u);
+}
+
+// out[c][r] = in[r][c] for an R x Cc matrix (32 x 32 tiles).
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_kernel(const cx<T>* __restrict__ in, cx<T>* __restrict__ out,
+                                                         long long R, long long Cc) {
+    __shared__ cx<T> t[32][33];
+    const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const long long r = r0 + y, c = c0 + threadIdx.x;
+        if (r < R && c < Cc) t[y][threadIdx.x] = in[r * Cc + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const long long c = c0 + y, r = r0 + threadIdx.x;
+        if (r < R && c < Cc) out[c * R + r] = t[threadIdx.x][y];
+    }
+}
+
+// Precision conversions between the FP64 state and working buffers.
+template <typename T>
+__global__ void __launch_bounds__(256) to_state_kernel(const cx<T>* in, double2* state, cx<T>* copy, long long N) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const cx<T> v = in[k];
+    state[k] = make_double2((double)v.x, (double)v.y);
+    if (copy) copy[k] = v;
+}
+template <typename T>
+__global__ void __launch_bounds__(256) from_state_kernel(const double2* state, cx<T>* out, long long N) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const double2 v = state[k];
+    out[k] = mkc((T)v.x, (T)v.y);
+}
+
+}  // namespace mpa

@@ -1,0 +1,68 @@
+// Row-pass launchers, double.
+#include "launch.h"
+
+namespace mpa {
+
+template <int L, int MODE>
+static cudaError_t kr_one(const KRParams<double>& p, cudaStream_t st) {
+    typedef KRGeom<double, L> Gm;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kr_kernel<double, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Gm::smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long nblk = (p.nrows + Gm::G - 1) / Gm::G;
+    if (nblk <= 0) return cudaSuccess;
+    kr_kernel<double, L, MODE><<<(unsigned)nblk, Gm::NT, Gm::smem_bytes, st>>>(p);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t kr_mode(int mode, const KRParams<double>& p, cudaStream_t st) {
+    switch (mode) {
+        case KR_MPA: return kr_one<L, KR_MPA>(p, st);
+        case KR_SS: return kr_one<L, KR_SS>(p, st);
+        case KR_FWD: return kr_one<L, KR_FWD>(p, st);
+        case KR_INV: return kr_one<L, KR_INV>(p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <>
+cudaError_t kr_launch<double>(int mode, int logL, const KRParams<double>& p, cudaStream_t st) {
+    switch (logL) {
+        case 4: return kr_mode<16>(mode, p, st);
+        case 5: return kr_mode<32>(mode, p, st);
+        case 6: return kr_mode<64>(mode, p, st);
+        case 7: return kr_mode<128>(mode, p, st);
+        case 8: return kr_mode<256>(mode, p, st);
+        case 9: return kr_mode<512>(mode, p, st);
+        case 10: return kr_mode<1024>(mode, p, st);
+        case 11: return kr_mode<2048>(mode, p, st);
+        case 12: return kr_mode<4096>(mode, p, st);
+        case 13: return kr_mode<8192>(mode, p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <>
+long long kr_blocks<double>(int logL, long long nrows) {
+    switch (logL) {
+        case 4: return (nrows + KRGeom<double, 16>::G - 1) / KRGeom<double, 16>::G;
+        case 5: return (nrows + KRGeom<double, 32>::G - 1) / KRGeom<double, 32>::G;
+        case 6: return (nrows + KRGeom<double, 64>::G - 1) / KRGeom<double, 64>::G;
+        case 7: return (nrows + KRGeom<double, 128>::G - 1) / KRGeom<double, 128>::G;
+        case 8: return (nrows + KRGeom<double, 256>::G - 1) / KRGeom<double, 256>::G;
+        case 9: return (nrows + KRGeom<double, 512>::G - 1) / KRGeom<double, 512>::G;
+        case 10: return (nrows + KRGeom<double, 1024>::G - 1) / KRGeom<double, 1024>::G;
+        case 11: return (nrows + KRGeom<double, 2048>::G - 1) / KRGeom<double, 2048>::G;
+        case 12: return (nrows + KRGeom<double, 4096>::G - 1) / KRGeom<double, 4096>::G;
+        case 13: return (nrows + KRGeom<double, 8192>::G - 1) / KRGeom<double, 8192>::G;
+    }
+    return -1;
+}
+
+}  // namespace mpa

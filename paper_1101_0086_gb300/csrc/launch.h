@@ -1,0 +1,31 @@
+// Host-side launchers of the kernels in kernels.cuh (one translation unit
+// per kernel family and precision, compiled in parallel).
+#pragma once
+
+#include <atomic>
+
+#include "kernels.cuh"
+
+namespace mpa {
+
+// Kernels launched by this library since load.
+extern std::atomic<long long> g_launches;
+
+// Column/row lengths supported by the column pass (2^4..2^11) and the row
+// pass (2^4..2^14 FP32, 2^4..2^13 FP64).
+constexpr int KC_LOG_MIN = 4, KC_LOG_MAX = 11;
+constexpr int KR_LOG_MIN = 4;
+template <typename T> constexpr int kr_log_max() { return sizeof(T) == 4 ? 14 : 13; }
+
+template <typename T> cudaError_t kc_launch(int mode, int logL, const KCParams<T>& p, cudaStream_t st);
+template <typename T> cudaError_t kr_launch(int mode, int logL, const KRParams<T>& p, cudaStream_t st);
+template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, cudaStream_t st);
+template <typename T> cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long C, cudaStream_t st);
+template <typename T> cudaError_t to_state_launch(const cx<T>* in, double2* state, cx<T>* copy, long long N, cudaStream_t st);
+template <typename T> cudaError_t from_state_launch(const double2* state, cx<T>* out, long long N, cudaStream_t st);
+
+// Grid of a column pass over ncols columns of column length L.
+template <typename T> long long kc_blocks(int logL, long long ncols);
+template <typename T> long long kr_blocks(int logL, long long nrows);
+
+}  // namespace mpa

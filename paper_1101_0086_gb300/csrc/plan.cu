@@ -1,0 +1,550 @@
+// C ABI of the MPA / split-step library: plan creation (host tables of the
+// per-node constants of Eq. (6)), workspace layout, and the launch schedule
+// of the MPA steps 1-7 and of the split-step of Eq. (4).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "mpa.h"
+
+using namespace mpa;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+int cuda_fail(cudaError_t e) {
+    g_cuda_err = cudaGetErrorString(e);
+    return MPA_ERR_CUDA;
+}
+
+#define MPA_TRY(expr)                              \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) return cuda_fail(_e); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ----------------------------------------------------------- fiber map
+struct HostMap {
+    std::vector<mpa_segment> seg;
+    double gamma = 0, z_a = 0, period = 0, length = 0;
+
+    int init(const mpa_fiber_map* m) {
+        if (!m || !m->segments || m->n_segments < 1 || m->n_periods < 1) return MPA_ERR_INVALID_ARG;
+        if (!(m->gamma_per_km >= 0.0) || !std::isfinite(m->gamma_per_km) || !std::isfinite(m->z_a_km))
+            return MPA_ERR_INVALID_ARG;
+        seg.assign(m->segments, m->segments + m->n_segments);
+        for (const auto& s : seg) {
+            if (!(s.length_km > 0.0) || !std::isfinite(s.beta2_ps2_per_km) || !std::isfinite(s.beta3_ps3_per_km) ||
+                !std::isfinite(s.sigma_per_W_km))
+                return MPA_ERR_INVALID_ARG;
+            period += s.length_km;
+        }
+        gamma = m->gamma_per_km;
+        z_a = m->z_a_km;
+        length = period * m->n_periods;
+        return MPA_OK;
+    }
+    static double coef(const mpa_segment& s, int col) {
+        return col == 1 ? s.beta2_ps2_per_km : col == 2 ? s.beta3_ps3_per_km : s.sigma_per_W_km;
+    }
+    // int_za^zb of a coefficient: shift za into the first period, then sum
+    // coefficient x overlap over the segment copies that [za, zb] covers.
+    double integ(double za, double zb, int col) const {
+        if (!(zb > za)) return 0.0;
+        const double shift = std::floor(za / period) * period;
+        const double u = za - shift, v = zb - shift;
+        double acc = 0.0;
+        for (long p = 0; (double)p * period < v; ++p) {
+            double a = (double)p * period;
+            for (const auto& s : seg) {
+                const double b = a + s.length_km;
+                const double lo = a > u ? a : u, hi = b < v ? b : v;
+                if (hi > lo) acc += coef(s, col) * (hi - lo);
+                a = b;
+            }
+        }
+        return acc;
+    }
+    // coefficient just left (side < 0) or right (side > 0) of z
+    double side(double z, int col, int sgn) const {
+        const double zz = z + (sgn > 0 ? 1e-9 : -1e-9) * period;
+        double u = zz - std::floor(zz / period) * period;
+        double a = 0.0;
+        for (size_t i = 0; i < seg.size(); ++i) {
+            a += seg[i].length_km;
+            if (u < a || i + 1 == seg.size()) return coef(seg[i], col);
+        }
+        return coef(seg.back(), col);
+    }
+    // amplifiers k z_a (k >= 1) in (za, zb]
+    long amps(double za, double zb) const {
+        if (!(z_a > 0.0)) return 0;
+        const double tol = 1e-9 * z_a;
+        long ka = (long)std::floor((za + tol) / z_a), kb = (long)std::floor((zb + tol) / z_a);
+        if (ka < 0) ka = 0;
+        return kb > ka ? kb - ka : 0;
+    }
+};
+
+// x mod 1 as a 128-bit binary fraction (exact whenever the FP64 value x has
+// no bits below 2^-128).
+void frac_q128(double x, unsigned long long* hi, unsigned long long* lo) {
+    typedef unsigned __int128 u128;
+    u128 q = 0;
+    if (x != 0.0 && std::isfinite(x)) {
+        const double ax = std::fabs(x);
+        int e = 0;
+        const double m = std::frexp(ax, &e);  // ax = m 2^e, m in [0.5, 1)
+        const unsigned long long mant = (unsigned long long)std::ldexp(m, 53);
+        const int sh = e - 53 + 128;  // ax 2^128 = mant 2^sh
+        if (sh >= 128) q = 0;
+        else if (sh >= 0) q = (u128)mant << sh;
+        else if (sh > -64) q = (u128)(mant >> (-sh));
+        if (x < 0) q = (u128)0 - q;
+    }
+    *hi = (unsigned long long)(q >> 64);
+    *lo = (unsigned long long)q;
+}
+
+// Phase constants of beta(w, .) over an integral (I2, I3) for window T:
+// theta = k'^2 pi I2/T^2 + k'^3 2 pi^2 I3/(3 T^3) turns.
+void phase_consts(double I2, double I3, double T, NodeC* c) {
+    frac_q128(kPi * I2 / (T * T), &c->a_hi, &c->a_lo);
+    frac_q128(2.0 * kPi * kPi * I3 / (3.0 * T * T * T), &c->b_hi, &c->b_lo);
+}
+
+bool whole(double x, double* r) {
+    const double n = std::nearbyint(x);
+    *r = n;
+    return std::fabs(x - n) <= 1e-9 * (std::fabs(x) > 1.0 ? std::fabs(x) : 1.0);
+}
+
+int ilog2(long long n) {
+    int l = 0;
+    while ((1ll << l) < n) ++l;
+    return l;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Split {
+    int logN, logN1, logN2;
+    long long N, N1, N2;
+};
+
+int split_n(long long N, int prec, Split* s) {
+    if (N < 256 || (N & (N - 1)) != 0) return MPA_ERR_UNSUPPORTED_N;
+    s->logN = ilog2(N);
+    if (s->logN > (prec == MPA_FP32 ? 25 : 24)) return MPA_ERR_UNSUPPORTED_N;
+    s->logN2 = s->logN / 2 < KC_LOG_MAX ? s->logN / 2 : KC_LOG_MAX;
+    s->logN1 = s->logN - s->logN2;
+    const int rmax = prec == MPA_FP32 ? kr_log_max<float>() : kr_log_max<double>();
+    if (s->logN2 < KC_LOG_MIN || s->logN1 > rmax) return MPA_ERR_UNSUPPORTED_N;
+    s->N = N;
+    s->N1 = 1ll << s->logN1;
+    s->N2 = 1ll << s->logN2;
+    return MPA_OK;
+}
+
+// ------------------------------------------------ natural-order transforms
+// Forward: natural A(t) in `data` -> natural spectrum in `out` (may alias
+// scratch); data viewed as N1 x N2 (rows n1), transposed into scratch.
+template <typename T>
+int fft_forward(const Split& s, const cx<T>* data, cx<T>* scratch, cudaStream_t st) {
+    MPA_TRY(transpose_launch<T>(data, scratch, s.N1, s.N2, st));
+    KRParams<T> r{scratch, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
+    MPA_TRY(kr_launch<T>(KR_FWD, s.logN1, r, st));
+    KCParams<T> c{};
+    c.src = scratch;
+    c.dst = scratch;
+    c.N = s.N;
+    c.logN = s.logN;
+    c.N1 = (int)s.N1;
+    c.logN1 = s.logN1;
+    c.ncols = s.N1;
+    MPA_TRY(kc_launch<T>(KC_FWD, s.logN2, c, st));
+    return MPA_OK;
+}
+
+// Inverse: natural spectrum in `spec` (overwritten) -> natural A(t) in `out`.
+template <typename T>
+int fft_inverse(const Split& s, cx<T>* spec, cx<T>* out, cudaStream_t st) {
+    KCParams<T> c{};
+    c.src = spec;
+    c.dst = spec;
+    c.N = s.N;
+    c.logN = s.logN;
+    c.N1 = (int)s.N1;
+    c.logN1 = s.logN1;
+    c.ncols = s.N1;
+    MPA_TRY(kc_launch<T>(KC_INV, s.logN2, c, st));
+    KRParams<T> r{spec, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
+    MPA_TRY(kr_launch<T>(KR_INV, s.logN1, r, st));
+    MPA_TRY(transpose_launch<T>(spec, out, s.N2, s.N1, st));
+    return MPA_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+struct mpa_plan {
+    HostMap map;
+    Split sp;
+    double T, L;
+    int M, n_iter, prec;
+    int n_types;                // distinct interval starts within the DM period
+    std::vector<NodeC> nodes;   // n_types x (M+1)
+    size_t csize;               // bytes per complex sample
+    size_t off_psi, off_state, off_psi0c, off_nodes, off_err, ws_need;
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace {
+
+int interval_type(const mpa_plan* p, double z0, int* t) {
+    if (p->n_types == 1) {
+        *t = 0;
+        return MPA_OK;
+    }
+    const double u = z0 - std::floor(z0 / p->map.period + 1e-12) * p->map.period;
+    double r;
+    if (!whole(u / p->L, &r)) return MPA_ERR_GRID;
+    long q = (long)r % p->n_types;
+    if (q < 0) q += p->n_types;
+    *t = (int)q;
+    return MPA_OK;
+}
+
+template <typename T>
+int run_interval(mpa_plan* p, int type, double gain, int scan_mode, double2* out, cudaStream_t st) {
+    const Split& s = p->sp;
+    const long long N = s.N;
+    cx<T>* psi = reinterpret_cast<cx<T>*>(p->ws + p->off_psi);
+    double2* state = reinterpret_cast<double2*>(p->ws + p->off_state);
+    cx<T>* psi0c = reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c);
+    const NodeC* nodes = reinterpret_cast<const NodeC*>(p->ws + p->off_nodes) + (size_t)type * (p->M + 1);
+    unsigned int* err = reinterpret_cast<unsigned int*>(p->ws + p->off_err);
+    for (int n = 0; n < p->n_iter; ++n) {
+        // steps 2-4 for every node of the interval; node 0 (psi_0 never
+        // changes, so V_0 is the same for every iteration) only on the first.
+        const int j0 = n == 0 ? 0 : 1;
+        const long long nn = p->M + 1 - j0;
+        KCParams<T> c{};
+        c.src = n == 0 ? psi0c : psi + N;
+        c.src_stride = n == 0 ? 0 : N;
+        c.dst = psi + (long long)j0 * N;
+        c.dst_stride = N;
+        c.N = N;
+        c.logN = s.logN;
+        c.N1 = (int)s.N1;
+        c.logN1 = s.logN1;
+        c.ncols = nn * s.N1;
+        c.nodes = nodes + j0;
+        MPA_TRY(kc_launch<T>(KC_MPA_PRE, s.logN2, c, st));
+        KRParams<T> r{psi + (long long)j0 * N, nn * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
+        MPA_TRY(kr_launch<T>(KR_MPA, s.logN1, r, st));
+        c.src = psi + (long long)j0 * N;
+        c.src_stride = N;
+        MPA_TRY(kc_launch<T>(KC_MPA_POST, s.logN2, c, st));
+        // step 5 (Eq. (6)); on the last iteration fused with step 7
+        ScanParams<T> q{};
+        q.psi = psi;
+        q.N = N;
+        q.M = p->M;
+        q.psi0c = psi0c;
+        q.state = state;
+        q.psi0c_out = psi0c;
+        q.out = out;
+        q.mode = (n == p->n_iter - 1) ? scan_mode : 0;
+        q.nodeM = p->nodes[(size_t)type * (p->M + 1) + p->M];
+        q.gain = gain;
+        q.err = err;
+        MPA_TRY(scan_launch<T>(q, st));
+    }
+    return MPA_OK;
+}
+
+template <typename T>
+int propagate_t(mpa_plan* p, void* field, double z_from, double z_to, cudaStream_t st) {
+    const Split& s = p->sp;
+    const double L = p->L;
+    double qf, ni;
+    if (!(z_from >= -1e-12) || !(z_to >= z_from) || z_to > p->map.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
+    if (!whole(z_from / L, &qf) || !whole((z_to - z_from) / L, &ni)) return MPA_ERR_GRID;
+    const long n_int = (long)ni;
+    std::vector<int> types((size_t)n_int);
+    std::vector<double> gains((size_t)n_int);
+    for (long q = 0; q < n_int; ++q) {
+        const double z0 = z_from + L * (double)q;
+        if (p->map.amps(z0, z0 + L - 1e-6 * L) != 0) return MPA_ERR_GRID;
+        int t;
+        if (interval_type(p, z0, &t) != MPA_OK) return MPA_ERR_GRID;
+        types[(size_t)q] = t;
+        gains[(size_t)q] = std::exp((double)p->map.amps(z0, z0 + L) * p->map.z_a * p->map.gamma);
+    }
+    cx<T>* f = reinterpret_cast<cx<T>*>(field);
+    cx<T>* psi = reinterpret_cast<cx<T>*>(p->ws + p->off_psi);
+    double2* state = reinterpret_cast<double2*>(p->ws + p->off_state);
+    cx<T>* psi0c = reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c);
+    // A_hat(z_from) = F[A] -> FP64 state and its working copy
+    int rc = fft_forward<T>(s, f, psi, st);
+    if (rc) return rc;
+    MPA_TRY(to_state_launch<T>(psi, state, sizeof(T) == 4 ? psi0c : nullptr, s.N, st));
+    for (long q = 0; q < n_int; ++q) {
+        rc = run_interval<T>(p, types[(size_t)q], gains[(size_t)q], 1, nullptr, st);
+        if (rc) return rc;
+    }
+    // A(z_to) = F^-1[A_hat]
+    MPA_TRY(from_state_launch<T>(state, psi, s.N, st));
+    return fft_inverse<T>(s, psi, f, st);
+}
+
+template <typename T>
+int interval_t(mpa_plan* p, const void* psi0, void* psiM, double z0, cudaStream_t st) {
+    double q;
+    if (!whole(z0 / p->L, &q) || z0 < -1e-12 || z0 + p->L > p->map.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
+    if (p->map.amps(z0, z0 + p->L - 1e-6 * p->L) != 0) return MPA_ERR_GRID;
+    int t;
+    if (interval_type(p, z0, &t) != MPA_OK) return MPA_ERR_GRID;
+    double2* state = reinterpret_cast<double2*>(p->ws + p->off_state);
+    cx<T>* psi0c = reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c);
+    MPA_TRY(cudaMemcpyAsync(state, psi0, (size_t)p->sp.N * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    if (sizeof(T) == 4) MPA_TRY(from_state_launch<T>(state, psi0c, p->sp.N, st));
+    return run_interval<T>(p, t, 1.0, 2, reinterpret_cast<double2*>(psiM), st);
+}
+
+template <typename T>
+int ss_t(const HostMap& m, const Split& s, double T_ps, double dz, void* field, double z_from, double z_to,
+         void* ws, cudaStream_t st) {
+    double kk;
+    if (!(z_from >= -1e-12) || !(z_to > z_from) || z_to > m.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
+    if (!whole((z_to - z_from) / dz, &kk) || kk < 1) return MPA_ERR_GRID;
+    const long K = (long)kk;
+    cx<T>* f = reinterpret_cast<cx<T>*>(field);
+    cx<T>* w = reinterpret_cast<cx<T>*>(ws);
+    auto flow = [&](double za, double zb) {
+        NodeC c{};
+        phase_consts(m.integ(za, zb, 1), m.integ(za, zb, 2), T_ps, &c);
+        c.pre = std::exp(-m.gamma * (zb - za) + (double)m.amps(za, zb) * m.z_a * m.gamma);
+        c.post = 1.0;
+        return c;
+    };
+    // time data -> (transpose) -> forward row pass; the column pass of every
+    // step finishes the forward transform, applies the linear step and starts
+    // the inverse transform.
+    MPA_TRY(transpose_launch<T>(f, w, s.N1, s.N2, st));
+    KRParams<T> r{w, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
+    MPA_TRY(kr_launch<T>(KR_FWD, s.logN1, r, st));
+    KCParams<T> c{};
+    c.src = w;
+    c.dst = w;
+    c.N = s.N;
+    c.logN = s.logN;
+    c.N1 = (int)s.N1;
+    c.logN1 = s.logN1;
+    c.ncols = s.N1;
+    c.flow = flow(z_from, z_from + 0.5 * dz);
+    MPA_TRY(kc_launch<T>(KC_SS_STEP, s.logN2, c, st));
+    for (long k = 0; k < K; ++k) {
+        const double zk = z_from + dz * (double)k;
+        r.rot = (T)m.integ(zk, zk + dz, 3);
+        MPA_TRY(kr_launch<T>(KR_SS, s.logN1, r, st));
+        const double za = zk + 0.5 * dz;
+        const double zb = (k == K - 1) ? z_to : za + dz;
+        c.flow = flow(za, zb);
+        MPA_TRY(kc_launch<T>(KC_SS_STEP, s.logN2, c, st));
+    }
+    KRParams<T> ri{w, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
+    MPA_TRY(kr_launch<T>(KR_INV, s.logN1, ri, st));
+    MPA_TRY(transpose_launch<T>(w, f, s.N2, s.N1, st));
+    return MPA_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_plan** out) {
+    if (!map || !prm || !out) return MPA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (prm->precision != MPA_FP32 && prm->precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+    if (!(prm->T_ps > 0.0) || !(prm->L_km > 0.0) || prm->M < 1 || prm->n_iter < 1) return MPA_ERR_INVALID_ARG;
+    mpa_plan* p = new (std::nothrow) mpa_plan();
+    if (!p) return MPA_ERR_INVALID_ARG;
+    int rc = p->map.init(map);
+    if (rc == MPA_OK) rc = split_n(prm->N, prm->precision, &p->sp);
+    if (rc != MPA_OK) {
+        delete p;
+        return rc;
+    }
+    p->T = prm->T_ps;
+    p->L = prm->L_km;
+    p->M = prm->M;
+    p->n_iter = prm->n_iter;
+    p->prec = prm->precision;
+    double r;
+    if (whole(p->map.period / p->L, &r) && r >= 1) p->n_types = (int)r;
+    else if (whole(p->L / p->map.period, &r) && r >= 1) p->n_types = 1;
+    else {
+        delete p;
+        return MPA_ERR_GRID;
+    }
+    // per-node constants of Eq. (6) for each interval start u0 = t L in the period
+    const int M = p->M;
+    const double dz = p->L / M;
+    p->nodes.resize((size_t)p->n_types * (M + 1));
+    for (int t = 0; t < p->n_types; ++t) {
+        const double u0 = p->L * t;
+        for (int j = 0; j <= M; ++j) {
+            const double zr = (j == M) ? p->L : dz * j;
+            NodeC& c = p->nodes[(size_t)t * (M + 1) + j];
+            phase_consts(p->map.integ(u0, u0 + zr, 1), p->map.integ(u0, u0 + zr, 2), p->T, &c);
+            c.pre = std::exp(-p->map.gamma * zr);
+            double sig;
+            if (j == 0) sig = p->map.side(u0, 3, +1);
+            else if (j == M) sig = p->map.side(u0 + zr, 3, -1);
+            else sig = 0.5 * (p->map.side(u0 + zr, 3, -1) + p->map.side(u0 + zr, 3, +1));
+            c.post = sig * dz / c.pre;
+        }
+    }
+    p->csize = p->prec == MPA_FP32 ? sizeof(float2) : sizeof(double2);
+    const size_t N = (size_t)p->sp.N;
+    p->off_psi = 0;
+    p->off_state = align256(p->off_psi + (size_t)(M + 1) * N * p->csize);
+    p->off_psi0c = align256(p->off_state + N * sizeof(double2));
+    const size_t psi0c_bytes = p->prec == MPA_FP32 ? N * sizeof(float2) : 0;
+    if (p->prec == MPA_FP64) p->off_psi0c = p->off_state;  // the FP64 state is its own working copy
+    const size_t after_psi0c = p->prec == MPA_FP32 ? p->off_psi0c + psi0c_bytes : p->off_state + N * sizeof(double2);
+    p->off_nodes = align256(after_psi0c);
+    p->off_err = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
+    p->ws_need = align256(p->off_err + sizeof(unsigned int));
+    *out = p;
+    return MPA_OK;
+}
+
+int mpa_plan_workspace_size(const mpa_plan* p, size_t* bytes) {
+    if (!p || !bytes) return MPA_ERR_INVALID_ARG;
+    *bytes = p->ws_need;
+    return MPA_OK;
+}
+
+int mpa_plan_set_workspace(mpa_plan* p, void* ws, size_t bytes) {
+    if (!p || !ws) return MPA_ERR_INVALID_ARG;
+    if (bytes < p->ws_need || ((uintptr_t)ws & 255u) != 0) return MPA_ERR_WORKSPACE;
+    p->ws = reinterpret_cast<unsigned char*>(ws);
+    p->ws_bytes = bytes;
+    MPA_TRY(cudaMemcpy(p->ws + p->off_nodes, p->nodes.data(), p->nodes.size() * sizeof(NodeC),
+                       cudaMemcpyHostToDevice));
+    MPA_TRY(cudaMemset(p->ws + p->off_err, 0, sizeof(unsigned int)));
+    return MPA_OK;
+}
+
+int mpa_propagate(mpa_plan* p, void* field, double z_from_km, double z_to_km, mpa_stream stream) {
+    if (!p || !field) return MPA_ERR_INVALID_ARG;
+    if (!p->ws) return MPA_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return p->prec == MPA_FP32 ? propagate_t<float>(p, field, z_from_km, z_to_km, st)
+                               : propagate_t<double>(p, field, z_from_km, z_to_km, st);
+}
+
+int mpa_interval(mpa_plan* p, const void* psi0, void* psiM, double z0_km, mpa_stream stream) {
+    if (!p || !psi0 || !psiM) return MPA_ERR_INVALID_ARG;
+    if (!p->ws) return MPA_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return p->prec == MPA_FP32 ? interval_t<float>(p, psi0, psiM, z0_km, st)
+                               : interval_t<double>(p, psi0, psiM, z0_km, st);
+}
+
+int mpa_plan_status(mpa_plan* p, mpa_stream stream) {
+    if (!p) return MPA_ERR_INVALID_ARG;
+    if (!p->ws) return MPA_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned int h = 0;
+    MPA_TRY(cudaMemcpyAsync(&h, p->ws + p->off_err, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MPA_TRY(cudaStreamSynchronize(st));
+    MPA_TRY(cudaMemsetAsync(p->ws + p->off_err, 0, sizeof(unsigned int), st));
+    return h ? MPA_ERR_NONFINITE : MPA_OK;
+}
+
+void mpa_plan_destroy(mpa_plan* p) { delete p; }
+
+int ss_workspace_size(int64_t N, int32_t precision, size_t* bytes) {
+    if (!bytes || (precision != MPA_FP32 && precision != MPA_FP64)) return MPA_ERR_INVALID_ARG;
+    Split s;
+    int rc = split_n(N, precision, &s);
+    if (rc) return rc;
+    *bytes = align256((size_t)N * (precision == MPA_FP32 ? sizeof(float2) : sizeof(double2)));
+    return MPA_OK;
+}
+
+int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision, void* field,
+                 double z_from_km, double z_to_km, void* workspace, size_t ws_bytes, mpa_stream stream) {
+    if (!map || !field || !workspace || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
+    if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+    HostMap m;
+    int rc = m.init(map);
+    if (rc) return rc;
+    Split s;
+    rc = split_n(N, precision, &s);
+    if (rc) return rc;
+    size_t need = 0;
+    ss_workspace_size(N, precision, &need);
+    if (ws_bytes < need) return MPA_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return precision == MPA_FP32 ? ss_t<float>(m, s, T_ps, dz_km, field, z_from_km, z_to_km, workspace, st)
+                                 : ss_t<double>(m, s, T_ps, dz_km, field, z_from_km, z_to_km, workspace, st);
+}
+
+int mpa_fft(int64_t N, int32_t precision, int32_t sign, void* data, void* workspace, size_t ws_bytes,
+            mpa_stream stream) {
+    if (!data || !workspace || (sign != 1 && sign != -1)) return MPA_ERR_INVALID_ARG;
+    if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+    Split s;
+    int rc = split_n(N, precision, &s);
+    if (rc) return rc;
+    size_t need = 0;
+    ss_workspace_size(N, precision, &need);
+    if (ws_bytes < need) return MPA_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)N * (precision == MPA_FP32 ? sizeof(float2) : sizeof(double2));
+    if (precision == MPA_FP32) {
+        float2* d = reinterpret_cast<float2*>(data);
+        float2* w = reinterpret_cast<float2*>(workspace);
+        rc = sign > 0 ? fft_forward<float>(s, d, w, st) : fft_inverse<float>(s, d, w, st);
+    } else {
+        double2* d = reinterpret_cast<double2*>(data);
+        double2* w = reinterpret_cast<double2*>(workspace);
+        rc = sign > 0 ? fft_forward<double>(s, d, w, st) : fft_inverse<double>(s, d, w, st);
+    }
+    if (rc) return rc;
+    MPA_TRY(cudaMemcpyAsync(data, workspace, bytes, cudaMemcpyDeviceToDevice, st));
+    return MPA_OK;
+}
+
+const char* mpa_status_string(int status) {
+    switch (status) {
+        case MPA_OK: return "ok";
+        case MPA_ERR_INVALID_ARG: return "invalid argument";
+        case MPA_ERR_UNSUPPORTED_N: return "unsupported N (power of two in [2^8, 2^25], 2^24 for FP64)";
+        case MPA_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case MPA_ERR_CUDA: return "CUDA error";
+        case MPA_ERR_GRID: return "z-grid inconsistent with the fiber map";
+        case MPA_ERR_NONFINITE: return "non-finite value produced";
+    }
+    return "unknown status";
+}
+
+const char* mpa_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int64_t mpa_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"

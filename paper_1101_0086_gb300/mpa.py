@@ -1,0 +1,217 @@
+"""Thin ctypes binding of ``libmpa.so`` (the C ABI declared in ``include/mpa.h``).
+
+Argument marshalling only: every step of the MPA and split-step paths runs in
+the library's CUDA kernels.  PyTorch provides device memory (tensors whose
+``data_ptr()`` is passed through) and the stream.  There is no CPU fallback:
+if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libmpa.so")
+_lib: Optional[ctypes.CDLL] = None
+
+FP32, FP64 = 0, 1
+_STATUS_NONFINITE = 6
+
+
+class MPAError(RuntimeError):
+    pass
+
+
+class _Segment(ctypes.Structure):
+    _fields_ = [("length_km", ctypes.c_double), ("beta2_ps2_per_km", ctypes.c_double),
+                ("beta3_ps3_per_km", ctypes.c_double), ("sigma_per_W_km", ctypes.c_double)]
+
+
+class _FiberMap(ctypes.Structure):
+    _fields_ = [("segments", ctypes.POINTER(_Segment)), ("n_segments", ctypes.c_int32),
+                ("gamma_per_km", ctypes.c_double), ("z_a_km", ctypes.c_double), ("n_periods", ctypes.c_int32)]
+
+
+class _PlanParams(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("T_ps", ctypes.c_double), ("L_km", ctypes.c_double),
+                ("M", ctypes.c_int32), ("n_iter", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
+           "mpa_interval", "mpa_plan_status", "mpa_plan_destroy", "ss_workspace_size", "ss_propagate",
+           "mpa_fft", "mpa_status_string", "mpa_last_cuda_error", "mpa_kernel_launches")
+
+
+def library_path() -> str:
+    return _SO
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libmpa.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise MPAError(f"{_SO} is missing: build it with paper_1101_0086_gb300.build.build()")
+        L = ctypes.CDLL(_SO)
+        vp, i32, i64, dbl, szp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_size_t)
+        L.mpa_plan_create.argtypes = [ctypes.POINTER(_FiberMap), ctypes.POINTER(_PlanParams), ctypes.POINTER(vp)]
+        L.mpa_plan_workspace_size.argtypes = [vp, szp]
+        L.mpa_plan_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+        L.mpa_propagate.argtypes = [vp, vp, dbl, dbl, vp]
+        L.mpa_interval.argtypes = [vp, vp, vp, dbl, vp]
+        L.mpa_plan_status.argtypes = [vp, vp]
+        L.mpa_plan_destroy.argtypes = [vp]
+        L.mpa_plan_destroy.restype = None
+        L.ss_workspace_size.argtypes = [i64, i32, szp]
+        L.ss_propagate.argtypes = [ctypes.POINTER(_FiberMap), i64, dbl, dbl, i32, vp, dbl, dbl, vp, ctypes.c_size_t, vp]
+        L.mpa_fft.argtypes = [i64, i32, i32, vp, vp, ctypes.c_size_t, vp]
+        L.mpa_status_string.argtypes = [ctypes.c_int]
+        L.mpa_status_string.restype = ctypes.c_char_p
+        L.mpa_last_cuda_error.restype = ctypes.c_char_p
+        L.mpa_kernel_launches.restype = i64
+        for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
+                  "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        L = lib()
+        msg = L.mpa_status_string(rc).decode()
+        if rc == 4:
+            msg += ": " + L.mpa_last_cuda_error().decode()
+        raise MPAError(f"{what}: {msg} (status {rc})")
+
+
+def _prec(precision) -> int:
+    if precision in (FP32, "fp32", "f32", torch.complex64):
+        return FP32
+    if precision in (FP64, "fp64", "f64", torch.complex128):
+        return FP64
+    raise ValueError(f"unknown precision {precision!r}")
+
+
+def _cdtype(prec: int) -> torch.dtype:
+    return torch.complex64 if prec == FP32 else torch.complex128
+
+
+def _fiber_struct(fiber):
+    rows = fiber.as_rows()
+    segs = (_Segment * len(rows))(*[_Segment(*map(float, r)) for r in rows])
+    fm = _FiberMap(ctypes.cast(segs, ctypes.POINTER(_Segment)), len(rows), float(fiber.gamma_per_km),
+                   float(fiber.z_a_km), int(fiber.n_periods))
+    return fm, segs  # keep segs alive with fm
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _field_ptr(t: torch.Tensor, dtype: torch.dtype, n: int, what: str) -> ctypes.c_void_p:
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{what}: expected a contiguous CUDA {dtype} tensor of {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """An MPA plan (``mpa_plan_create``) with its caller-owned workspace."""
+
+    def __init__(self, fiber, N: int, T_ps: float, L_km: float, M: int, n_iter: int,
+                 precision="fp32", device="cuda", workspace: Optional[torch.Tensor] = None):
+        L = lib()
+        self.prec = _prec(precision)
+        self.N = int(N)
+        self.dtype = _cdtype(self.prec)
+        self._fm, self._segs = _fiber_struct(fiber)
+        prm = _PlanParams(self.N, float(T_ps), float(L_km), int(M), int(n_iter), self.prec)
+        h = ctypes.c_void_p()
+        _check(L.mpa_plan_create(ctypes.byref(self._fm), ctypes.byref(prm), ctypes.byref(h)), "mpa_plan_create")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        _check(L.mpa_plan_workspace_size(h, ctypes.byref(nbytes)), "mpa_plan_workspace_size")
+        self.workspace_bytes = int(nbytes.value)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+        self.workspace = workspace
+        _check(L.mpa_plan_set_workspace(h, ctypes.c_void_p(workspace.data_ptr()), workspace.numel()),
+               "mpa_plan_set_workspace")
+
+    def propagate(self, field: torch.Tensor, z_from_km: float, z_to_km: float, stream=None) -> torch.Tensor:
+        """In-place MPA propagation of the time-domain field (``mpa_propagate``)."""
+        ptr = _field_ptr(field, self.dtype, self.N, "propagate")
+        _check(lib().mpa_propagate(self._h, ptr, float(z_from_km), float(z_to_km), _stream(stream)), "mpa_propagate")
+        return field
+
+    def interval(self, psi0: torch.Tensor, z0_km: float, stream=None) -> torch.Tensor:
+        """psi^{(n_iter)} at the last node of one interval (``mpa_interval``)."""
+        p0 = _field_ptr(psi0, torch.complex128, self.N, "interval")
+        out = torch.empty_like(psi0)
+        _check(lib().mpa_interval(self._h, p0, ctypes.c_void_p(out.data_ptr()), float(z0_km), _stream(stream)),
+               "mpa_interval")
+        return out
+
+    def status(self, stream=None) -> bool:
+        """False if a NaN/Inf was produced since the last call (synchronises)."""
+        rc = lib().mpa_plan_status(self._h, _stream(stream))
+        if rc == _STATUS_NONFINITE:
+            return False
+        _check(rc, "mpa_plan_status")
+        return True
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().mpa_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ss_workspace_bytes(N: int, precision="fp32") -> int:
+    n = ctypes.c_size_t()
+    _check(lib().ss_workspace_size(int(N), _prec(precision), ctypes.byref(n)), "ss_workspace_size")
+    return int(n.value)
+
+
+def ss_propagate(field: torch.Tensor, fiber, T_ps: float, dz_km: float, z_from_km: float, z_to_km: float,
+                 workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """In-place split-step propagation of Eq. (4) (``ss_propagate``); precision from the dtype."""
+    prec = _prec(field.dtype)
+    N = field.numel()
+    ptr = _field_ptr(field, _cdtype(prec), N, "ss_propagate")
+    need = ss_workspace_bytes(N, prec)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=field.device)
+    fm, segs = _fiber_struct(fiber)
+    _check(lib().ss_propagate(ctypes.byref(fm), N, float(T_ps), float(dz_km), prec, ptr, float(z_from_km),
+                              float(z_to_km), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                              _stream(stream)), "ss_propagate")
+    return field
+
+
+def fft(data: torch.Tensor, sign: int, workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """In-place transform in the paper's convention (``mpa_fft``): +1 = F, -1 = F^-1 (1/N)."""
+    prec = _prec(data.dtype)
+    N = data.numel()
+    ptr = _field_ptr(data, _cdtype(prec), N, "fft")
+    need = ss_workspace_bytes(N, prec)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=data.device)
+    _check(lib().mpa_fft(N, prec, int(sign), ptr, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                         _stream(stream)), "mpa_fft")
+    return data
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched since it was loaded."""
+    return int(lib().mpa_kernel_launches())

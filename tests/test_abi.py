@@ -1,0 +1,97 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/mpa.h; host-only argument and grid validation."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1101_0086_gb300 import build as B
+from paper_1101_0086_gb300 import mpa
+from paper_1101_0086_gb300.workloads import FiberMap, Segment, dm_map
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return mpa.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "mpa.h")).read()
+    return sorted(set(re.findall(r"MPA_API\s+[\w\s\*]+?\b((?:mpa|ss)_\w+)\s*\(", txt)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
+              "ss_propagate", "mpa_plan_destroy", "mpa_status_string"):
+        assert n in names
+    assert set(names) == set(mpa.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for n in declared_functions():
+        assert hasattr(L, n), n
+    out = os.popen(f"nm -D --defined-only {mpa.library_path()}").read()
+    exported = set(re.findall(r" T (\w+)", out))
+    assert set(declared_functions()) <= exported
+    # nothing but the C ABI is exported
+    assert {s for s in exported if not s.startswith(("mpa_", "ss_"))} == set()
+
+
+def test_status_strings(L):
+    for s in range(0, 7):
+        assert L.mpa_status_string(s)
+    assert L.mpa_status_string(99) == b"unknown status"
+
+
+def _plan(L, fiber, N, T, Lkm, M, n, prec=0):
+    fm, segs = mpa._fiber_struct(fiber)
+    prm = mpa._PlanParams(N, T, Lkm, M, n, prec)
+    h = ctypes.c_void_p()
+    rc = L.mpa_plan_create(ctypes.byref(fm), ctypes.byref(prm), ctypes.byref(h))
+    return rc, h
+
+
+def test_plan_validation_is_host_only(L):
+    fib = dm_map(4)
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 710, 3)
+    assert rc == 0
+    n = ctypes.c_size_t()
+    assert L.mpa_plan_workspace_size(h, ctypes.byref(n)) == 0
+    # (M+1) node spectra of complex64 + FP64 state + complex64 copy + tables
+    assert n.value >= 711 * (1 << 14) * 8 + (1 << 14) * 24
+    # propagate without workspace is refused before any CUDA call
+    assert L.mpa_propagate(h, ctypes.c_void_p(16), 0.0, 50.0, None) == 3
+    L.mpa_plan_destroy(h)
+    assert _plan(L, fib, 3000, 12800.0, 50.0, 710, 3)[0] == 2      # N not a power of two
+    assert _plan(L, fib, 1 << 26, 12800.0, 50.0, 710, 3)[0] == 2   # too large
+    assert _plan(L, fib, 1 << 25, 12800.0, 50.0, 7, 3, 1)[0] == 2  # FP64 limit 2^24
+    assert _plan(L, fib, 1 << 14, 12800.0, 7.0, 10, 3)[0] == 5     # L neither divides nor is a multiple of 50 km
+    assert _plan(L, fib, 1 << 14, -1.0, 50.0, 10, 3)[0] == 1
+    assert _plan(L, fib, 1 << 14, 12800.0, 50.0, 0, 3)[0] == 1
+    assert _plan(L, fib, 1 << 14, 12800.0, 50.0, 10, 0)[0] == 1
+    assert _plan(L, fib, 1 << 14, 12800.0, 50.0, 10, 3, 7)[0] == 1
+    bad = FiberMap((Segment(-1.0, 0.0, 0.0, 0.0),), 0.0, 0.0, 1)
+    assert _plan(L, bad, 1 << 14, 12800.0, 50.0, 10, 3)[0] == 1
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 100.0, 10, 3)  # L a multiple of the period
+    assert rc == 0
+    L.mpa_plan_destroy(h)
+
+
+def test_ss_workspace_size(L):
+    n = ctypes.c_size_t()
+    assert L.ss_workspace_size(1 << 20, 0, ctypes.byref(n)) == 0 and n.value == (1 << 20) * 8
+    assert L.ss_workspace_size(1 << 20, 1, ctypes.byref(n)) == 0 and n.value == (1 << 20) * 16
+    assert L.ss_workspace_size(100, 0, ctypes.byref(n)) == 2
+    assert L.ss_workspace_size(1 << 20, 5, ctypes.byref(n)) == 1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(mpa, "_SO", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(mpa, "_lib", None)
+    with pytest.raises(mpa.MPAError):
+        mpa.lib()

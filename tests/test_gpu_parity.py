@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 CPU
+oracle on the same seeded inputs.  Tolerances (relative L2): 1e-10 for FP64
+runs and 1e-4 for FP32 runs against the same algorithm's FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_0086_gb300.workloads import (FiberMap, Segment, chirped_gaussian, dm_map, random_field, wdm_field,
+                                             workload)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    from paper_1101_0086_gb300 import build as B
+    from paper_1101_0086_gb300 import mpa
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    B.build()
+    mpa.lib()
+    return mpa
+
+
+def dev(x, prec):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex64 if prec == "fp32" else np.complex128)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+# ------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("logn", [8, 9, 12, 13, 14, 17, 20])
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_fft_matches_oracle(M, prec, logn, sign):
+    N = 1 << logn
+    x = random_field(N, seed=logn)
+    ref = oracle.fft(x, sign)
+    got = host(M.fft(dev(x, prec), sign))
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert oracle.rel_l2(got, ref) < tol
+
+
+# ------------------------------------------------------------- intervals
+def small_map(sigma=1.3, gamma_db=0.2):
+    # two segments with a dispersion jump, beta3 and loss; period 10 km
+    from paper_1101_0086_gb300.workloads import gamma_from_db_per_km
+    return FiberMap((Segment(8.0, -21.7, 0.1, sigma), Segment(2.0, 85.0, 0.1, sigma)),
+                    gamma_from_db_per_km(gamma_db), 10.0, 10)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("N,Lk,Mn,n_iter,z0", [
+    (1 << 10, 10.0, 20, 3, 0.0),      # one interval = one DM period (node on the 8 km jump)
+    (1 << 12, 2.0, 36, 3, 8.0),       # ragged node batch, interval in the +85 segment
+    (1 << 12, 5.0, 1, 1, 5.0),        # degenerate: M = 1, one iteration
+    (1 << 14, 10.0, 50, 4, 20.0),     # several tiles per node, interval type 0 of period 3
+])
+def test_interval_matches_oracle(M, prec, N, Lk, Mn, n_iter, z0):
+    fib = small_map()
+    T = 800.0 * N / 1024
+    A0 = wdm_field(N, T, 2, 50.0, 8 * N // 1024, 30.0, 20.0, "qpsk", seed=N + Mn)
+    psi0 = oracle.fft(A0, +1)
+    ref = oracle.mpa_interval(psi0, fib, T, z0, Lk, Mn, n_iter)
+    plan = M.Plan(fib, N, T, Lk, Mn, n_iter, precision=prec)
+    got = host(plan.interval(dev(psi0, "fp64"), z0))
+    err = oracle.rel_l2(got, ref)
+    assert err < TOL[prec], err
+    # the nonlinear correction is what the kernels compute: compare it too
+    dref = ref - psi0
+    assert oracle.rel_l2(got - psi0, dref) < (1e-9 if prec == "fp64" else 3e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_propagate_matches_oracle_across_amplifiers(M, prec):
+    fib = small_map()
+    N, T = 1 << 12, 3200.0
+    A0 = wdm_field(N, T, 3, 50.0, 32, 30.0, 10.0, "qpsk", seed=5)
+    ref = oracle.mpa(A0, fib, T, 0.0, 30.0, 2.0, 24, 3)
+    plan = M.Plan(fib, N, T, 2.0, 24, 3, precision=prec)
+    got = host(plan.propagate(dev(A0, prec), 0.0, 30.0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+    assert plan.status()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_linear_limit_is_exact(M, prec):
+    # sigma = 0: psi is constant (text after Eq. (2)); the result is the exact
+    # linear flow, computed here with numpy's FFT
+    fib = small_map(sigma=0.0)
+    N, T = 1 << 13, 6400.0
+    A0 = chirped_gaussian(N, T, 15.0, 1.0, chirp=0.3)
+    plan = M.Plan(fib, N, T, 10.0, 4, 2, precision=prec)
+    got = host(plan.propagate(dev(A0, prec), 0.0, 50.0))
+    w = 2 * np.pi * np.fft.fftfreq(N, d=T / N)
+    I2 = 5 * (8.0 * -21.7 + 2.0 * 85.0)
+    I3 = 50.0 * 0.1
+    g = fib.gamma_per_km
+    X = np.fft.ifft(A0) * N * np.exp(1j * (0.5 * w**2 * I2 + w**3 * I3 / 6)) * math.exp(-g * 50 + 5 * 10 * g)
+    ref = np.fft.fft(X) / N
+    assert oracle.rel_l2(got, ref) < (1e-12 if prec == "fp64" else 5e-6)
+
+
+def test_grid_errors_are_reported(M):
+    fib = small_map()
+    plan = M.Plan(fib, 1 << 10, 800.0, 2.0, 4, 2, precision="fp32")
+    f = dev(np.zeros(1 << 10), "fp32")
+    for z0, z1 in ((1.0, 5.0), (0.0, 3.0), (0.0, 200.0)):
+        with pytest.raises(M.MPAError):
+            plan.propagate(f, z0, z1)
+    with pytest.raises(ValueError):
+        plan.propagate(dev(np.zeros(1 << 10), "fp64"), 0.0, 2.0)
+
+
+# ------------------------------------------------------------ split-step
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("logn", [10, 14])
+def test_split_step_matches_oracle(M, prec, logn):
+    fib = small_map()
+    N = 1 << logn
+    T = 800.0 * N / 1024
+    A0 = wdm_field(N, T, 2, 50.0, 8 * N // 1024, 30.0, 20.0, "qpsk", seed=logn)
+    ref = oracle.ss(A0, fib, T, 0.0, 20.0, 0.1)
+    got = host(M.ss_propagate(dev(A0, prec), fib, T, 0.1, 0.0, 20.0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+
+
+# ------------------------------------------------- benchmark workloads
+def test_small_workload_full_length_fp64(M):
+    """The N = 2^14, 4-channel, 200 km link at full size: FP64 MPA (L = one
+    span, M = 710, n = 3) and FP64 split-step (dz = 0.1 km) against the oracle."""
+    w = workload("0")
+    A0 = w.field()
+    ref = oracle.mpa(A0, w.fiber, w.T_ps, 0.0, w.length_km, w.mpa_L_km, w.mpa_M, w.mpa_n_iter)
+    plan = M.Plan(w.fiber, w.N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp64")
+    got = host(plan.propagate(dev(A0, "fp64"), 0.0, w.length_km))
+    assert oracle.rel_l2(got, ref) < TOL["fp64"]
+    ref_ss = oracle.ss(A0, w.fiber, w.T_ps, 0.0, w.length_km, w.ss_dz_km)
+    got_ss = host(M.ss_propagate(dev(A0, "fp64"), w.fiber, w.T_ps, w.ss_dz_km, 0.0, w.length_km))
+    assert oracle.rel_l2(got_ss, ref_ss) < TOL["fp64"]
+
+
+def test_small_workload_fp32(M):
+    w = workload("0")
+    A0 = w.field()
+    ref = oracle.mpa(A0, w.fiber, w.T_ps, 0.0, 100.0, w.mpa_L_km, w.mpa_M, w.mpa_n_iter)
+    plan = M.Plan(w.fiber, w.N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32")
+    got = host(plan.propagate(dev(A0, "fp32"), 0.0, 100.0))
+    assert oracle.rel_l2(got, ref) < TOL["fp32"]
+
+
+def test_bench_workload_sampled_interval_fp32(M):
+    """The N = 2^20, 16-channel workload in the benchmark's launch
+    configuration (L = 5 km, M = 142, n = 3): one full interval against the
+    oracle, starting from the seeded field's spectrum at z = 45 km."""
+    w = workload("1")
+    A0 = w.field()
+    psi0 = oracle.fft(A0, +1)
+    z0 = 45.0
+    ref = oracle.mpa_interval(psi0, w.fiber, w.T_ps, z0, w.mpa_L_km, w.mpa_M, w.mpa_n_iter)
+    plan = M.Plan(w.fiber, w.N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32")
+    got = host(plan.interval(dev(psi0, "fp64"), z0))
+    assert oracle.rel_l2(got, ref) < TOL["fp32"]
