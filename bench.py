@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the MPA large-z step on one GB300, in Fourier modes x km per
+second, on the seeded 16-channel QPSK DM link with N = 2^20 modes over
+40 spans (2000 km): FP32 MPA (FP64 state, exact phase, Kahan-compensated
+trapezoid sums), L = 5 km intervals, M = 142, n_tot = 3.
+
+One step = one full 2000-km propagation of the link (every row of the hot
+path: phase, inverse FFT, |A|^2 A, forward FFT, weighting, quadrature,
+reconstruction, for all 400 intervals).  The split-step method of Eq. (4) on
+the same GPU (FP64 and FP32, dz = 0.05 km) is timed on a bounded stretch as
+the comparator, and the FP64 CPU oracle on a bounded sample as the CPU
+baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mpa|reference]
+
+Under torchrun (N > 1) every rank propagates its own copy of the link
+(independent replicas, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mode*km/s on 1 GB300, MPA vs SS on same GPU, at rel-L2 <=1e-4 vs FP64 oracle"
+UNIT = "mode*km/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpa", choices=["mpa", "reference"])
+    ap.add_argument("--workload", default="1")
+    ap.add_argument("--km", type=float, default=None, help="propagate this many km per step (default: whole link)")
+    ap.add_argument("--ss-km", type=float, default=25.0, help="km of split-step timed as the comparator")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, split-step and CPU legs (profiling runs)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- helpers
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1101_0086_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    with open(os.path.join(ROOT, "include", "mpa.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash() or e.get("workload") != workload:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle on the host cores: each step is one 5-km interval of
+    the same link (M = 142, n_tot = 3) at N = 2^20."""
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1101_0086_gb300.workloads import workload
+    w = workload(args.workload)
+    psi0 = oracle.fft(w.field(), +1)
+    times, used = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.mpa_interval(psi0, w.fiber, w.T_ps, 0.0, w.mpa_L_km, w.mpa_M, w.mpa_n_iter)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    used = os.cpu_count() or 1
+    t = sum(times) / len(times)
+    value = w.N * w.mpa_L_km / t
+    sample = (f"one {w.mpa_L_km:g}-km MPA interval (M={w.mpa_M}, n_tot={w.mpa_n_iter}) of {w.name}, "
+              f"FP64, OpenMP over z-nodes")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "km_per_step": w.mpa_L_km, "L_km": w.mpa_L_km, "M": w.mpa_M,
+                       "n_iter": w.mpa_n_iter, "method": "MPA (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_mpa(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1101_0086_gb300 import build as B
+    from paper_1101_0086_gb300 import mpa
+    from paper_1101_0086_gb300.workloads import workload
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    mpa.lib()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = workload(args.workload)
+    km = w.length_km if args.km is None else float(args.km)
+    N = w.N
+    A0 = w.field()
+    src = torch.from_numpy(A0.astype(np.complex64)).cuda()
+    f = torch.empty_like(src)
+    plan = mpa.Plan(w.fiber, N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step():
+        f.copy_(src)
+        plan.propagate(f, 0.0, km, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(torch.cuda.current_device())
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    mpa.profile(True)
+    l0 = mpa.kernel_launches()
+    for s, e in evs:
+        flush.zero_()
+        s.record(stream)
+        step()
+        e.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = mpa.kernel_launches() - l0
+    prof = mpa.profile_read()
+    mpa.profile(False)
+    ck = clocks.stop()
+    t = sum(s.elapsed_time(e) for s, e in evs) / 1e3
+    tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_max = float(tt.item())
+    value = world * N * km * args.steps / t_max
+    ok = plan.status(stream)
+
+    # ---- dominant kernel roofline (CUDA events around each launch, same region)
+    peak, peak_src = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n, dom_bytes) = dom
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    kern = {k: {"ms_total": round(v[0], 3), "launches": v[1], "share": round(v[0] / sum(x[0] for x in prof.values()), 4),
+                "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1)} for k, v in prof.items()}
+    traffic = ncu_traffic(dom_name, w.name)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom_name,
+                "algorithmic_bytes_per_launch": dom_bytes / dom_n, "peak_source": peak_src}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "N": N, "km_per_step": km, "channels": w.n_channels,
+                       "symbols_per_channel": w.n_symbols, "L_km": w.mpa_L_km, "M": w.mpa_M,
+                       "n_iter": w.mpa_n_iter, "method": "MPA FP32 (FP64 state)",
+                       "l2": "flushed between steps (256 MB write outside the events)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": roofline, "kernels": kern, "clocks": ck, "gpu_launches": launches,
+            "finite": ok}
+
+    if not args.no_extras:
+        # ---- end to end through the public API: pinned host in, host out
+        h_in = torch.from_numpy(A0.astype(np.complex64)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es.record(stream)
+        for _ in range(args.steps):
+            f.copy_(h_in, non_blocking=True)
+            plan.propagate(f, 0.0, km, stream)
+            h_out.copy_(f, non_blocking=True)
+        ee.record(stream)
+        torch.cuda.synchronize()
+        te = torch.tensor([es.elapsed_time(ee) / 1e3], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * N * km * args.steps / float(te.item()), "unit": UNIT,
+                       "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
+                       "d2h_bytes_per_step": h_out.numel() * h_out.element_size()}
+
+        # ---- split-step comparator on the same GPU (bounded stretch)
+        ss = {}
+        for prec, dt in (("fp64", torch.complex128), ("fp32", torch.complex64)):
+            g0 = torch.from_numpy(A0).to(dt).cuda()
+            g = torch.empty_like(g0)
+            ws = torch.empty(mpa.ss_workspace_bytes(N, prec), dtype=torch.uint8, device="cuda")
+            g.copy_(g0)
+            mpa.ss_propagate(g, w.fiber, w.T_ps, w.ss_dz_km, 0.0, w.ss_dz_km * 20, ws, stream)
+            torch.cuda.synchronize()
+            g.copy_(g0)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            mpa.ss_propagate(g, w.fiber, w.T_ps, w.ss_dz_km, 0.0, args.ss_km, ws, stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            ts = s.elapsed_time(e) / 1e3
+            ss[f"ss_{prec}"] = {"value": N * args.ss_km / ts, "unit": UNIT, "km_timed": args.ss_km,
+                                "dz_km": w.ss_dz_km}
+        line["comparator"] = ss
+        line["mpa_over_ss_fp64"] = value / world / ss["ss_fp64"]["value"]
+
+        # ---- CPU oracle baseline + full-size parity sample (rank 0, N = 1)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            import oracle
+            psi0 = oracle.fft(A0, +1)
+            t0 = time.perf_counter()
+            ref, used = None, os.cpu_count() or 1
+            ref = oracle.mpa_interval(psi0, w.fiber, w.T_ps, 0.0, w.mpa_L_km, w.mpa_M, w.mpa_n_iter)
+            tc = time.perf_counter() - t0
+            got = plan.interval(torch.from_numpy(psi0).cuda(), 0.0, stream)
+            torch.cuda.synchronize()
+            err = oracle.rel_l2(got.cpu().numpy(), ref)
+            line["cpu_baseline"] = {"value": N * w.mpa_L_km / tc, "unit": UNIT, "cores": used, "kind": "oracle",
+                                    "sample": f"one {w.mpa_L_km:g}-km interval (M={w.mpa_M}, n_tot={w.mpa_n_iter}) "
+                                              f"of {w.name} in FP64, OpenMP over z-nodes, {tc:.1f} s"}
+            line["parity"] = {"rel_l2_vs_oracle": err, "sample": "psi at the last node of the first 5-km interval",
+                              "tolerance": 1e-4}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_mpa(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -149,6 +149,17 @@ MPA_API const char* mpa_last_cuda_error(void);
 /* Number of this library's kernels launched since load (all threads). */
 MPA_API int64_t mpa_kernel_launches(void);
 
+/* Launch timing (tooling): with enable != 0 every subsequent launch of a
+ * column pass, row pass or scan is bracketed by CUDA events on its stream
+ * (totals reset); mpa_profile_read synchronises on the recorded events and
+ * returns, for kernel kind `kind` (0 .. mpa_profile_kind_name() == NULL),
+ * the summed device time in ms, the number of launches and the summed
+ * algorithmic bytes (each element a launch must read or write, counted
+ * once). */
+MPA_API void mpa_profile(int enable);
+MPA_API int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* bytes);
+MPA_API const char* mpa_profile_kind_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -256,15 +256,94 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
     __syncthreads();
 }
 
-// Full transform: radix-RMAX passes, the last one of radix L/NS.
-template <typename T, int L, int G, int NT, int RMAX, int NS, int S, int LAYOUT, int PSH>
-__device__ __forceinline__ void stockham(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
-    if constexpr (NS < L) {
-        constexpr int R = (L / NS) < RMAX ? (L / NS) : RMAX;
-        stockham_pass<T, L, G, NT, R, NS, S, LAYOUT, PSH>(s, hi, lo);
-        stockham<T, L, G, NT, RMAX, NS * R, S, LAYOUT, PSH>(s, hi, lo);
+// Pass schedule of a length-L transform with radices RMAX and one smaller
+// radix 2^b when log2 L is not a multiple of log2 RMAX.  SMALL_FIRST puts
+// the small radix first (the transform then ends with an RMAX pass), else
+// last.  Two transforms meet in registers when the last radix of the first
+// equals the first radix of the second: the last pass leaves element
+// j + r L/R of butterfly j in v[r], which is exactly what a first pass of
+// the same radix reads.
+template <int L, int RMAX> struct Sched {
+    __host__ __device__ static constexpr int lg(int x) { return x <= 1 ? 0 : 1 + lg(x / 2); }
+    static constexpr int LOGL = lg(L), LOGR = lg(RMAX);
+    static constexpr int NFULL = LOGL / LOGR;
+    static constexpr int SMALL = 1 << (LOGL % LOGR);  // 1 if none
+    static constexpr int NP = NFULL + (SMALL > 1 ? 1 : 0);
+    template <bool SF> __host__ __device__ static constexpr int radix(int p) {
+        return SMALL == 1 ? RMAX : SF ? (p == 0 ? SMALL : RMAX) : (p == NP - 1 ? SMALL : RMAX);
+    }
+    template <bool SF> __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : ns<SF>(p - 1) * radix<SF>(p - 1); }
+};
+
+template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH, bool SF, int P, int NP>
+__device__ __forceinline__ void mid_passes(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
+    if constexpr (P < NP - 1) {
+        typedef Sched<L, RMAX> SC;
+        stockham_pass<T, L, G, NT, SC::template radix<SF>(P), SC::template ns<SF>(P), S, LAYOUT, PSH>(s, hi, lo);
+        mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, P + 1, NP>(s, hi, lo);
     }
 }
+
+// Butterfly b of a radix-R pass -> (j, g).
+template <int LAYOUT, int L, int G, int R> __device__ __forceinline__ void bmap(int b, int& j, int& g) {
+    if constexpr (LAYOUT == LAYOUT_COL) {
+        j = b / G;
+        g = b % G;
+    } else {
+        j = b % (L / R);
+        g = b / (L / R);
+    }
+}
+
+// A whole transform with register endpoints.  vin[q][r] holds input element
+// j + r L/R0 of butterfly b = tid + q NT (R0 = first radix), vout[q][r]
+// receives output element j + r L/RL (RL = last radix).  Shared memory is
+// used by the middle passes only; the transform ends with a barrier so the
+// caller may reuse `s`.
+template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH, bool SF> struct Xform {
+    typedef Sched<L, RMAX> SC;
+    typedef cx<T> C;
+    static constexpr int NP = SC::NP;
+    static constexpr int R0 = SC::template radix<SF>(0);
+    static constexpr int RL = SC::template radix<SF>(NP - 1);
+    static constexpr int Q0 = (L / R0) * G / NT;
+    static constexpr int QL = (L / RL) * G / NT;
+    static_assert((L / R0) * G % NT == 0 && (L / RL) * G % NT == 0, "butterflies must divide among threads");
+
+    static __device__ __forceinline__ void run(C (&vin)[Q0][R0], C (&vout)[QL][RL], C* s, const C* hi, const C* lo) {
+        if constexpr (NP == 1) {
+#pragma unroll
+            for (int q = 0; q < Q0; ++q) {
+                Dft<R0, S, C>::run(vin[q]);
+#pragma unroll
+                for (int r = 0; r < R0; ++r) vout[q][r] = vin[q][r];
+            }
+        } else {
+            // first pass: DFT of the register inputs (NS = 1), scatter to j R0 + r
+#pragma unroll
+            for (int q = 0; q < Q0; ++q) {
+                int j, g;
+                bmap<LAYOUT, L, G, R0>(threadIdx.x + q * NT, j, g);
+                Dft<R0, S, C>::run(vin[q]);
+#pragma unroll
+                for (int r = 0; r < R0; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(j * R0 + r, g))] = vin[q][r];
+            }
+            __syncthreads();
+            mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, 1, NP>(s, hi, lo);
+            // last pass (NS = L/RL, so k = j): gather j + r L/RL, twiddle W_L^{S r j}, DFT
+#pragma unroll
+            for (int q = 0; q < QL; ++q) {
+                int j, g;
+                bmap<LAYOUT, L, G, RL>(threadIdx.x + q * NT, j, g);
+#pragma unroll
+                for (int r = 0; r < RL; ++r) vout[q][r] = s[phys<PSH>(eidx<LAYOUT, L, G>(j + r * (L / RL), g))];
+                twiddle_row<T, L, RL, S>(vout[q], j, hi, lo);
+                Dft<RL, S, C>::run(vout[q]);
+            }
+            __syncthreads();
+        }
+    }
+};
 
 // Precision-dependent tiling: elements per thread E, largest radix, the
 // padding shift, the minimum column-tile width (64-byte row segments) and

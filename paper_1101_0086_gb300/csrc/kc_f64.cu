@@ -11,11 +11,22 @@ static cudaError_t kc_one(const KCParams<double>& p, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kc_kernel<double, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kc_kernel<double, L, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const long long nblk = (p.ncols + Gm::G - 1) / Gm::G;
     if (nblk <= 0) return cudaSuccess;
+    const bool prof = g_prof_on.load(std::memory_order_relaxed);
+    if (prof) prof_begin(st);
     kc_kernel<double, L, MODE><<<(unsigned)nblk, Gm::NT, Gm::smem_bytes, st>>>(p);
+    if (prof) {
+        // algorithmic bytes: every tile element read once and written once
+        // (a shared source, src_stride == 0, is read once for all nodes)
+        const double cs = (double)sizeof(cx<double>), tile = (double)p.ncols * L;
+        const double rd = p.src_stride == 0 ? (double)p.N1 * L : tile;
+        prof_end(prof_kc_kind(MODE), st, (rd + tile) * cs);
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -22,6 +22,8 @@
 //                     every frequency, fused with step 7 on the last iteration.
 #pragma once
 
+#include <type_traits>
+
 #include "device.cuh"
 
 namespace mpa {
@@ -82,107 +84,141 @@ template <typename T, int L> struct KRGeom {
 __device__ __forceinline__ long long signed_k(long long k, long long N) { return k < (N >> 1) ? k : k - N; }
 
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(KCGeom<T, L>::NT) kc_kernel(const KCParams<T> p) {
+__global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 : 1)
+    kc_kernel(const KCParams<T> p) {
     typedef cx<T> C;
     typedef KCGeom<T, L> Gm;
     typedef Tiling<T> P;
     constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
     constexpr bool FWD = (MODE == KC_MPA_POST || MODE == KC_SS_STEP || MODE == KC_FWD);
     constexpr bool INV = (MODE == KC_MPA_PRE || MODE == KC_SS_STEP || MODE == KC_INV);
+    // forward: small radix first, so it ends with an RMAX pass that meets the
+    // inverse's first RMAX pass in registers (split-step column pass)
+    typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_COL, P::PSH, true> XF;
+    typedef Xform<T, L, G, NT, P::RMAX, -1, LAYOUT_COL, P::PSH, false> XI;
+    static_assert(!(FWD && INV) || XF::RL == XI::R0, "forward/inverse junction radix");
+    typedef typename std::conditional<FWD, XF, XI>::type XA;  // first transform
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     C* thi = s + TE + (TE >> P::PSH) + 1;
     C* tlo = thi + TwDims<L>::NHI;
-    C* olo = tlo + TwDims<L>::NLO;  // [G][OLO]
-    C* ohi = olo + G * Gm::OLO;     // [G][OHI]
+    C* olo = tlo + TwDims<L>::NLO;  // [OLO][G]
+    C* ohi = olo + G * Gm::OLO;     // [OHI][G]
     const int tid = threadIdx.x;
     const long long col0 = (long long)blockIdx.x * G;
     const int N1m = p.N1 - 1;
 
     tw_init<T, L>(thi, tlo, tid, NT);
     if constexpr (INV) {
-        // W_N^{-n2 k1} for the tile's columns: olo[g][m] = W^{-k1 m}, ohi[g][h] = W^{-k1 32 h}
+        // W_N^{-n2 k1} for the tile's columns: olo[m][g] = W^{-k1 m}, ohi[h][g] = W^{-k1 32 h}
         for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
-            const int g = i / (Gm::OLO + Gm::OHI), m = i % (Gm::OLO + Gm::OHI);
+            const int g = i % G, m = i / G;
             const long long k1 = (col0 + g) & N1m;
-            if (m < Gm::OLO) olo[g * Gm::OLO + m] = expi_ratio<T>(-k1 * m, p.logN);
-            else ohi[g * Gm::OHI + (m - Gm::OLO)] = expi_ratio<T>(-k1 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+            if (m < Gm::OLO) olo[m * G + g] = expi_ratio<T>(-k1 * m, p.logN);
+            else ohi[(m - Gm::OLO) * G + g] = expi_ratio<T>(-k1 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
         }
-    }
-
-    // load the tile (element (l, g) = row l of column col0 + g)
-#pragma unroll 4
-    for (int i = tid; i < TE; i += NT) {
-        const int l = i / G, g = i % G;
-        const long long col = col0 + g;
-        C v = mkc(T(0), T(0));
-        if (col < p.ncols) {
-            const long long node = col >> p.logN1;
-            const long long c = col & N1m;
-            v = p.src[node * p.src_stride + (long long)l * p.N1 + c];
-            if constexpr (MODE == KC_MPA_PRE) {
-                // MPA step 2: A_hat_j = psi_j exp(i beta(w, z_j) + int G)
-                const NodeC nc = p.nodes[node];
-                const long long k = c + (long long)l * p.N1;
-                const C ph = expi_turns<T>(phase_q64(signed_k(k, p.N), nc));
-                v = cscale(cmul(v, ph), (T)nc.pre);
-            }
-        }
-        s[phys<P::PSH>(i)] = v;
     }
     __syncthreads();
 
-    if constexpr (FWD) stockham<T, L, G, NT, P::RMAX, 1, +1, LAYOUT_COL, P::PSH>(s, thi, tlo);
-
-    if constexpr (MODE == KC_SS_STEP) {
-        // exact linear step exp(i beta(w; za, zb) + int G) between the kicks
-        for (int i = tid; i < TE; i += NT) {
-            const int l = i / G, g = i % G;
-            const long long c = (col0 + g) & N1m;
-            const long long k = c + (long long)l * p.N1;
-            C v = s[phys<P::PSH>(i)];
-            const C ph = expi_turns<T>(phase_q64(signed_k(k, p.N), p.flow));
-            s[phys<P::PSH>(i)] = cscale(cmul(v, ph), (T)p.flow.pre);
+    // ---- load: element j + r L/R0 of column col0 + g, straight into registers
+    C vin[XA::Q0][XA::R0];
+#pragma unroll
+    for (int q = 0; q < XA::Q0; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, XA::R0>(tid + q * NT, j, g);
+        const long long col = col0 + g;
+        const bool ok = col < p.ncols;
+        const long long node = ok ? (col >> p.logN1) : 0;
+        const long long c = col & N1m;
+        const C* src = p.src + node * p.src_stride + c;
+        NodeC nc;
+        if constexpr (MODE == KC_MPA_PRE) nc = p.nodes[node];
+#pragma unroll
+        for (int r = 0; r < XA::R0; ++r) {
+            const int row = j + r * (L / XA::R0);
+            C v = ok ? src[(long long)row * p.N1] : mkc(T(0), T(0));
+            if constexpr (MODE == KC_MPA_PRE) {
+                // MPA step 2: A_hat_j = psi_j exp(i beta(w, z_j) + int G)
+                const C ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
+                v = cscale(cmul(v, ph), (T)nc.pre);
+            }
+            vin[q][r] = v;
         }
-        __syncthreads();
     }
 
-    if constexpr (INV) stockham<T, L, G, NT, P::RMAX, 1, -1, LAYOUT_COL, P::PSH>(s, thi, tlo);
+    // ---- transforms
+    constexpr int QO = INV ? XI::QL : XF::QL, RO = INV ? XI::RL : XF::RL;
+    C vout[QO][RO];
+    if constexpr (FWD && INV) {
+        C vm[XF::QL][XF::RL];
+        XF::run(vin, vm, s, thi, tlo);
+        // exact linear step exp(i beta(w; za, zb) + int G) between the kicks of Eq. (4)
+#pragma unroll
+        for (int q = 0; q < XF::QL; ++q) {
+            int j, g;
+            bmap<LAYOUT_COL, L, G, XF::RL>(tid + q * NT, j, g);
+            const long long c = (col0 + g) & N1m;
+#pragma unroll
+            for (int r = 0; r < XF::RL; ++r) {
+                const int row = j + r * (L / XF::RL);
+                const C ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), p.flow));
+                vm[q][r] = cscale(cmul(vm[q][r], ph), (T)p.flow.pre);
+            }
+        }
+        XI::run(vm, vout, s, thi, tlo);
+    } else if constexpr (FWD) {
+        XF::run(vin, vout, s, thi, tlo);
+    } else {
+        XI::run(vin, vout, s, thi, tlo);
+    }
 
-    // store
-#pragma unroll 4
-    for (int i = tid; i < TE; i += NT) {
-        const int l = i / G, g = i % G;
+    // ---- epilogue and store: element j + r L/RO of column col0 + g
+#pragma unroll
+    for (int q = 0; q < QO; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, RO>(tid + q * NT, j, g);
         const long long col = col0 + g;
         if (col >= p.ncols) continue;
         const long long node = col >> p.logN1;
         const long long c = col & N1m;
-        C v = s[phys<P::PSH>(i)];
-        if constexpr (INV) {
-            // four-step factor W_N^{-n2 k1}, n2 = l
-            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
-            if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
-            v = cmul(v, w);
+        C* dst = p.dst + node * p.dst_stride + c;
+        NodeC nc;
+        if constexpr (MODE == KC_MPA_POST) nc = p.nodes[node];
+#pragma unroll
+        for (int r = 0; r < RO; ++r) {
+            const int row = j + r * (L / RO);
+            C v = vout[q][r];
+            if constexpr (INV) {
+                // four-step factor W_N^{-n2 k1}, n2 = row
+                C w = olo[(row & (Gm::OLO - 1)) * G + g];
+                if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
+                v = cmul(v, w);
+            }
+            if constexpr (MODE == KC_MPA_POST) {
+                // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
+                const C ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
+                v = cscale(cmul(v, cconj(ph)), (T)nc.post);
+            }
+            dst[(long long)row * p.N1] = v;
         }
-        if constexpr (MODE == KC_MPA_POST) {
-            // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
-            const NodeC nc = p.nodes[node];
-            const long long k = c + (long long)l * p.N1;
-            const C ph = expi_turns<T>(phase_q64(signed_k(k, p.N), nc));
-            v = cscale(cmul(v, cconj(ph)), (T)nc.post);
-        }
-        p.dst[node * p.dst_stride + (long long)l * p.N1 + c] = v;
     }
 }
 
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(KRGeom<T, L>::NT) kr_kernel(const KRParams<T> p) {
+__global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? 2 : 1)
+    kr_kernel(const KRParams<T> p) {
     typedef cx<T> C;
     typedef KRGeom<T, L> Gm;
     typedef Tiling<T> P;
     constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
     constexpr bool INV = (MODE != KR_FWD);
     constexpr bool FWD = (MODE != KR_INV);
+    // inverse: small radix last, forward: small radix first, so the two meet
+    // in registers around the pointwise step
+    typedef Xform<T, L, G, NT, P::RMAX, -1, LAYOUT_ROW, P::PSH, false> XI;
+    typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_ROW, P::PSH, true> XF;
+    static_assert(!(FWD && INV) || XI::RL == XF::R0, "inverse/forward junction radix");
+    typedef typename std::conditional<INV, XI, XF>::type XA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     C* thi = s + TE + (TE >> P::PSH) + 1;
@@ -197,23 +233,34 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT) kr_kernel(const KRParams<T> 
         // W_N^{+n2 k1} for the tile's rows: olo[g][m] = W^{n2 m}, ohi[g][h] = W^{n2 128 h}
         for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
             const int g = i / (Gm::OLO + Gm::OHI), m = i % (Gm::OLO + Gm::OHI);
-            const long long n2 = (row0 + g) % p.N2;
+            const long long n2 = (row0 + g) & (p.N2 - 1);
             if (m < Gm::OLO) olo[g * Gm::OLO + m] = expi_ratio<T>(n2 * m, p.logN);
             else ohi[g * Gm::OHI + (m - Gm::OLO)] = expi_ratio<T>(n2 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
         }
     }
-
-    C* base = p.data + row0 * L;
-    const long long lim = (p.nrows - row0) * L;  // elements of this tile that exist
-#pragma unroll 4
-    for (int i = tid; i < TE; i += NT) s[phys<P::PSH>(i)] = (i < lim) ? base[i] : mkc(T(0), T(0));
     __syncthreads();
 
-    if constexpr (INV) {
-        stockham<T, L, G, NT, P::RMAX, 1, -1, LAYOUT_ROW, P::PSH>(s, thi, tlo);
-        if constexpr (MODE != KR_INV) {
-            for (int i = tid; i < TE; i += NT) {
-                C a = cscale(s[phys<P::PSH>(i)], p.inv_n);  // A(t) (MPA step 3 / SS inverse)
+    C vin[XA::Q0][XA::R0];
+#pragma unroll
+    for (int q = 0; q < XA::Q0; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XA::R0>(tid + q * NT, j, g);
+        const bool ok = row0 + g < p.nrows;
+        const C* src = p.data + (row0 + g) * L;
+#pragma unroll
+        for (int r = 0; r < XA::R0; ++r) vin[q][r] = ok ? src[j + r * (L / XA::R0)] : mkc(T(0), T(0));
+    }
+
+    constexpr int QO = FWD ? XF::QL : XI::QL, RO = FWD ? XF::RL : XI::RL;
+    C vout[QO][RO];
+    if constexpr (INV && FWD) {
+        C vm[XI::QL][XI::RL];
+        XI::run(vin, vm, s, thi, tlo);
+#pragma unroll
+        for (int q = 0; q < XI::QL; ++q) {
+#pragma unroll
+            for (int r = 0; r < XI::RL; ++r) {
+                C a = cscale(vm[q][r], p.inv_n);  // A(t) (MPA step 3 / SS inverse)
                 const T pw = a.x * a.x + a.y * a.y;
                 if constexpr (MODE == KR_MPA) {
                     a = cscale(a, pw);  // |A|^2 A (MPA step 4)
@@ -223,26 +270,35 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT) kr_kernel(const KRParams<T> 
                     else sincos(p.rot * pw, &sn, &cs);
                     a = cmul(a, mkc(cs, sn));
                 }
-                s[phys<P::PSH>(i)] = a;
+                vm[q][r] = a;
             }
-            __syncthreads();
         }
+        XF::run(vm, vout, s, thi, tlo);
+    } else if constexpr (INV) {
+        XI::run(vin, vout, s, thi, tlo);
+    } else {
+        XF::run(vin, vout, s, thi, tlo);
     }
-    if constexpr (FWD) stockham<T, L, G, NT, P::RMAX, 1, +1, LAYOUT_ROW, P::PSH>(s, thi, tlo);
 
-#pragma unroll 4
-    for (int i = tid; i < TE; i += NT) {
-        if (i >= lim) continue;
-        C v = s[phys<P::PSH>(i)];
-        if constexpr (FWD) {
-            const int g = i / L, l = i % L;  // l = k1
-            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
-            if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
-            v = cmul(v, w);
-        } else {
-            v = cscale(v, p.inv_n);
+#pragma unroll
+    for (int q = 0; q < QO; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, RO>(tid + q * NT, j, g);
+        if (row0 + g >= p.nrows) continue;
+        C* dst = p.data + (row0 + g) * L;
+#pragma unroll
+        for (int r = 0; r < RO; ++r) {
+            const int l = j + r * (L / RO);  // k1
+            C v = vout[q][r];
+            if constexpr (FWD) {
+                C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+                if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
+                v = cmul(v, w);
+            } else {
+                v = cscale(v, p.inv_n);
+            }
+            dst[l] = v;
         }
-        base[i] = v;
     }
 }
 

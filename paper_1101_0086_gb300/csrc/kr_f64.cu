@@ -11,11 +11,16 @@ static cudaError_t kr_one(const KRParams<double>& p, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kr_kernel<double, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kr_kernel<double, L, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const long long nblk = (p.nrows + Gm::G - 1) / Gm::G;
     if (nblk <= 0) return cudaSuccess;
+    const bool prof = g_prof_on.load(std::memory_order_relaxed);
+    if (prof) prof_begin(st);
     kr_kernel<double, L, MODE><<<(unsigned)nblk, Gm::NT, Gm::smem_bytes, st>>>(p);
+    if (prof) prof_end(prof_kr_kind(MODE), st, 2.0 * (double)p.nrows * L * sizeof(cx<double>));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

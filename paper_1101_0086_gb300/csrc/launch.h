@@ -11,6 +11,20 @@ namespace mpa {
 // Kernels launched by this library since load.
 extern std::atomic<long long> g_launches;
 
+// Optional CUDA-event timing of every launch, by kernel kind (off by
+// default; enabled through mpa_profile).
+enum {
+    PK_KC_MPA_PRE = 0, PK_KC_MPA_POST, PK_KC_SS, PK_KC_FFT, PK_KR_MPA, PK_KR_SS, PK_KR_FFT, PK_SCAN, PK_AUX,
+    PK_COUNT
+};
+extern std::atomic<bool> g_prof_on;
+void prof_begin(cudaStream_t st);
+void prof_end(int kind, cudaStream_t st, double bytes);
+int prof_kc_kind(int mode);
+int prof_kr_kind(int mode);
+cudaError_t prof_read(int kind, double* ms, long long* n, double* bytes);
+void prof_reset();
+
 // Column/row lengths supported by the column pass (2^4..2^11) and the row
 // pass (2^4..2^14 FP32, 2^4..2^13 FP64).
 constexpr int KC_LOG_MIN = 4, KC_LOG_MAX = 11;

@@ -1,14 +1,124 @@
-// Launchers of the scan, transpose and precision-conversion kernels.
+// Launchers of the scan, transpose and precision-conversion kernels, and the
+// optional per-launch CUDA-event timer.
+#include <mutex>
+#include <vector>
+
 #include "launch.h"
 
 namespace mpa {
 
 std::atomic<long long> g_launches{0};
+std::atomic<bool> g_prof_on{false};
+
+namespace {
+struct Prof {
+    std::mutex mu;
+    std::vector<cudaEvent_t> free_events;
+    struct Pending {
+        cudaEvent_t a, b;
+        int kind;
+        double bytes;
+    };
+    std::vector<Pending> pending;
+    cudaEvent_t open = nullptr;
+    double ms[PK_COUNT] = {};
+    long long n[PK_COUNT] = {};
+    double bytes[PK_COUNT] = {};
+    cudaEvent_t get() {
+        if (!free_events.empty()) {
+            cudaEvent_t e = free_events.back();
+            free_events.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    // fold finished intervals into the totals (synchronises on each end event)
+    cudaError_t drain() {
+        cudaError_t rc = cudaSuccess;
+        for (auto& p : pending) {
+            float t = 0.f;
+            cudaError_t e = cudaEventSynchronize(p.b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.a, p.b);
+            if (e == cudaSuccess) {
+                ms[p.kind] += t;
+                n[p.kind] += 1;
+                bytes[p.kind] += p.bytes;
+            } else {
+                rc = e;
+            }
+            free_events.push_back(p.a);
+            free_events.push_back(p.b);
+        }
+        pending.clear();
+        return rc;
+    }
+};
+Prof& prof() {
+    static Prof p;
+    return p;
+}
+}  // namespace
+
+void prof_begin(cudaStream_t st) {
+    Prof& P = prof();
+    std::lock_guard<std::mutex> g(P.mu);
+    P.open = P.get();
+    if (P.open) cudaEventRecord(P.open, st);
+}
+
+void prof_end(int kind, cudaStream_t st, double bytes) {
+    Prof& P = prof();
+    std::lock_guard<std::mutex> g(P.mu);
+    if (!P.open) return;
+    cudaEvent_t b = P.get();
+    if (!b) return;
+    cudaEventRecord(b, st);
+    P.pending.push_back({P.open, b, kind, bytes});
+    P.open = nullptr;
+    if (P.pending.size() > 4096) P.drain();
+}
+
+int prof_kc_kind(int mode) {
+    return mode == KC_MPA_PRE ? PK_KC_MPA_PRE : mode == KC_MPA_POST ? PK_KC_MPA_POST
+         : mode == KC_SS_STEP ? PK_KC_SS : PK_KC_FFT;
+}
+int prof_kr_kind(int mode) { return mode == KR_MPA ? PK_KR_MPA : mode == KR_SS ? PK_KR_SS : PK_KR_FFT; }
+
+cudaError_t prof_read(int kind, double* ms, long long* n, double* bytes) {
+    Prof& P = prof();
+    std::lock_guard<std::mutex> g(P.mu);
+    cudaError_t rc = P.drain();
+    *ms = P.ms[kind];
+    *n = P.n[kind];
+    *bytes = P.bytes[kind];
+    return rc;
+}
+
+void prof_reset() {
+    Prof& P = prof();
+    std::lock_guard<std::mutex> g(P.mu);
+    P.drain();
+    for (int k = 0; k < PK_COUNT; ++k) {
+        P.ms[k] = 0.0;
+        P.n[k] = 0;
+    }
+}
 
 static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, cudaStream_t st) {
+    const bool pr = g_prof_on.load(std::memory_order_relaxed);
+    if (pr) prof_begin(st);
     scan_kernel<T><<<blocks_for(p.N, 256), 256, 0, st>>>(p);
+    if (pr) {
+        const double cs = (double)sizeof(cx<T>), n = (double)p.N;
+        double b = (p.M + 1) * n * cs + n * cs;  // V_0..V_M and psi_0
+        if (p.mode == 0) b += p.M * n * cs;      // psi^{(n+1)}_1..M
+        else b += n * 16.0 + (p.mode == 1 ? n * (16.0 + cs) : n * 16.0);  // FP64 state in, result out
+        prof_end(PK_SCAN, st, b);
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -547,4 +547,24 @@ const char* mpa_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 int64_t mpa_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+void mpa_profile(int enable) {
+    if (enable) prof_reset();
+    g_prof_on.store(enable != 0);
+}
+
+int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* bytes) {
+    if (kind < 0 || kind >= PK_COUNT || !total_ms || !launches || !bytes) return MPA_ERR_INVALID_ARG;
+    long long n = 0;
+    cudaError_t e = prof_read(kind, total_ms, &n, bytes);
+    *launches = n;
+    if (e != cudaSuccess) return cuda_fail(e);
+    return MPA_OK;
+}
+
+const char* mpa_profile_kind_name(int kind) {
+    static const char* names[PK_COUNT] = {"kc_mpa_pre", "kc_mpa_post", "kc_ss_step", "kc_fft", "kr_mpa",
+                                          "kr_ss", "kr_fft", "scan", "aux"};
+    return (kind >= 0 && kind < PK_COUNT) ? names[kind] : nullptr;
+}
+
 }  // extern "C"

@@ -42,7 +42,8 @@ class _PlanParams(ctypes.Structure):
 
 EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
            "mpa_interval", "mpa_plan_status", "mpa_plan_destroy", "ss_workspace_size", "ss_propagate",
-           "mpa_fft", "mpa_status_string", "mpa_last_cuda_error", "mpa_kernel_launches")
+           "mpa_fft", "mpa_status_string", "mpa_last_cuda_error", "mpa_kernel_launches", "mpa_profile",
+           "mpa_profile_read", "mpa_profile_kind_name")
 
 
 def library_path() -> str:
@@ -72,6 +73,13 @@ def lib() -> ctypes.CDLL:
         L.mpa_status_string.restype = ctypes.c_char_p
         L.mpa_last_cuda_error.restype = ctypes.c_char_p
         L.mpa_kernel_launches.restype = i64
+        L.mpa_profile.argtypes = [ctypes.c_int]
+        L.mpa_profile.restype = None
+        L.mpa_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                       ctypes.POINTER(ctypes.c_double)]
+        L.mpa_profile_read.restype = ctypes.c_int
+        L.mpa_profile_kind_name.argtypes = [ctypes.c_int]
+        L.mpa_profile_kind_name.restype = ctypes.c_char_p
         for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
                   "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft"):
             getattr(L, f).restype = ctypes.c_int
@@ -215,3 +223,25 @@ def fft(data: torch.Tensor, sign: int, workspace: Optional[torch.Tensor] = None,
 def kernel_launches() -> int:
     """Kernels this library has launched since it was loaded."""
     return int(lib().mpa_kernel_launches())
+
+
+def profile(enable: bool) -> None:
+    """Bracket every subsequent kernel launch with CUDA events (resets totals)."""
+    lib().mpa_profile(1 if enable else 0)
+
+
+def profile_read() -> dict:
+    """{kernel kind: (total device ms, launches, algorithmic bytes)} of the launches timed so far."""
+    L = lib()
+    out = {}
+    k = 0
+    while True:
+        name = L.mpa_profile_kind_name(k)
+        if not name:
+            break
+        ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(L.mpa_profile_read(k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)), "mpa_profile_read")
+        if n.value:
+            out[name.decode()] = (float(ms.value), int(n.value), float(b.value))
+        k += 1
+    return out
