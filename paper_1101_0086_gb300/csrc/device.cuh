@@ -146,6 +146,59 @@ template <> __device__ __forceinline__ double2 expi_turns<double>(unsigned long 
     return make_double2(c, s);
 }
 
+// exp(2 pi i theta) for a Q0.64 turn fraction from a table of
+// exp(2 pi i m / 1024) (m = 0..1023) and the Taylor series of the residual
+// phi = 2 pi (theta - m/1024), |phi| <= pi/1024: cos = 1 - phi^2/2 (next
+// term phi^4/24 < 4e-12), sin = phi - phi^3/6 (next term < 3e-15).  Accurate
+// to FP32 rounding; replaces sincospif where the phase is evaluated per
+// element.
+constexpr int EXPI_TAB = 1024;
+__device__ __forceinline__ float2 expi_turns_tab(unsigned long long th, const float2* tab) {
+    const unsigned long long m = (th + (1ull << 53)) >> 54;  // nearest m/1024
+    const long long d = (long long)(th - (m << 54));          // residual in 2^-64 turns, |d| <= 2^53
+    const float phi = __ll2float_rn(d) * 3.4061215800865545e-19f;  // 2 pi 2^-64
+    const float p2 = phi * phi;
+    const float c = fmaf(-0.5f, p2, 1.0f);
+    const float sn = phi * fmaf(p2, -0.16666667f, 1.0f);
+    const float2 t = tab[m & (EXPI_TAB - 1)];
+    return make_float2(t.x * c - t.y * sn, t.x * sn + t.y * c);
+}
+
+__device__ __forceinline__ void expi_tab_init(float2* tab, int tid, int nt) {
+    for (int i = tid; i < EXPI_TAB; i += nt) {
+        float s, c;
+        sincospif((float)i * (2.0f / EXPI_TAB), &s, &c);
+        tab[i] = make_float2(c, s);
+    }
+}
+
+// Phases of the R elements k'_s = k'_0 + s D, s = -R/2 .. R/2-1 of one
+// butterfly by exact finite differences in Q0.64 arithmetic: theta is a
+// cubic in s, so after four direct evaluations every further value costs
+// three 64-bit additions (the direct values carry < 3 ulp of 2^-64 each, so
+// the accumulated error stays below 2^-50 turns).  th[r] receives the phase
+// of element r, where s = r for r < R/2 and s = r - R for r >= R/2.
+template <int R>
+__device__ __forceinline__ void phase_run(long long k0, long long D, const NodeC& c, unsigned long long (&th)[R]) {
+    static_assert(R >= 4, "finite differences need four points");
+    const long long ks = k0 - (long long)(R / 2) * D;
+    unsigned long long t0 = phase_q64(ks, c), t1 = phase_q64(ks + D, c), t2 = phase_q64(ks + 2 * D, c),
+                       t3 = phase_q64(ks + 3 * D, c);
+    unsigned long long d1 = t3 - t2, d2 = t3 - 2 * t2 + t1, d3 = t3 - 3 * t2 + 3 * t1 - t0;
+    th[R / 2] = t0;
+    th[R / 2 + 1] = t1;
+    th[R / 2 + 2] = t2;
+    th[R / 2 + 3] = t3;
+    unsigned long long t = t3;
+#pragma unroll
+    for (int s = -R / 2 + 4; s < R / 2; ++s) {
+        d2 += d3;
+        d1 += d2;
+        t += d1;
+        th[(s + R) % R] = t;
+    }
+}
+
 // exp(2 pi i e / n) for an integer e (|e| small enough to be exact in T
 // after reduction to [-n/2, n/2)), n a power of two given by log2.
 template <typename T> __device__ __forceinline__ cx<T> expi_ratio(long long e, int log2n) {
@@ -348,11 +401,25 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
 // Precision-dependent tiling: elements per thread E, largest radix, the
 // padding shift, the minimum column-tile width (64-byte row segments) and
 // the target tile size in elements.
-template <typename T> struct Tiling;
-template <> struct Tiling<float> {
-    static constexpr int E = 32, RMAX = 16, PSH = 4, CMIN = 8, TE = 8192;
+// KIND 0 = column pass, 1 = row pass (tuned separately).
+#ifndef MPA_KC_E
+#define MPA_KC_E 32
+#endif
+#ifndef MPA_KC_TE
+#define MPA_KC_TE 8192
+#endif
+#ifndef MPA_KR_E
+#define MPA_KR_E 32
+#endif
+#ifndef MPA_KR_TE
+#define MPA_KR_TE 8192
+#endif
+template <typename T, int KIND = 0> struct Tiling;
+template <int KIND> struct Tiling<float, KIND> {
+    static constexpr int E = KIND == 0 ? MPA_KC_E : MPA_KR_E, RMAX = 16, PSH = 4, CMIN = 8;
+    static constexpr int TE = KIND == 0 ? MPA_KC_TE : MPA_KR_TE;
 };
-template <> struct Tiling<double> {
+template <int KIND> struct Tiling<double, KIND> {
     static constexpr int E = 16, RMAX = 8, PSH = 3, CMIN = 4, TE = 4096;
 };
 

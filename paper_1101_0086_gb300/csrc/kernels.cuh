@@ -65,11 +65,12 @@ template <typename T, int L> struct KCGeom {
     static constexpr int OHI = L > 32 ? L / 32 : 1;
     static constexpr size_t smem_elems = (size_t)TE + (TE >> P::PSH) + 1 + TwDims<L>::NLO + TwDims<L>::NHI +
                                          (size_t)G * (OLO + OHI);
-    static constexpr size_t smem_bytes = smem_elems * sizeof(cx<T>);
+    // FP32: + the exp(2 pi i m/1024) table of the per-element phases
+    static constexpr size_t smem_bytes = smem_elems * sizeof(cx<T>) + (sizeof(T) == 4 ? EXPI_TAB * sizeof(float2) : 0);
 };
 
 template <typename T, int L> struct KRGeom {
-    typedef Tiling<T> P;
+    typedef Tiling<T, 1> P;
     static constexpr int G = (P::TE / L) > 1 ? (P::TE / L) : 1;
     static constexpr int TE = G * L;
     static constexpr int NT = TE / P::E;
@@ -104,11 +105,15 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
     C* tlo = thi + TwDims<L>::NHI;
     C* olo = tlo + TwDims<L>::NLO;  // [OLO][G]
     C* ohi = olo + G * Gm::OLO;     // [OHI][G]
+    float2* etab = reinterpret_cast<float2*>(ohi + G * Gm::OHI);
     const int tid = threadIdx.x;
     const long long col0 = (long long)blockIdx.x * G;
     const int N1m = p.N1 - 1;
+    constexpr bool FAST = sizeof(T) == 4;  // FP32: finite-difference phases + table exp
 
     tw_init<T, L>(thi, tlo, tid, NT);
+    if constexpr (FAST && (MODE == KC_MPA_PRE || MODE == KC_MPA_POST || MODE == KC_SS_STEP))
+        expi_tab_init(etab, tid, NT);
     if constexpr (INV) {
         // W_N^{-n2 k1} for the tile's columns: olo[m][g] = W^{-k1 m}, ohi[h][g] = W^{-k1 32 h}
         for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
@@ -133,13 +138,18 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
         const C* src = p.src + node * p.src_stride + c;
         NodeC nc;
         if constexpr (MODE == KC_MPA_PRE) nc = p.nodes[node];
+        unsigned long long th[XA::R0];
+        if constexpr (FAST && MODE == KC_MPA_PRE)
+            phase_run<XA::R0>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::R0), nc, th);
 #pragma unroll
         for (int r = 0; r < XA::R0; ++r) {
             const int row = j + r * (L / XA::R0);
             C v = ok ? src[(long long)row * p.N1] : mkc(T(0), T(0));
             if constexpr (MODE == KC_MPA_PRE) {
                 // MPA step 2: A_hat_j = psi_j exp(i beta(w, z_j) + int G)
-                const C ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
+                C ph;
+                if constexpr (FAST) ph = expi_turns_tab(th[r], etab);
+                else ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
                 v = cscale(cmul(v, ph), (T)nc.pre);
             }
             vin[q][r] = v;
@@ -158,10 +168,14 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
             int j, g;
             bmap<LAYOUT_COL, L, G, XF::RL>(tid + q * NT, j, g);
             const long long c = (col0 + g) & N1m;
+            unsigned long long th[XF::RL];
+            if constexpr (FAST) phase_run<XF::RL>(c + (long long)j * p.N1, (long long)p.N1 * (L / XF::RL), p.flow, th);
 #pragma unroll
             for (int r = 0; r < XF::RL; ++r) {
                 const int row = j + r * (L / XF::RL);
-                const C ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), p.flow));
+                C ph;
+                if constexpr (FAST) ph = expi_turns_tab(th[r], etab);
+                else ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), p.flow));
                 vm[q][r] = cscale(cmul(vm[q][r], ph), (T)p.flow.pre);
             }
         }
@@ -184,6 +198,9 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
         C* dst = p.dst + node * p.dst_stride + c;
         NodeC nc;
         if constexpr (MODE == KC_MPA_POST) nc = p.nodes[node];
+        unsigned long long th[RO];
+        if constexpr (FAST && MODE == KC_MPA_POST)
+            phase_run<RO>(c + (long long)j * p.N1, (long long)p.N1 * (L / RO), nc, th);
 #pragma unroll
         for (int r = 0; r < RO; ++r) {
             const int row = j + r * (L / RO);
@@ -196,7 +213,9 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
             }
             if constexpr (MODE == KC_MPA_POST) {
                 // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
-                const C ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
+                C ph;
+                if constexpr (FAST) ph = expi_turns_tab(th[r], etab);
+                else ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
                 v = cscale(cmul(v, cconj(ph)), (T)nc.post);
             }
             dst[(long long)row * p.N1] = v;
@@ -209,7 +228,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? 2 
     kr_kernel(const KRParams<T> p) {
     typedef cx<T> C;
     typedef KRGeom<T, L> Gm;
-    typedef Tiling<T> P;
+    typedef Tiling<T, 1> P;
     constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
     constexpr bool INV = (MODE != KR_FWD);
     constexpr bool FWD = (MODE != KR_INV);
