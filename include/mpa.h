@@ -142,6 +142,28 @@ MPA_API int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, doubl
 MPA_API int mpa_fft(int64_t N, int32_t precision, int32_t sign, void* data, void* workspace, size_t ws_bytes,
             mpa_stream stream);
 
+/* Size limit of mpa_fft_noalloc: N times the element size (8 or 16 bytes)
+ * may not exceed this many bytes (N <= 2^20 in FP32, 2^19 in FP64). */
+#define MPA_FFT_NOALLOC_MAX_BYTES (8u << 20)
+
+/* mpa_fft for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a library convenience.  A plugin inside a host
+ * application that owns all device memory through its own pool, or a
+ * latency-critical loop that must not stall on cudaMalloc, may have no
+ * workspace to pass: this entry point takes only `data` (N samples of the
+ * precision's complex type, transformed in place exactly as mpa_fft does)
+ * and uses a scratch array compiled into the library, which every GPU that
+ * loads the library holds (MPA_FFT_NOALLOC_MAX_BYTES) until the process
+ * exits.  It calls no cudaMalloc, cudaFree or allocating routine.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array, so calls that overlap on the GPU race:
+ * order them on one stream or synchronise between them.  Nothing in the
+ * array needs to start at zero (each call overwrites what it reads).
+ * Errors: MPA_ERR_WORKSPACE when N times the element size exceeds
+ * MPA_FFT_NOALLOC_MAX_BYTES; otherwise as mpa_fft. */
+MPA_API int mpa_fft_noalloc(int64_t N, int32_t precision, int32_t sign, void* data, mpa_stream stream);
+
 /* Human-readable status; the last CUDA error string for MPA_ERR_CUDA. */
 MPA_API const char* mpa_status_string(int status);
 MPA_API const char* mpa_last_cuda_error(void);

@@ -43,7 +43,7 @@ class _PlanParams(ctypes.Structure):
 EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
            "mpa_interval", "mpa_plan_status", "mpa_plan_destroy", "ss_workspace_size", "ss_propagate",
            "mpa_fft", "mpa_status_string", "mpa_last_cuda_error", "mpa_kernel_launches", "mpa_profile",
-           "mpa_profile_read", "mpa_profile_kind_name")
+           "mpa_profile_read", "mpa_profile_kind_name", "mpa_fft_noalloc")
 
 
 def library_path() -> str:
@@ -69,6 +69,8 @@ def lib() -> ctypes.CDLL:
         L.ss_workspace_size.argtypes = [i64, i32, szp]
         L.ss_propagate.argtypes = [ctypes.POINTER(_FiberMap), i64, dbl, dbl, i32, vp, dbl, dbl, vp, ctypes.c_size_t, vp]
         L.mpa_fft.argtypes = [i64, i32, i32, vp, vp, ctypes.c_size_t, vp]
+        L.mpa_fft_noalloc.argtypes = [i64, i32, i32, vp, vp]
+        L.mpa_fft_noalloc.restype = ctypes.c_int
         L.mpa_status_string.argtypes = [ctypes.c_int]
         L.mpa_status_string.restype = ctypes.c_char_p
         L.mpa_last_cuda_error.restype = ctypes.c_char_p
@@ -217,6 +219,17 @@ def fft(data: torch.Tensor, sign: int, workspace: Optional[torch.Tensor] = None,
         workspace = torch.empty(need, dtype=torch.uint8, device=data.device)
     _check(lib().mpa_fft(N, prec, int(sign), ptr, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                          _stream(stream)), "mpa_fft")
+    return data
+
+
+def fft_noalloc(data: torch.Tensor, sign: int, stream=None) -> torch.Tensor:
+    """``mpa_fft`` without a workspace (``mpa_fft_noalloc``): the library's own
+    static scratch is used, so the caller allocates nothing; calls must not
+    overlap on the GPU.  N x element size <= 8 MiB."""
+    prec = _prec(data.dtype)
+    N = data.numel()
+    ptr = _field_ptr(data, _cdtype(prec), N, "fft_noalloc")
+    _check(lib().mpa_fft_noalloc(N, prec, int(sign), ptr, _stream(stream)), "mpa_fft_noalloc")
     return data
 
 
