@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--ss-km", type=float, default=25.0, help="km of split-step timed as the comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, split-step and CPU legs (profiling runs)")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "level", "wavefront"])
     return ap.parse_args()
 
 
@@ -213,7 +214,7 @@ def run_mpa(args, world, rank, local):
     A0 = w.field()
     src = torch.from_numpy(A0.astype(np.complex64)).cuda()
     f = torch.empty_like(src)
-    plan = mpa.Plan(w.fiber, N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32")
+    plan = mpa.Plan(w.fiber, N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32", schedule=args.schedule)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -269,7 +270,7 @@ def run_mpa(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "N": N, "km_per_step": km, "channels": w.n_channels,
                        "symbols_per_channel": w.n_symbols, "L_km": w.mpa_L_km, "M": w.mpa_M,
-                       "n_iter": w.mpa_n_iter, "method": "MPA FP32 (FP64 state)",
+                       "n_iter": w.mpa_n_iter, "method": "MPA FP32 (FP64 state)", "schedule": args.schedule,
                        "l2": "flushed between steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": roofline, "kernels": kern, "clocks": ck, "gpu_launches": launches,

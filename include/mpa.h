@@ -54,6 +54,17 @@ enum {
 
 enum { MPA_FP32 = 0, MPA_FP64 = 1 };
 
+/* Launch schedule of the MPA steps within an interval.  LEVEL: the paper's
+ * order, every node of an iteration, then the next iteration (memory
+ * (M+1) N samples).  WAVEFRONT: node blocks advance through the iterations
+ * one step at a time, the forward and inverse column transforms of
+ * consecutive iterations and the trapezoid sums fused in one kernel (FP32,
+ * memory about 3 n_iter N samples + 256 MiB).  Both compute Eq. (6); they
+ * differ only in FP32 summation order.  WAVEFRONT needs FP32, N >= 2^14 and
+ * n_iter <= 8.  AUTO picks LEVEL, the faster of the two on GB300 at the
+ * benchmark sizes (the wavefront saves memory, not time). */
+enum { MPA_SCHEDULE_AUTO = 0, MPA_SCHEDULE_LEVEL = 1, MPA_SCHEDULE_WAVEFRONT = 2 };
+
 typedef void* mpa_stream; /* cudaStream_t */
 
 /* One piece of the dispersion-management period with constant coefficients. */
@@ -87,6 +98,7 @@ typedef struct {
     int32_t M;         /* intervals of the z-quadrature per interval (M+1 nodes) */
     int32_t n_iter;    /* n_tot, Picard iterations per interval (>= 1) */
     int32_t precision; /* MPA_FP32 (FFT/nonlinearity in FP32, phase exact, Kahan sums, FP64 state) or MPA_FP64 */
+    int32_t schedule;  /* MPA_SCHEDULE_* (0 = AUTO); WAVEFRONT where unsupported is MPA_ERR_INVALID_ARG */
 } mpa_plan_params;
 
 typedef struct mpa_plan mpa_plan;

@@ -146,31 +146,62 @@ template <> __device__ __forceinline__ double2 expi_turns<double>(unsigned long 
     return make_double2(c, s);
 }
 
-// exp(2 pi i theta) for a Q0.64 turn fraction from a table of
-// exp(2 pi i m / 1024) (m = 0..1023) and the Taylor series of the residual
-// phi = 2 pi (theta - m/1024), |phi| <= pi/1024: cos = 1 - phi^2/2 (next
-// term phi^4/24 < 4e-12), sin = phi - phi^3/6 (next term < 3e-15).  Accurate
-// to FP32 rounding; replaces sincospif where the phase is evaluated per
-// element.
-constexpr int EXPI_TAB = 1024;
-__device__ __forceinline__ float2 expi_turns_tab(unsigned long long th, const float2* tab) {
-    const unsigned long long m = (th + (1ull << 53)) >> 54;  // nearest m/1024
-    const long long d = (long long)(th - (m << 54));          // residual in 2^-64 turns, |d| <= 2^53
-    const float phi = __ll2float_rn(d) * 3.4061215800865545e-19f;  // 2 pi 2^-64
-    const float p2 = phi * phi;
-    const float c = fmaf(-0.5f, p2, 1.0f);
-    const float sn = phi * fmaf(p2, -0.16666667f, 1.0f);
-    const float2 t = tab[m & (EXPI_TAB - 1)];
-    return make_float2(t.x * c - t.y * sn, t.x * sn + t.y * c);
+// exp(2 pi i theta) for a Q0.64 turn fraction in FP32 without tables:
+// split theta into the nearest quarter turn q and a residual angle
+// x = 2 pi (theta - q/4), |x| <= pi/4, evaluate cos x and sin x by their
+// Taylor series through x^8 and x^9 (truncation below 2.5e-8 and 1.8e-9),
+// and rotate by i^q.
+__device__ __forceinline__ float2 expi_turns_poly(unsigned long long th) {
+    const unsigned long long q = (th + (1ull << 61)) >> 62;  // 0..4
+    // residual in units of 2^-32 turn (|d| <= 2^29; the dropped bits are < 2^-32 turn)
+    const int d = (int)((long long)(th - (q << 62)) >> 32);
+    const float x = __int2float_rn(d) * 1.4629180792671596e-09f;  // 2 pi 2^-32
+    const float x2 = x * x;
+    float c = fmaf(x2, 2.4801587e-05f, -1.3888889e-03f);  // 1/8!, -1/6!
+    c = fmaf(c, x2, 4.1666668e-02f);                     // 1/4!
+    c = fmaf(c, x2, -0.5f);
+    c = fmaf(c, x2, 1.0f);
+    float sn = fmaf(x2, 2.7557319e-06f, -1.9841270e-04f);  // 1/9!, -1/7!
+    sn = fmaf(sn, x2, 8.3333338e-03f);                     // 1/5!
+    sn = fmaf(sn, x2, -0.16666667f);
+    sn = fmaf(sn * x2, x, x);
+    // multiply by i^q without branches: odd q swaps (c, s) -> (-s, c), q & 2 negates
+    const bool odd = (q & 1) != 0;
+    const float a = odd ? -sn : c, b = odd ? c : sn;
+    const unsigned neg = (unsigned)(q & 2) << 30;
+    return make_float2(__uint_as_float(__float_as_uint(a) ^ neg), __uint_as_float(__float_as_uint(b) ^ neg));
 }
 
-__device__ __forceinline__ void expi_tab_init(float2* tab, int tid, int nt) {
-    for (int i = tid; i < EXPI_TAB; i += nt) {
-        float s, c;
-        sincospif((float)i * (2.0f / EXPI_TAB), &s, &c);
-        tab[i] = make_float2(c, s);
+// Exact phases theta(k'_0 + s D), s = -R/2 .. R/2-1, produced in s order
+// by finite differences in Q0.64 arithmetic: theta is a cubic in s, so
+// after four direct evaluations every further value costs three 64-bit
+// additions (each direct value carries < 3 ulp of 2^-64; the accumulated
+// error stays below 2^-50 turns).
+struct PhaseRun {
+    unsigned long long t0, t1, t2, t3, d1, d2, d3;
+    int n;
+    __device__ __forceinline__ PhaseRun(long long k_first, long long D, const NodeC& c) : n(0) {
+        t0 = phase_q64(k_first, c);
+        t1 = phase_q64(k_first + D, c);
+        t2 = phase_q64(k_first + 2 * D, c);
+        t3 = phase_q64(k_first + 3 * D, c);
+        d1 = t3 - t2;
+        d2 = t3 - 2 * t2 + t1;
+        d3 = t3 - 3 * t2 + 3 * t1 - t0;
     }
-}
+    // value number n (n = 0, 1, 2, ...) of the progression
+    __device__ __forceinline__ unsigned long long next() {
+        const int m = n++;
+        if (m == 0) return t0;
+        if (m == 1) return t1;
+        if (m == 2) return t2;
+        if (m == 3) return t3;
+        d2 += d3;
+        d1 += d2;
+        t3 += d1;
+        return t3;
+    }
+};
 
 // Phases of the R elements k'_s = k'_0 + s D, s = -R/2 .. R/2-1 of one
 // butterfly by exact finite differences in Q0.64 arithmetic: theta is a
@@ -414,10 +445,14 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
 #ifndef MPA_KR_TE
 #define MPA_KR_TE 8192
 #endif
+#ifndef MPA_KCW_E
+#define MPA_KCW_E 16
+#endif
+// KIND 2 = wavefront column pass.
 template <typename T, int KIND = 0> struct Tiling;
 template <int KIND> struct Tiling<float, KIND> {
-    static constexpr int E = KIND == 0 ? MPA_KC_E : MPA_KR_E, RMAX = 16, PSH = 4, CMIN = 8;
-    static constexpr int TE = KIND == 0 ? MPA_KC_TE : MPA_KR_TE;
+    static constexpr int E = KIND == 0 ? MPA_KC_E : KIND == 1 ? MPA_KR_E : MPA_KCW_E, RMAX = 16, PSH = 4, CMIN = 8;
+    static constexpr int TE = KIND == 1 ? MPA_KR_TE : MPA_KC_TE;
 };
 template <int KIND> struct Tiling<double, KIND> {
     static constexpr int E = 16, RMAX = 8, PSH = 3, CMIN = 4, TE = 4096;

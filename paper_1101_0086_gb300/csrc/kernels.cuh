@@ -66,7 +66,7 @@ template <typename T, int L> struct KCGeom {
     static constexpr size_t smem_elems = (size_t)TE + (TE >> P::PSH) + 1 + TwDims<L>::NLO + TwDims<L>::NHI +
                                          (size_t)G * (OLO + OHI);
     // FP32: + the exp(2 pi i m/1024) table of the per-element phases
-    static constexpr size_t smem_bytes = smem_elems * sizeof(cx<T>) + (sizeof(T) == 4 ? EXPI_TAB * sizeof(float2) : 0);
+    static constexpr size_t smem_bytes = smem_elems * sizeof(cx<T>);
 };
 
 template <typename T, int L> struct KRGeom {
@@ -83,6 +83,14 @@ template <typename T, int L> struct KRGeom {
 };
 
 __device__ __forceinline__ long long signed_k(long long k, long long N) { return k < (N >> 1) ? k : k - N; }
+
+// Kahan-compensated s += v (c carries the lost low-order part).
+template <typename T> __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
 
 template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 : 1)
@@ -105,15 +113,12 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
     C* tlo = thi + TwDims<L>::NHI;
     C* olo = tlo + TwDims<L>::NLO;  // [OLO][G]
     C* ohi = olo + G * Gm::OLO;     // [OHI][G]
-    float2* etab = reinterpret_cast<float2*>(ohi + G * Gm::OHI);
     const int tid = threadIdx.x;
     const long long col0 = (long long)blockIdx.x * G;
     const int N1m = p.N1 - 1;
-    constexpr bool FAST = sizeof(T) == 4;  // FP32: finite-difference phases + table exp
+    constexpr bool FAST = sizeof(T) == 4;  // FP32: finite-difference phases + polynomial exp
 
     tw_init<T, L>(thi, tlo, tid, NT);
-    if constexpr (FAST && (MODE == KC_MPA_PRE || MODE == KC_MPA_POST || MODE == KC_SS_STEP))
-        expi_tab_init(etab, tid, NT);
     if constexpr (INV) {
         // W_N^{-n2 k1} for the tile's columns: olo[m][g] = W^{-k1 m}, ohi[h][g] = W^{-k1 32 h}
         for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
             if constexpr (MODE == KC_MPA_PRE) {
                 // MPA step 2: A_hat_j = psi_j exp(i beta(w, z_j) + int G)
                 C ph;
-                if constexpr (FAST) ph = expi_turns_tab(th[r], etab);
+                if constexpr (FAST) ph = expi_turns_poly(th[r]);
                 else ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
                 v = cscale(cmul(v, ph), (T)nc.pre);
             }
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
             for (int r = 0; r < XF::RL; ++r) {
                 const int row = j + r * (L / XF::RL);
                 C ph;
-                if constexpr (FAST) ph = expi_turns_tab(th[r], etab);
+                if constexpr (FAST) ph = expi_turns_poly(th[r]);
                 else ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), p.flow));
                 vm[q][r] = cscale(cmul(vm[q][r], ph), (T)p.flow.pre);
             }
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
             if constexpr (MODE == KC_MPA_POST) {
                 // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
                 C ph;
-                if constexpr (FAST) ph = expi_turns_tab(th[r], etab);
+                if constexpr (FAST) ph = expi_turns_poly(th[r]);
                 else ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
                 v = cscale(cmul(v, cconj(ph)), (T)nc.post);
             }
@@ -321,6 +326,231 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? 2 
     }
 }
 
+// ------------------------------------------------------------------
+// Wavefront column pass (FP32): one CTA owns one column tile of one block
+// of B consecutive nodes at one Picard level and walks the nodes in order:
+//   forward column DFTs (finishing F[|A_j|^2 A_j])
+//   V_j = F[...] exp(-i beta_j) sigma_j dz / exp(int G)          (Eq. (6))
+//   psi^{(n+1)}_j = psi_0 + i (R + V_j/2),  R += V_j              (step 5)
+//   A_hat = psi^{(n+1)}_j exp(i beta_j + int G) and the inverse column DFTs
+//   of level n+1 (steps 2-3), written back over the node's buffer.
+// R (the trapezoid running sum of this level, Kahan-compensated, the
+// compensation kept in shared memory) persists across the block in
+// registers and across blocks in global memory.  The phase of node j is
+// evaluated once for both directions.  On the last level the inverse
+// transform is instead that of the next block's first iteration for the
+// node S B further on (psi_0 exp(i beta + int G)), and the node-M value
+// psi_0 + i (R + V_M/2) is emitted in FP64 for step 7.
+struct KCWJob {
+    int level, slot, node_first, n_nodes, head_first, n_head, last;
+};
+
+struct KCWParams {
+    float2* work;           // slots of B node buffers
+    long long slot_stride;  // elements between slots
+    long long N;
+    int logN, N1, logN1, M;
+    const NodeC* nodes;     // this interval's constants, node j at nodes[j]
+    const float2* psi0;     // psi_0 (complex64, natural order)
+    const float2* v0;       // V_0 (complex64) for blocks that start at node 1
+    float2* Rg;             // [levels][N] running sums
+    float2* Cg;             // [levels][N] Kahan compensations
+    double2* D;             // R + V_M/2 at node M (so psi_M = psi_0 + i D), FP64
+    int n_jobs;
+    KCWJob job[8];  // one per Picard level (n_iter <= 8)
+};
+
+template <int L> struct KCWGeom {
+    typedef Tiling<float, 2> P;
+    // tiles of at most 8192 elements (32- or 64-byte row segments): the
+    // running sums and compensations take 16 bytes per element of shared memory
+    static constexpr int G = (8192 / L) > 4 ? (8192 / L) : 4, TE = G * L, NT = TE / P::E;
+    static constexpr int OSH = 5, OLO = L < 32 ? L : 32, OHI = L > 32 ? L / 32 : 1;
+    // float2 offset of the running sums (float4 per element): rounded up to
+    // an even count so the array starts on a 16-byte boundary
+    static constexpr size_t RC_OFF =
+        (((size_t)TE + (TE >> P::PSH) + 1 + TwDims<L>::NLO + TwDims<L>::NHI + (size_t)G * (OLO + OHI)) + 1) & ~(size_t)1;
+    static constexpr size_t smem_bytes = RC_OFF * sizeof(float2) + (size_t)TE * sizeof(float4);
+};
+
+// The node loop of one job; LAST selects the last Picard level (heads of
+// the next blocks instead of the next level, and the node-M output).
+template <int L, bool LAST>
+__device__ __forceinline__ void kcw_job(const KCWParams& p, const KCWJob& job, float2* s, const float2* thi,
+                                        const float2* tlo, const float2* olo, const float2* ohi, float4* rc,
+                                        int col0) {
+    typedef float2 C;
+    typedef KCWGeom<L> Gm;
+    typedef Tiling<float, 2> P;
+    constexpr int G = Gm::G, NT = Gm::NT;
+    typedef Xform<float, L, G, NT, P::RMAX, +1, LAYOUT_COL, P::PSH, true> XF;
+    typedef Xform<float, L, G, NT, P::RMAX, -1, LAYOUT_COL, P::PSH, false> XI;
+    constexpr int QJ = XF::QL, RJ = XF::RL;
+    const int tid = threadIdx.x;
+    const long long N = p.N;
+    const long long D = (long long)p.N1 * (L / RJ);
+
+    // running sums of this level (and Kahan compensations) for the thread's
+    // junction elements, kept in shared memory across the node loop
+#pragma unroll
+    for (int q = 0; q < QJ; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, RJ>(tid + q * NT, j, g);
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+            const long long k = (col0 + g) + (long long)(j + r * (L / RJ)) * p.N1;
+            float4 e;
+            if (job.node_first == 1) {
+                const float2 v = p.v0[k];
+                e = make_float4(0.5f * v.x, 0.5f * v.y, 0.f, 0.f);  // V_0 / 2
+            } else {
+                const float2 rv = p.Rg[(long long)job.level * N + k], cv = p.Cg[(long long)job.level * N + k];
+                e = make_float4(rv.x, rv.y, cv.x, cv.y);
+            }
+            rc[(q * RJ + r) * NT + tid] = e;
+        }
+    }
+
+    float2* slot = p.work + (long long)job.slot * p.slot_stride;
+    for (int i = 0; i < job.n_nodes; ++i) {
+        const int jn = job.node_first + i;
+        float2* buf = slot + (long long)i * N;
+        // ---- forward column DFTs of node jn (first pass straight from global)
+        C vin[XF::Q0][XF::R0];
+#pragma unroll
+        for (int q = 0; q < XF::Q0; ++q) {
+            int j, g;
+            bmap<LAYOUT_COL, L, G, XF::R0>(tid + q * NT, j, g);
+            const C* src = buf + col0 + g;
+#pragma unroll
+            for (int r = 0; r < XF::R0; ++r) vin[q][r] = src[(long long)(j + r * (L / XF::R0)) * p.N1];
+        }
+        C v[QJ][RJ];
+        XF::run(vin, v, s, thi, tlo);
+        const bool head = LAST && i < job.n_head;
+        const NodeC nc = p.nodes[jn];
+        const float post = (float)nc.post;
+#pragma unroll
+        for (int q = 0; q < QJ; ++q) {
+            int j, g;
+            bmap<LAYOUT_COL, L, G, RJ>(tid + q * NT, j, g);
+            const long long c = col0 + g;
+            // elements in s order: s = -RJ/2 .. RJ/2-1, r = (s + RJ) mod RJ, k' = c + N1 (j + s L/RJ)
+            const long long kf = c + (long long)p.N1 * j - (long long)(RJ / 2) * D;
+            PhaseRun pr(kf, D, nc);
+            if constexpr (!LAST) {
+                const float pre = (float)nc.pre;
+#pragma unroll
+                for (int t = 0; t < RJ; ++t) {
+                    const int r = (t + RJ / 2) % RJ;
+                    const long long k = c + (long long)(j + r * (L / RJ)) * p.N1;
+                    const C ph = expi_turns_poly(pr.next());
+                    // V_j (Eq. (6)) and psi^{(n+1)}_j = psi_0 + i (R + V_j/2) (step 5)
+                    const C V = cscale(cmul(v[q][r], cconj(ph)), post);
+                    float4 e = rc[(q * RJ + r) * NT + tid];  // (R, compensation)
+                    const float2 p0 = p.psi0[k];
+                    const float sx = (e.x - e.z) + 0.5f * V.x, sy = (e.y - e.w) + 0.5f * V.y;
+                    kahan_add(e.x, e.z, V.x);
+                    kahan_add(e.y, e.w, V.y);
+                    rc[(q * RJ + r) * NT + tid] = e;
+                    // step 2 of the next iteration at the same node
+                    v[q][r] = cscale(cmul(make_float2(p0.x - sy, p0.y + sx), ph), pre);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < RJ; ++t) {
+                    const int r = (t + RJ / 2) % RJ;
+                    const C ph = expi_turns_poly(pr.next());
+                    const C V = cscale(cmul(v[q][r], cconj(ph)), post);
+                    float4 e = rc[(q * RJ + r) * NT + tid];  // (R, compensation)
+                    if (jn == p.M) {
+                        // R + V_M/2 before adding V_M: psi_M = psi_0 + i D (FP64)
+                        const long long k = c + (long long)(j + r * (L / RJ)) * p.N1;
+                        p.D[k] = make_double2(((double)e.x - (double)e.z) + 0.5 * (double)V.x,
+                                              ((double)e.y - (double)e.w) + 0.5 * (double)V.y);
+                    }
+                    kahan_add(e.x, e.z, V.x);
+                    kahan_add(e.y, e.w, V.y);
+                    rc[(q * RJ + r) * NT + tid] = e;
+                }
+                if (head) {
+                    // first iteration of the node S B further on: psi_0 exp(i beta + int G)
+                    const NodeC nh = p.nodes[job.head_first + i];
+                    const float preh = (float)nh.pre;
+                    PhaseRun ph2(kf, D, nh);
+#pragma unroll
+                    for (int t = 0; t < RJ; ++t) {
+                        const int r = (t + RJ / 2) % RJ;
+                        const long long k = c + (long long)(j + r * (L / RJ)) * p.N1;
+                        v[q][r] = cscale(cmul(p.psi0[k], expi_turns_poly(ph2.next())), preh);
+                    }
+                }
+            }
+        }
+        if (!LAST || head) {
+            // ---- inverse column DFTs, four-step factor, store over the node buffer
+            C vo[XI::QL][XI::RL];
+            XI::run(v, vo, s, thi, tlo);
+#pragma unroll
+            for (int q = 0; q < XI::QL; ++q) {
+                int j, g;
+                bmap<LAYOUT_COL, L, G, XI::RL>(tid + q * NT, j, g);
+                C* dst = buf + col0 + g;
+#pragma unroll
+                for (int r = 0; r < XI::RL; ++r) {
+                    const int row = j + r * (L / XI::RL);
+                    C w = olo[(row & (Gm::OLO - 1)) * G + g];
+                    if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
+                    dst[(long long)row * p.N1] = cmul(vo[q][r], w);
+                }
+            }
+        }
+    }
+
+    // ---- running sums back to global memory for the next block
+#pragma unroll
+    for (int q = 0; q < QJ; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, RJ>(tid + q * NT, j, g);
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+            const long long k = (col0 + g) + (long long)(j + r * (L / RJ)) * p.N1;
+            const float4 e = rc[(q * RJ + r) * NT + tid];
+            p.Rg[(long long)job.level * N + k] = make_float2(e.x, e.y);
+            p.Cg[(long long)job.level * N + k] = make_float2(e.z, e.w);
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(KCWGeom<L>::NT, 1) kcw_kernel(const KCWParams p) {
+    typedef float2 C;
+    typedef KCWGeom<L> Gm;
+    typedef Tiling<float, 2> P;
+    constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    C* olo = tlo + TwDims<L>::NLO;  // [OLO][G]
+    C* ohi = olo + G * Gm::OLO;     // [OHI][G]
+    float4* rc = reinterpret_cast<float4*>(s + Gm::RC_OFF);  // [E][NT] (R, compensation), 16-B aligned
+    const int tid = threadIdx.x;
+    const KCWJob job = p.job[blockIdx.y];
+    const int col0 = blockIdx.x * G;  // column within a node (tiles never straddle nodes)
+
+    tw_init<float, L>(thi, tlo, tid, NT);
+    for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
+        const int g = i % G, m = i / G;
+        const long long k1 = col0 + g;
+        if (m < Gm::OLO) olo[m * G + g] = expi_ratio<float>(-k1 * m, p.logN);
+        else ohi[(m - Gm::OLO) * G + g] = expi_ratio<float>(-k1 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+    }
+    __syncthreads();
+    if (job.last) kcw_job<L, true>(p, job, s, thi, tlo, olo, ohi, rc, col0);
+    else kcw_job<L, false>(p, job, s, thi, tlo, olo, ohi, rc, col0);
+}
+
 // Eq. (6) for every frequency k: running trapezoid sum over nodes j = 1..M
 //   psi^{(n+1)}_l = psi_0 + i (V_0/2 + sum_{j=1}^{l-1} V_j + V_l/2),
 // with V_j stored in psi[j] (node 0 holds V_0).  FP32 sums are Kahan-
@@ -341,13 +571,6 @@ template <typename T> struct ScanParams {
     double gain;
     unsigned int* err;
 };
-
-template <typename T> __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
-    const T y = v - c;
-    const T t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {

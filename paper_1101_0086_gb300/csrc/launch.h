@@ -15,7 +15,7 @@ extern std::atomic<long long> g_launches;
 // default; enabled through mpa_profile).
 enum {
     PK_KC_MPA_PRE = 0, PK_KC_MPA_POST, PK_KC_SS, PK_KC_FFT, PK_KR_MPA, PK_KR_SS, PK_KR_FFT, PK_SCAN, PK_AUX,
-    PK_COUNT
+    PK_KCW, PK_COUNT
 };
 extern std::atomic<bool> g_prof_on;
 void prof_begin(cudaStream_t st);
@@ -37,6 +37,13 @@ template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, cudaStream
 template <typename T> cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long C, cudaStream_t st);
 template <typename T> cudaError_t to_state_launch(const cx<T>* in, double2* state, cx<T>* copy, long long N, cudaStream_t st);
 template <typename T> cudaError_t from_state_launch(const double2* state, cx<T>* out, long long N, cudaStream_t st);
+
+// Wavefront column pass (FP32): columns per tile for column length 2^logL,
+// the launch, and the step-7 kernel that follows a wavefront interval.
+int kcw_tile_cols(int logL);
+cudaError_t kcw_launch(int logL, const KCWParams& p, cudaStream_t st);
+cudaError_t reconstruct_launch(double2* state, float2* psi0c, const double2* D, const NodeC& nodeM, double gain,
+                               long long N, unsigned int* err, double2* out, cudaStream_t st);
 
 // Grid of a column pass over ncols columns of column length L.
 template <typename T> long long kc_blocks(int logL, long long ncols);

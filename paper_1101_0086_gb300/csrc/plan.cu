@@ -203,6 +203,10 @@ struct mpa_plan {
     std::vector<NodeC> nodes;   // n_types x (M+1)
     size_t csize;               // bytes per complex sample
     size_t off_psi, off_state, off_psi0c, off_nodes, off_err, ws_need;
+    // wavefront schedule (FP32): S = n_iter slots of B node buffers
+    bool wf = false;
+    int B = 0;
+    size_t off_work = 0, off_y0 = 0, off_R = 0, off_C = 0, off_D = 0;
     unsigned char* ws = nullptr;
     size_t ws_bytes = 0;
 };
@@ -272,6 +276,92 @@ int run_interval(mpa_plan* p, int type, double gain, int scan_mode, double2* out
     return MPA_OK;
 }
 
+// Wavefront schedule of one interval (FP32): node blocks of B move through
+// the n_iter levels one step at a time; at step s level n works on block
+// s - n.  Each step is one row pass per active block and one wavefront
+// column pass for all active blocks.  Results equal the level-synchronous
+// schedule up to the summation order of the FP32 sums.
+int run_interval_wf(mpa_plan* p, int type, double gain, double2* out, cudaStream_t st) {
+    const Split& s = p->sp;
+    const long long N = s.N;
+    const int M = p->M, S = p->n_iter, B = p->B;
+    const int nb = (M + B - 1) / B;
+    float2* work = reinterpret_cast<float2*>(p->ws + p->off_work);
+    float2* y0 = reinterpret_cast<float2*>(p->ws + p->off_y0);
+    float2* psi0c = reinterpret_cast<float2*>(p->ws + p->off_psi0c);
+    double2* state = reinterpret_cast<double2*>(p->ws + p->off_state);
+    const NodeC* nodes = reinterpret_cast<const NodeC*>(p->ws + p->off_nodes) + (size_t)type * (M + 1);
+    unsigned int* err = reinterpret_cast<unsigned int*>(p->ws + p->off_err);
+    const long long slot_stride = (long long)B * N;
+    auto nn = [&](int b) { return (b < nb) ? ((b + 1) * B <= M ? B : M - b * B) : 0; };
+    auto kc = [&](int mode, const float2* src, long long src_stride, float2* dst, int first, int count) {
+        KCParams<float> c{};
+        c.src = src;
+        c.src_stride = src_stride;
+        c.dst = dst;
+        c.dst_stride = N;
+        c.N = N;
+        c.logN = s.logN;
+        c.N1 = (int)s.N1;
+        c.logN1 = s.logN1;
+        c.ncols = (long long)count * s.N1;
+        c.nodes = nodes + first;
+        return kc_launch<float>(mode, s.logN2, c, st);
+    };
+    auto kr = [&](float2* data, int count) {
+        KRParams<float> r{data, (long long)count * s.N2, N, s.logN, (int)s.N2, (float)(1.0 / (double)N), 0.f};
+        return kr_launch<float>(KR_MPA, s.logN1, r, st);
+    };
+    // node 0: V_0 (the same for every iteration)
+    MPA_TRY(kc(KC_MPA_PRE, psi0c, 0, y0, 0, 1));
+    MPA_TRY(kr(y0, 1));
+    MPA_TRY(kc(KC_MPA_POST, y0, N, y0, 0, 1));
+    // first iteration inputs of the first S blocks
+    for (int b = 0; b < S && b < nb; ++b) MPA_TRY(kc(KC_MPA_PRE, psi0c, 0, work + (long long)(b % S) * slot_stride, 1 + b * B, nn(b)));
+    KCWParams w{};
+    w.work = work;
+    w.slot_stride = slot_stride;
+    w.N = N;
+    w.logN = s.logN;
+    w.N1 = (int)s.N1;
+    w.logN1 = s.logN1;
+    w.M = M;
+    w.nodes = nodes;
+    w.psi0 = psi0c;
+    w.v0 = y0;
+    w.Rg = reinterpret_cast<float2*>(p->ws + p->off_R);
+    w.Cg = reinterpret_cast<float2*>(p->ws + p->off_C);
+    w.D = reinterpret_cast<double2*>(p->ws + p->off_D);
+    for (int step = 0; step < nb + S - 1; ++step) {
+        w.n_jobs = 0;
+        for (int n = 0; n < S; ++n) {
+            const int b = step - n;
+            if (b < 0 || b >= nb) continue;
+            KCWJob& j = w.job[w.n_jobs++];
+            j.level = n;
+            j.slot = b % S;
+            j.node_first = 1 + b * B;
+            j.n_nodes = nn(b);
+            j.last = (n == S - 1);
+            j.head_first = 1 + (b + S) * B;
+            j.n_head = j.last ? nn(b + S) : 0;
+        }
+        // row passes (steps 3-4): one launch over all slots when every slot is
+        // busy (the slots are contiguous), else one per active block
+        if (w.n_jobs == S) {
+            MPA_TRY(kr(work, S * B));
+        } else {
+            for (int i = 0; i < w.n_jobs; ++i)
+                MPA_TRY(kr(work + (long long)w.job[i].slot * slot_stride, w.job[i].n_nodes));
+        }
+        MPA_TRY(kcw_launch(s.logN2, w, st));
+    }
+    // step 7 (or psi_M only)
+    const NodeC nodeM = p->nodes[(size_t)type * (M + 1) + M];
+    MPA_TRY(reconstruct_launch(state, psi0c, w.D, nodeM, gain, N, err, out, st));
+    return MPA_OK;
+}
+
 template <typename T>
 int propagate_t(mpa_plan* p, void* field, double z_from, double z_to, cudaStream_t st) {
     const Split& s = p->sp;
@@ -299,7 +389,8 @@ int propagate_t(mpa_plan* p, void* field, double z_from, double z_to, cudaStream
     if (rc) return rc;
     MPA_TRY(to_state_launch<T>(psi, state, sizeof(T) == 4 ? psi0c : nullptr, s.N, st));
     for (long q = 0; q < n_int; ++q) {
-        rc = run_interval<T>(p, types[(size_t)q], gains[(size_t)q], 1, nullptr, st);
+        rc = p->wf ? run_interval_wf(p, types[(size_t)q], gains[(size_t)q], nullptr, st)
+                   : run_interval<T>(p, types[(size_t)q], gains[(size_t)q], 1, nullptr, st);
         if (rc) return rc;
     }
     // A(z_to) = F^-1[A_hat]
@@ -318,6 +409,7 @@ int interval_t(mpa_plan* p, const void* psi0, void* psiM, double z0, cudaStream_
     cx<T>* psi0c = reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c);
     MPA_TRY(cudaMemcpyAsync(state, psi0, (size_t)p->sp.N * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     if (sizeof(T) == 4) MPA_TRY(from_state_launch<T>(state, psi0c, p->sp.N, st));
+    if (p->wf) return run_interval_wf(p, t, 1.0, reinterpret_cast<double2*>(psiM), st);
     return run_interval<T>(p, t, 1.0, 2, reinterpret_cast<double2*>(psiM), st);
 }
 
@@ -378,6 +470,7 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
     *out = nullptr;
     if (prm->precision != MPA_FP32 && prm->precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
     if (!(prm->T_ps > 0.0) || !(prm->L_km > 0.0) || prm->M < 1 || prm->n_iter < 1) return MPA_ERR_INVALID_ARG;
+    if (prm->schedule < MPA_SCHEDULE_AUTO || prm->schedule > MPA_SCHEDULE_WAVEFRONT) return MPA_ERR_INVALID_ARG;
     mpa_plan* p = new (std::nothrow) mpa_plan();
     if (!p) return MPA_ERR_INVALID_ARG;
     int rc = p->map.init(map);
@@ -418,6 +511,35 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
     }
     p->csize = p->prec == MPA_FP32 ? sizeof(float2) : sizeof(double2);
     const size_t N = (size_t)p->sp.N;
+    // schedule: the wavefront needs FP32 and whole column tiles per node
+    // (column length >= 128 keeps its shared memory within the 227 KB limit)
+    p->wf = prm->schedule == MPA_SCHEDULE_WAVEFRONT && p->prec == MPA_FP32 && p->n_iter <= 8 && p->sp.logN2 >= 7 &&
+            p->sp.N1 >= kcw_tile_cols(p->sp.logN2) && p->sp.N1 % kcw_tile_cols(p->sp.logN2) == 0;
+    if (prm->schedule == MPA_SCHEDULE_WAVEFRONT && !p->wf) {
+        delete p;
+        return MPA_ERR_INVALID_ARG;
+    }
+    if (p->wf) {
+        // B nodes per block: about 256 MiB of node buffers over the n_iter slots
+        const size_t per = (size_t)p->n_iter * N * sizeof(float2);
+        long b = (long)((256ull << 20) / per);
+        b = b < 1 ? 1 : b > 16 ? 16 : b;
+        p->B = (int)(b < M ? b : M);
+        const size_t S = (size_t)p->n_iter;
+        p->off_work = 0;
+        p->off_y0 = align256(p->off_work + S * (size_t)p->B * N * sizeof(float2));
+        p->off_R = align256(p->off_y0 + N * sizeof(float2));
+        p->off_C = align256(p->off_R + S * N * sizeof(float2));
+        p->off_D = align256(p->off_C + S * N * sizeof(float2));
+        p->off_state = align256(p->off_D + N * sizeof(double2));
+        p->off_psi0c = align256(p->off_state + N * sizeof(double2));
+        p->off_psi = p->off_work;  // scratch of the entry/exit transforms
+        p->off_nodes = align256(p->off_psi0c + N * sizeof(float2));
+        p->off_err = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
+        p->ws_need = align256(p->off_err + sizeof(unsigned int));
+        *out = p;
+        return MPA_OK;
+    }
     p->off_psi = 0;
     p->off_state = align256(p->off_psi + (size_t)(M + 1) * N * p->csize);
     p->off_psi0c = align256(p->off_state + N * sizeof(double2));
@@ -563,7 +685,7 @@ int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* byte
 
 const char* mpa_profile_kind_name(int kind) {
     static const char* names[PK_COUNT] = {"kc_mpa_pre", "kc_mpa_post", "kc_ss_step", "kc_fft", "kr_mpa",
-                                          "kr_ss", "kr_fft", "scan", "aux"};
+                                          "kr_ss", "kr_fft", "scan", "aux", "kc_wavefront"};
     return (kind >= 0 && kind < PK_COUNT) ? names[kind] : nullptr;
 }
 

@@ -18,6 +18,7 @@ _SO = os.path.join(_HERE, "libmpa.so")
 _lib: Optional[ctypes.CDLL] = None
 
 FP32, FP64 = 0, 1
+SCHEDULES = {"auto": 0, "level": 1, "wavefront": 2}
 _STATUS_NONFINITE = 6
 
 
@@ -37,7 +38,8 @@ class _FiberMap(ctypes.Structure):
 
 class _PlanParams(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("T_ps", ctypes.c_double), ("L_km", ctypes.c_double),
-                ("M", ctypes.c_int32), ("n_iter", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("M", ctypes.c_int32), ("n_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
@@ -134,13 +136,13 @@ class Plan:
     """An MPA plan (``mpa_plan_create``) with its caller-owned workspace."""
 
     def __init__(self, fiber, N: int, T_ps: float, L_km: float, M: int, n_iter: int,
-                 precision="fp32", device="cuda", workspace: Optional[torch.Tensor] = None):
+                 precision="fp32", device="cuda", workspace: Optional[torch.Tensor] = None, schedule="auto"):
         L = lib()
         self.prec = _prec(precision)
         self.N = int(N)
         self.dtype = _cdtype(self.prec)
         self._fm, self._segs = _fiber_struct(fiber)
-        prm = _PlanParams(self.N, float(T_ps), float(L_km), int(M), int(n_iter), self.prec)
+        prm = _PlanParams(self.N, float(T_ps), float(L_km), int(M), int(n_iter), self.prec, SCHEDULES[schedule])
         h = ctypes.c_void_p()
         _check(L.mpa_plan_create(ctypes.byref(self._fm), ctypes.byref(prm), ctypes.byref(h)), "mpa_plan_create")
         self._h = h

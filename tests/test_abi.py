@@ -48,9 +48,9 @@ def test_status_strings(L):
     assert L.mpa_status_string(99) == b"unknown status"
 
 
-def _plan(L, fiber, N, T, Lkm, M, n, prec=0):
+def _plan(L, fiber, N, T, Lkm, M, n, prec=0, schedule=0):
     fm, segs = mpa._fiber_struct(fiber)
-    prm = mpa._PlanParams(N, T, Lkm, M, n, prec)
+    prm = mpa._PlanParams(N, T, Lkm, M, n, prec, schedule)
     h = ctypes.c_void_p()
     rc = L.mpa_plan_create(ctypes.byref(fm), ctypes.byref(prm), ctypes.byref(h))
     return rc, h
@@ -58,12 +58,28 @@ def _plan(L, fiber, N, T, Lkm, M, n, prec=0):
 
 def test_plan_validation_is_host_only(L):
     fib = dm_map(4)
-    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 710, 3)
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 710, 3, schedule=1)
     assert rc == 0
     n = ctypes.c_size_t()
     assert L.mpa_plan_workspace_size(h, ctypes.byref(n)) == 0
-    # (M+1) node spectra of complex64 + FP64 state + complex64 copy + tables
+    # level-synchronous: (M+1) node spectra of complex64 + FP64 state + complex64 copy + tables
     assert n.value >= 711 * (1 << 14) * 8 + (1 << 14) * 24
+    L.mpa_plan_destroy(h)
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 710, 3, schedule=2)
+    assert rc == 0
+    nw = ctypes.c_size_t()
+    assert L.mpa_plan_workspace_size(h, ctypes.byref(nw)) == 0
+    # wavefront: 3 slots of 16 node buffers + V_0 + 2 x 3 running-sum arrays + FP64 D and state + copy
+    assert nw.value >= (3 * 16 + 1 + 6) * (1 << 14) * 8 + (1 << 14) * 40 and nw.value < n.value
+    L.mpa_plan_destroy(h)
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 710, 3, schedule=0)  # AUTO: level-synchronous
+    na = ctypes.c_size_t()
+    assert L.mpa_plan_workspace_size(h, ctypes.byref(na)) == 0 and na.value == n.value
+    L.mpa_plan_destroy(h)
+    assert _plan(L, fib, 1 << 10, 800.0, 50.0, 10, 3, schedule=2)[0] == 1  # too small for whole column tiles
+    assert _plan(L, fib, 1 << 14, 12800.0, 50.0, 10, 3, prec=1, schedule=2)[0] == 1  # FP32 only
+    assert _plan(L, fib, 1 << 14, 12800.0, 50.0, 10, 3, schedule=3)[0] == 1
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 710, 3)
     # propagate without workspace is refused before any CUDA call
     assert L.mpa_propagate(h, ctypes.c_void_p(16), 0.0, 50.0, None) == 3
     L.mpa_plan_destroy(h)

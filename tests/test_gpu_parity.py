@@ -58,20 +58,24 @@ def small_map(sigma=1.3, gamma_db=0.2):
                     gamma_from_db_per_km(gamma_db), 10.0, 10)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec,schedule", [("fp32", "level"), ("fp32", "wavefront"), ("fp64", "auto")])
 @pytest.mark.parametrize("N,Lk,Mn,n_iter,z0", [
     (1 << 10, 10.0, 20, 3, 0.0),      # one interval = one DM period (node on the 8 km jump)
     (1 << 12, 2.0, 36, 3, 8.0),       # ragged node batch, interval in the +85 segment
     (1 << 12, 5.0, 1, 1, 5.0),        # degenerate: M = 1, one iteration
     (1 << 14, 10.0, 50, 4, 20.0),     # several tiles per node, interval type 0 of period 3
+    (1 << 14, 2.0, 37, 1, 4.0),       # one iteration (wavefront: a single slot)
+    (1 << 16, 5.0, 45, 5, 0.0),       # five iterations, ragged last block
 ])
-def test_interval_matches_oracle(M, prec, N, Lk, Mn, n_iter, z0):
+def test_interval_matches_oracle(M, prec, schedule, N, Lk, Mn, n_iter, z0):
     fib = small_map()
     T = 800.0 * N / 1024
     A0 = wdm_field(N, T, 2, 50.0, 8 * N // 1024, 30.0, 20.0, "qpsk", seed=N + Mn)
     psi0 = oracle.fft(A0, +1)
     ref = oracle.mpa_interval(psi0, fib, T, z0, Lk, Mn, n_iter)
-    plan = M.Plan(fib, N, T, Lk, Mn, n_iter, precision=prec)
+    if schedule == "wavefront" and N < (1 << 14):
+        schedule = "level"  # the wavefront needs N >= 2^14
+    plan = M.Plan(fib, N, T, Lk, Mn, n_iter, precision=prec, schedule=schedule)
     got = host(plan.interval(dev(psi0, "fp64"), z0))
     err = oracle.rel_l2(got, ref)
     assert err < TOL[prec], err
@@ -108,6 +112,21 @@ def test_linear_limit_is_exact(M, prec):
     X = np.fft.ifft(A0) * N * np.exp(1j * (0.5 * w**2 * I2 + w**3 * I3 / 6)) * math.exp(-g * 50 + 5 * 10 * g)
     ref = np.fft.fft(X) / N
     assert oracle.rel_l2(got, ref) < (1e-12 if prec == "fp64" else 5e-6)
+
+
+@pytest.mark.parametrize("N,Mn,n_iter", [(1 << 14, 40, 3), (1 << 16, 71, 2), (1 << 18, 17, 4)])
+def test_wavefront_schedule_equals_level_schedule(M, N, Mn, n_iter):
+    # the two launch schedules compute the same Eq. (6); only the FP32
+    # summation order differs
+    fib = small_map()
+    T = 800.0 * N / 1024
+    A0 = wdm_field(N, T, 3, 50.0, 8 * N // 1024, 30.0, 10.0, "qpsk", seed=N)
+    a = M.Plan(fib, N, T, 10.0, Mn, n_iter, precision="fp32", schedule="level")
+    b = M.Plan(fib, N, T, 10.0, Mn, n_iter, precision="fp32", schedule="wavefront")
+    fa = host(a.propagate(dev(A0, "fp32"), 0.0, 30.0))
+    fb = host(b.propagate(dev(A0, "fp32"), 0.0, 30.0))
+    assert oracle.rel_l2(fb, fa) < 1e-5
+    assert b.status()
 
 
 def test_grid_errors_are_reported(M):
