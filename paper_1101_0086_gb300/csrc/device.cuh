@@ -38,31 +38,45 @@ template <int S, class C> __device__ __forceinline__ C mul_dir(C a, C w) {
 }
 
 // ------------------------------------------------------------------ DFTs
-// cos and sin of multiples of 2 pi/16 (closed forms: cos(pi/8) =
-// sqrt(2+sqrt(2))/2, cos(pi/4) = sqrt(2)/2, sin(pi/8) = sqrt(2-sqrt(2))/2).
+// cos and sin of multiples of 2 pi/32 (closed forms: cos(pi/4) = sqrt(2)/2,
+// cos(pi/8) = sqrt(2+sqrt(2))/2, sin(pi/8) = sqrt(2-sqrt(2))/2,
+// cos(pi/16) = sqrt(2+sqrt(2+sqrt(2)))/2, sin(pi/16) = sqrt(2-sqrt(2+sqrt(2)))/2,
+// cos(3pi/16) = sqrt(2+sqrt(2-sqrt(2)))/2, sin(3pi/16) = sqrt(2-sqrt(2-sqrt(2)))/2).
+#define MPA_COS_PI_4 0.70710678118654752440
 #define MPA_COS_PI_8 0.92387953251128675613
 #define MPA_SIN_PI_8 0.38268343236508977173
-#define MPA_COS_PI_4 0.70710678118654752440
+#define MPA_COS_PI_16 0.98078528040323044913
+#define MPA_SIN_PI_16 0.19509032201612826785
+#define MPA_COS_3PI_16 0.83146961230254523708
+#define MPA_SIN_3PI_16 0.55557023301960222474
 
-// v * exp(S 2 pi i K/R), R <= 16, 0 <= K < R/2 (compile-time special cases)
+// (cos, sin) of 2 pi m/32 for 0 < m < 16, m not a multiple of 4
+template <int M32> struct Cs32 {
+    static constexpr double c = (M32 == 1) ? MPA_COS_PI_16 : (M32 == 2) ? MPA_COS_PI_8 : (M32 == 3) ? MPA_COS_3PI_16
+                              : (M32 == 5) ? MPA_SIN_3PI_16 : (M32 == 6) ? MPA_SIN_PI_8 : (M32 == 7) ? MPA_SIN_PI_16
+                              : (M32 == 9) ? -MPA_SIN_PI_16 : (M32 == 10) ? -MPA_SIN_PI_8 : (M32 == 11) ? -MPA_SIN_3PI_16
+                              : (M32 == 13) ? -MPA_COS_3PI_16 : (M32 == 14) ? -MPA_COS_PI_8 : -MPA_COS_PI_16;
+    static constexpr double s = (M32 == 1) ? MPA_SIN_PI_16 : (M32 == 2) ? MPA_SIN_PI_8 : (M32 == 3) ? MPA_SIN_3PI_16
+                              : (M32 == 5) ? MPA_COS_3PI_16 : (M32 == 6) ? MPA_COS_PI_8 : (M32 == 7) ? MPA_COS_PI_16
+                              : (M32 == 9) ? MPA_COS_PI_16 : (M32 == 10) ? MPA_COS_PI_8 : (M32 == 11) ? MPA_COS_3PI_16
+                              : (M32 == 13) ? MPA_SIN_3PI_16 : (M32 == 14) ? MPA_SIN_PI_8 : MPA_SIN_PI_16;
+};
+
+// v * exp(S 2 pi i K/R), R <= 32, 0 <= K < R/2 (compile-time special cases)
 template <int R, int K, int S, class C> __device__ __forceinline__ C tw_const(C v) {
     typedef decltype(v.x) T;
-    constexpr int K16 = K * (16 / R);
-    if constexpr (K16 == 0) {
+    constexpr int M32 = K * (32 / R);
+    if constexpr (M32 == 0) {
         return v;
-    } else if constexpr (K16 == 4) {
+    } else if constexpr (M32 == 8) {
         return mul_si<S>(v);
-    } else if constexpr (K16 == 2 || K16 == 6) {
+    } else if constexpr (M32 == 4 || M32 == 12) {
         const T c = (T)MPA_COS_PI_4;
-        constexpr T re = (K16 == 2) ? T(1) : T(-1);
+        constexpr T re = (M32 == 4) ? T(1) : T(-1);
         // (re + S i) c
         return mkc(c * (re * v.x - T(S) * v.y), c * (re * v.y + T(S) * v.x));
     } else {
-        const T a = (T)MPA_COS_PI_8, b = (T)MPA_SIN_PI_8;
-        // K16 = 1: (a, b); 3: (b, a); 5: (-b, a); 7: (-a, b)
-        const T cr = (K16 == 1) ? a : (K16 == 3) ? b : (K16 == 5) ? -b : -a;
-        const T ci = (K16 == 1 || K16 == 7) ? b : a;
-        const T si = T(S) * ci;
+        const T cr = (T)Cs32<M32>::c, si = T(S) * (T)Cs32<M32>::s;
         return mkc(v.x * cr - v.y * si, v.x * si + v.y * cr);
     }
 }
@@ -76,7 +90,7 @@ template <int R, int S, int K, class C> __device__ __forceinline__ void dft_comb
     }
 }
 
-// In-register DFT of R points (power of two <= 16): X_k = sum_r x_r W^{rk},
+// In-register DFT of R points (power of two <= 32): X_k = sum_r x_r W^{rk},
 // W = exp(S 2 pi i / R), by even/odd splitting.
 template <int R, int S, class C> struct Dft {
     static __device__ __forceinline__ void run(C* x) {
@@ -281,28 +295,37 @@ template <typename T, int L> __device__ __forceinline__ cx<T> tw_get(const cx<T>
     else return cmul(hi[e >> D::SH], lo[e & (D::NLO - 1)]);
 }
 
-// v[r] *= W_L^{S r e1} for r = 1..R-1, from table powers w1, w2, w4, w8
-// (each a table lookup) combined in at most three products.
+// v[r] *= W_L^{S r e1} for r = 1..R-1 (R <= 32): table lookups of
+// w1, w2, w4 (combined into w1..w7) and w8, w16 (w24 = w8 w16), then
+// w_r = w_{r mod 8} w_{8 floor(r/8)}, at most three products deep.
 template <typename T, int L, int R, int S>
 __device__ __forceinline__ void twiddle_row(cx<T>* v, int e1, const cx<T>* hi, const cx<T>* lo) {
     typedef cx<T> C;
-    C w[R];
+    C w[8];
     w[1] = tw_get<T, L>(hi, lo, e1);
     if constexpr (R > 2) w[2] = tw_get<T, L>(hi, lo, 2 * e1);
-    if constexpr (R > 4) w[4] = tw_get<T, L>(hi, lo, 4 * e1);
-    if constexpr (R > 8) w[8] = tw_get<T, L>(hi, lo, 8 * e1);
     if constexpr (R > 2) w[3] = cmul(w[1], w[2]);
     if constexpr (R > 4) {
+        w[4] = tw_get<T, L>(hi, lo, 4 * e1);
         w[5] = cmul(w[1], w[4]);
         w[6] = cmul(w[2], w[4]);
         w[7] = cmul(w[3], w[4]);
     }
-    if constexpr (R > 8) {
-#pragma unroll
-        for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+    C u[4];
+    if constexpr (R > 8) u[1] = tw_get<T, L>(hi, lo, 8 * e1);
+    if constexpr (R > 16) {
+        u[2] = tw_get<T, L>(hi, lo, 16 * e1);
+        u[3] = cmul(u[1], u[2]);
     }
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = mul_dir<S>(v[r], w[r]);
+    for (int r = 1; r < R; ++r) {
+        const int a = r & 7, b = r >> 3;
+        C t;
+        if (b == 0) t = w[a];
+        else if (a == 0) t = u[b];
+        else t = cmul(w[a], u[b]);
+        v[r] = mul_dir<S>(v[r], t);
+    }
 }
 
 // One radix-R Stockham pass over the tile (in place, barrier-separated
@@ -450,8 +473,14 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
 #endif
 // KIND 2 = wavefront column pass.
 template <typename T, int KIND = 0> struct Tiling;
+#ifndef MPA_RMAX32
+#define MPA_RMAX32 32
+#endif
 template <int KIND> struct Tiling<float, KIND> {
-    static constexpr int E = KIND == 0 ? MPA_KC_E : KIND == 1 ? MPA_KR_E : MPA_KCW_E, RMAX = 16, PSH = 4, CMIN = 8;
+    // radix-32 passes (one smem exchange for a 1024-point transform) where a
+    // thread holds 32 elements; the wavefront pass (16 per thread) uses 16
+    static constexpr int E = KIND == 0 ? MPA_KC_E : KIND == 1 ? MPA_KR_E : MPA_KCW_E;
+    static constexpr int RMAX = E >= 32 ? MPA_RMAX32 : 16, PSH = RMAX == 32 ? 5 : 4, CMIN = 8;
     static constexpr int TE = KIND == 1 ? MPA_KR_TE : MPA_KC_TE;
 };
 template <int KIND> struct Tiling<double, KIND> {
