@@ -142,6 +142,22 @@ def ncu_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(t: float, dist=None, device="cpu") -> float:
+    """The job's time: the largest per-rank time (each rank times its own
+    replica; the barrier before and after the timed region aligns them)."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world: int, units_per_rank: float, t_max: float) -> float:
+    """Whole-job throughput: units all ranks processed over the job's time."""
+    return world * units_per_rank / t_max
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -246,11 +262,8 @@ def run_mpa(args, world, rank, local):
     mpa.profile(False)
     ck = clocks.stop()
     t = sum(s.elapsed_time(e) for s, e in evs) / 1e3
-    tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t_max = float(tt.item())
-    value = world * N * km * args.steps / t_max
+    t_max = max_over_ranks(t, dist, "cuda")
+    value = job_value(world, N * km * args.steps, t_max)
     ok = plan.status(stream)
 
     # ---- dominant kernel roofline (CUDA events around each launch, same region)
@@ -290,10 +303,8 @@ def run_mpa(args, world, rank, local):
             h_out.copy_(f, non_blocking=True)
         ee.record(stream)
         torch.cuda.synchronize()
-        te = torch.tensor([es.elapsed_time(ee) / 1e3], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * N * km * args.steps / float(te.item()), "unit": UNIT,
+        te = max_over_ranks(es.elapsed_time(ee) / 1e3, dist, "cuda")
+        line["e2e"] = {"value": job_value(world, N * km * args.steps, te), "unit": UNIT,
                        "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
                        "d2h_bytes_per_step": h_out.numel() * h_out.element_size()}
 

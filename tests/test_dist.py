@@ -1,0 +1,55 @@
+"""Host-side logic of the multi-process benchmark path on CPU (gloo,
+world size 2): every rank runs an independent replica, the job time is the
+maximum over ranks and the job value counts the units of all ranks.  No
+collective touches the data path."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, r, local = bench.dist_env()
+        t_local = 1.0 + rank  # rank 1 is the slower replica
+        t_max = bench.max_over_ranks(t_local, dist, "cpu")
+        value = bench.job_value(w, 100.0, t_max)
+        out[rank] = (w, r, local, t_max, value)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_count_all_units():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert set(res) == {0, 1}
+    for rank, (w, r, local, t_max, value) in res.items():
+        assert (w, r, local) == (2, rank, rank)
+        assert t_max == pytest.approx(2.0)
+        assert value == pytest.approx(2 * 100.0 / 2.0)
+
+
+def test_single_process_defaults():
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        os.environ.pop(k, None)
+    assert bench.dist_env() == (1, 0, 0)
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.job_value(1, 10.0, 2.0) == 5.0

@@ -189,3 +189,20 @@ def test_bench_workload_sampled_interval_fp32(M):
     plan = M.Plan(w.fiber, w.N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32")
     got = host(plan.interval(dev(psi0, "fp64"), z0))
     assert oracle.rel_l2(got, ref) < TOL["fp32"]
+
+
+def test_largest_workload_sampled_interval_and_split_step(M):
+    """N = 2^24 (the 64-channel 25-GHz link, beta3 = 0.08): the same kernels
+    and launch shapes as a full run, on a short interval the oracle computes
+    in seconds (M = 4, n_iter = 2), and two FP64 split-steps."""
+    w = workload("2")
+    A0 = w.field()
+    psi0 = oracle.fft(A0, +1)
+    ref = oracle.mpa_interval(psi0, w.fiber, w.T_ps, 0.0, 0.5, 4, 2)
+    plan = M.Plan(w.fiber, w.N, w.T_ps, 0.5, 4, 2, precision="fp32")
+    got = host(plan.interval(dev(psi0, "fp64"), 0.0))
+    assert oracle.rel_l2(got, ref) < TOL["fp32"]
+    del plan
+    ref_ss = oracle.ss(A0, w.fiber, w.T_ps, 0.0, 0.1, 0.05)
+    got_ss = host(M.ss_propagate(dev(A0, "fp64"), w.fiber, w.T_ps, 0.05, 0.0, 0.1))
+    assert oracle.rel_l2(got_ss, ref_ss) < TOL["fp64"]
