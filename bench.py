@@ -329,6 +329,34 @@ def run_mpa(args, world, rank, local):
         line["comparator"] = ss
         line["mpa_over_ss_fp64"] = value / world / ss["ss_fp64"]["value"]
 
+        # ---- accuracy of both timed methods against the exact solution over
+        # one span (DM jump, +190 ps^2/km segment, amplifier): "numerically
+        # exact" = FP64 split-step at dz/4 and dz/8 with one Richardson step
+        # (the paper's fine split-step reference, text before Fig. 3)
+        span = w.fiber.period_km
+        g0 = torch.from_numpy(A0).cuda()
+        ws64 = torch.empty(mpa.ss_workspace_bytes(N, "fp64"), dtype=torch.uint8, device="cuda")
+
+        def ss64(dz):
+            g = g0.clone()
+            mpa.ss_propagate(g, w.fiber, w.T_ps, dz, 0.0, span, ws64, stream)
+            return g
+
+        r1, r2 = ss64(w.ss_dz_km / 4), ss64(w.ss_dz_km / 8)
+        exact = r2 + (r2 - r1) / 3.0
+        e_ref = float(torch.linalg.vector_norm(r2 - exact) / torch.linalg.vector_norm(exact))
+        e_ss = float(torch.linalg.vector_norm(ss64(w.ss_dz_km) - exact) / torch.linalg.vector_norm(exact))
+        g32 = g0.to(torch.complex64)
+        ws32 = torch.empty(mpa.ss_workspace_bytes(N, "fp32"), dtype=torch.uint8, device="cuda")
+        mpa.ss_propagate(g32, w.fiber, w.T_ps, w.ss_dz_km, 0.0, span, ws32, stream)
+        e_ss32 = float(torch.linalg.vector_norm(g32.to(torch.complex128) - exact) / torch.linalg.vector_norm(exact))
+        fm = g0.to(torch.complex64)
+        plan.propagate(fm, 0.0, span, stream)
+        e_mpa = float(torch.linalg.vector_norm(fm.to(torch.complex128) - exact) / torch.linalg.vector_norm(exact))
+        line["accuracy"] = {"km": span, "reference": "FP64 split-step at dz/4 and dz/8 + Richardson",
+                            "reference_uncertainty": e_ref, "mpa_fp32_rel_l2": e_mpa,
+                            "ss_fp64_rel_l2": e_ss, "ss_fp32_rel_l2": e_ss32, "mpa_at_least_as_accurate": e_mpa <= e_ss}
+
         # ---- CPU oracle baseline + full-size parity sample (rank 0, N = 1)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             import oracle
