@@ -137,6 +137,38 @@ MPA_API int mpa_plan_status(mpa_plan* plan, mpa_stream stream);
 
 MPA_API void mpa_plan_destroy(mpa_plan* plan);
 
+/* Many independent links propagated together (no counterpart in the paper;
+ * the batching of independent problems of the MPA node transforms).  Each
+ * link has its own fiber map, N, window and length z_to (from z = 0, a
+ * multiple of L_km); all share the discretisation L_km, M, n_iter and the
+ * precision.  Links with equal N are batched into the same launches (each
+ * with its own node constants); groups of different N run as parallel
+ * branches of one CUDA graph.  Field pointers are fixed at creation (the
+ * graph captures them); fields are updated in place, as by mpa_propagate. */
+typedef struct {
+    mpa_fiber_map map;  /* copied at creation */
+    int64_t N;
+    double T_ps;
+    double z_to_km;     /* propagation 0 -> z_to_km */
+    void* field;        /* device, N samples of the batch precision's complex type */
+} mpa_link;
+
+typedef struct mpa_batch mpa_batch;
+
+MPA_API int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_t M, int32_t n_iter,
+                             int32_t precision, mpa_batch** out);
+MPA_API int mpa_batch_workspace_size(const mpa_batch* batch, size_t* bytes);
+/* Attaches caller-owned device workspace and uploads the node tables
+ * (synchronous); a previously captured graph is discarded. */
+MPA_API int mpa_batch_set_workspace(mpa_batch* batch, void* workspace, size_t bytes);
+/* Propagates every link.  use_graph != 0: the first such call runs the
+ * launches directly and captures them into a CUDA graph (one parallel
+ * branch per N group, on library-owned streams joined to `stream`); later
+ * calls replay the graph on `stream`.  Do not call it while `stream` is
+ * being captured by the caller. */
+MPA_API int mpa_batch_propagate(mpa_batch* batch, int32_t use_graph, mpa_stream stream);
+MPA_API void mpa_batch_destroy(mpa_batch* batch);
+
 /* Symmetric split-step of Eq. (4) on the GPU: half linear step, then
  * (nonlinear phase rotation exp(i sigma |A|^2 dz), linear step) repeated,
  * the last linear step halved.  Linear steps are exact Fourier multipliers

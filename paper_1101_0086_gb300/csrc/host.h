@@ -1,0 +1,200 @@
+// Host-side helpers shared by the single-link plan (plan.cu) and the
+// batched links (batch.cu): fiber-map integration, the fixed-point phase
+// constants, the four-step split of N, and the natural-order transforms.
+#pragma once
+
+#include <cmath>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "mpa.h"
+
+namespace mpa {
+namespace host {
+
+// Records the CUDA error string for mpa_last_cuda_error.
+int cuda_fail(cudaError_t e);
+
+#define MPA_TRY(expr)                                            \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) return ::mpa::host::cuda_fail(_e); \
+    } while (0)
+
+inline constexpr double kPi = 3.14159265358979323846264338327950288;
+// amplifiers that may end one interval (a longer interval than the
+// amplifier spacing would cross one inside it, which is rejected)
+inline constexpr int kMaxAmpsPerInterval = 4;
+
+// ----------------------------------------------------------- fiber map
+struct HostMap {
+    std::vector<mpa_segment> seg;
+    double gamma = 0, z_a = 0, period = 0, length = 0;
+
+    int init(const mpa_fiber_map* m) {
+        if (!m || !m->segments || m->n_segments < 1 || m->n_periods < 1) return MPA_ERR_INVALID_ARG;
+        if (!(m->gamma_per_km >= 0.0) || !std::isfinite(m->gamma_per_km) || !std::isfinite(m->z_a_km))
+            return MPA_ERR_INVALID_ARG;
+        seg.assign(m->segments, m->segments + m->n_segments);
+        for (const auto& s : seg) {
+            if (!(s.length_km > 0.0) || !std::isfinite(s.beta2_ps2_per_km) || !std::isfinite(s.beta3_ps3_per_km) ||
+                !std::isfinite(s.sigma_per_W_km))
+                return MPA_ERR_INVALID_ARG;
+            period += s.length_km;
+        }
+        gamma = m->gamma_per_km;
+        z_a = m->z_a_km;
+        length = period * m->n_periods;
+        return MPA_OK;
+    }
+    static double coef(const mpa_segment& s, int col) {
+        return col == 1 ? s.beta2_ps2_per_km : col == 2 ? s.beta3_ps3_per_km : s.sigma_per_W_km;
+    }
+    // int_za^zb of a coefficient: shift za into the first period, then sum
+    // coefficient x overlap over the segment copies that [za, zb] covers.
+    double integ(double za, double zb, int col) const {
+        if (!(zb > za)) return 0.0;
+        const double shift = std::floor(za / period) * period;
+        const double u = za - shift, v = zb - shift;
+        double acc = 0.0;
+        for (long p = 0; (double)p * period < v; ++p) {
+            double a = (double)p * period;
+            for (const auto& s : seg) {
+                const double b = a + s.length_km;
+                const double lo = a > u ? a : u, hi = b < v ? b : v;
+                if (hi > lo) acc += coef(s, col) * (hi - lo);
+                a = b;
+            }
+        }
+        return acc;
+    }
+    // coefficient just left (side < 0) or right (side > 0) of z
+    double side(double z, int col, int sgn) const {
+        const double zz = z + (sgn > 0 ? 1e-9 : -1e-9) * period;
+        double u = zz - std::floor(zz / period) * period;
+        double a = 0.0;
+        for (size_t i = 0; i < seg.size(); ++i) {
+            a += seg[i].length_km;
+            if (u < a || i + 1 == seg.size()) return coef(seg[i], col);
+        }
+        return coef(seg.back(), col);
+    }
+    // amplifiers k z_a (k >= 1) in (za, zb]
+    long amps(double za, double zb) const {
+        if (!(z_a > 0.0)) return 0;
+        const double tol = 1e-9 * z_a;
+        long ka = (long)std::floor((za + tol) / z_a), kb = (long)std::floor((zb + tol) / z_a);
+        if (ka < 0) ka = 0;
+        return kb > ka ? kb - ka : 0;
+    }
+};
+
+// x mod 1 as a 128-bit binary fraction (exact whenever the FP64 value x has
+// no bits below 2^-128).
+inline void frac_q128(double x, unsigned long long* hi, unsigned long long* lo) {
+    typedef unsigned __int128 u128;
+    u128 q = 0;
+    if (x != 0.0 && std::isfinite(x)) {
+        const double ax = std::fabs(x);
+        int e = 0;
+        const double m = std::frexp(ax, &e);  // ax = m 2^e, m in [0.5, 1)
+        const unsigned long long mant = (unsigned long long)std::ldexp(m, 53);
+        const int sh = e - 53 + 128;  // ax 2^128 = mant 2^sh
+        if (sh >= 128) q = 0;
+        else if (sh >= 0) q = (u128)mant << sh;
+        else if (sh > -64) q = (u128)(mant >> (-sh));
+        if (x < 0) q = (u128)0 - q;
+    }
+    *hi = (unsigned long long)(q >> 64);
+    *lo = (unsigned long long)q;
+}
+
+// Phase constants of beta(w, .) over an integral (I2, I3) for window T:
+// theta = k'^2 pi I2/T^2 + k'^3 2 pi^2 I3/(3 T^3) turns.
+inline void phase_consts(double I2, double I3, double T, NodeC* c) {
+    frac_q128(kPi * I2 / (T * T), &c->a_hi, &c->a_lo);
+    frac_q128(2.0 * kPi * kPi * I3 / (3.0 * T * T * T), &c->b_hi, &c->b_lo);
+}
+
+inline bool whole(double x, double* r) {
+    const double n = std::nearbyint(x);
+    *r = n;
+    return std::fabs(x - n) <= 1e-9 * (std::fabs(x) > 1.0 ? std::fabs(x) : 1.0);
+}
+
+inline int ilog2(long long n) {
+    int l = 0;
+    while ((1ll << l) < n) ++l;
+    return l;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Split {
+    int logN, logN1, logN2;
+    long long N, N1, N2;
+};
+
+inline int split_n(long long N, int prec, Split* s) {
+    if (N < 256 || (N & (N - 1)) != 0) return MPA_ERR_UNSUPPORTED_N;
+    s->logN = ilog2(N);
+    if (s->logN > (prec == MPA_FP32 ? 25 : 24)) return MPA_ERR_UNSUPPORTED_N;
+    s->logN2 = s->logN / 2 < KC_LOG_MAX ? s->logN / 2 : KC_LOG_MAX;
+    s->logN1 = s->logN - s->logN2;
+    const int rmax = prec == MPA_FP32 ? kr_log_max<float>() : kr_log_max<double>();
+    if (s->logN2 < KC_LOG_MIN || s->logN1 > rmax) return MPA_ERR_UNSUPPORTED_N;
+    s->N = N;
+    s->N1 = 1ll << s->logN1;
+    s->N2 = 1ll << s->logN2;
+    return MPA_OK;
+}
+
+// ------------------------------------------------ natural-order transforms
+// Forward: natural A(t) in `data` -> natural spectrum in `out` (may alias
+// scratch); data viewed as N1 x N2 (rows n1), transposed into scratch.
+template <typename T>
+inline int fft_forward(const Split& s, const cx<T>* data, cx<T>* scratch, cudaStream_t st) {
+    MPA_TRY(transpose_launch<T>(data, scratch, s.N1, s.N2, st));
+    KRParams<T> r{scratch, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
+    MPA_TRY(kr_launch<T>(KR_FWD, s.logN1, r, st));
+    KCParams<T> c{};
+    c.src = scratch;
+    c.dst = scratch;
+    c.N = s.N;
+    c.logN = s.logN;
+    c.N1 = (int)s.N1;
+    c.logN1 = s.logN1;
+    c.ncols = s.N1;
+    MPA_TRY(kc_launch<T>(KC_FWD, s.logN2, c, st));
+    return MPA_OK;
+}
+
+// Inverse: natural spectrum in `spec` (overwritten) -> natural A(t) in `out`.
+template <typename T>
+inline int fft_inverse(const Split& s, cx<T>* spec, cx<T>* out, cudaStream_t st) {
+    KCParams<T> c{};
+    c.src = spec;
+    c.dst = spec;
+    c.N = s.N;
+    c.logN = s.logN;
+    c.N1 = (int)s.N1;
+    c.logN1 = s.logN1;
+    c.ncols = s.N1;
+    MPA_TRY(kc_launch<T>(KC_INV, s.logN2, c, st));
+    KRParams<T> r{spec, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
+    MPA_TRY(kr_launch<T>(KR_INV, s.logN1, r, st));
+    MPA_TRY(transpose_launch<T>(spec, out, s.N2, s.N1, st));
+    return MPA_OK;
+}
+
+// One level-synchronous interval (MPA steps 2-7) for nl links stored
+// link-major; defined in plan.cu for float and double.
+template <typename T>
+int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi0c, double2* state,
+               const NodeC* nodes, const int* loff, const double* gain, unsigned int* err, int scan_mode,
+               double2* out, cudaStream_t st);
+
+}  // namespace host
+}  // namespace mpa

@@ -4,7 +4,10 @@
 namespace mpa {
 
 template <int L, int MODE>
-static cudaError_t kc_one(const KCParams<float>& p, cudaStream_t st) {
+static cudaError_t kc_one(const KCParams<float>& pin, cudaStream_t st) {
+    // callers that leave the link fields unset launch one run of nodes
+    KCParams<float> p = pin;
+    if (p.npl <= 0) p.npl = (int)(p.ncols >> p.logN1) > 0 ? (int)(p.ncols >> p.logN1) : 1;
     typedef KCGeom<float, L> Gm;
     static bool attr_set = false;
     if (!attr_set) {
@@ -24,7 +27,7 @@ static cudaError_t kc_one(const KCParams<float>& p, cudaStream_t st) {
         // algorithmic bytes: every tile element read once and written once
         // (a shared source, src_stride == 0, is read once for all nodes)
         const double cs = (double)sizeof(cx<float>), tile = (double)p.ncols * L;
-        const double rd = p.src_stride == 0 ? (double)p.N1 * L : tile;
+        const double rd = p.src_stride == 0 ? (double)p.ncols / p.npl * L : tile;
         prof_end(prof_kc_kind(MODE), st, (rd + tile) * cs);
     }
     g_launches.fetch_add(1, std::memory_order_relaxed);

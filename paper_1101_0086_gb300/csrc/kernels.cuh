@@ -31,17 +31,25 @@ namespace mpa {
 enum { KC_MPA_PRE = 0, KC_MPA_POST = 1, KC_SS_STEP = 2, KC_FWD = 3, KC_INV = 4 };
 enum { KR_MPA = 0, KR_SS = 1, KR_FWD = 2, KR_INV = 3 };
 
+// A launch covers nl links x npl nodes each (node index within the launch
+// n = l npl + jn); a single link is nl = 1.
 template <typename T> struct KCParams {
     const cx<T>* src;
-    long long src_stride;  // elements between consecutive nodes of the source (0: shared source)
+    long long src_stride;   // elements between consecutive nodes of a link's source (0: shared source)
+    long long src_lstride;  // elements between links' sources
     cx<T>* dst;
     long long dst_stride;
+    long long dst_lstride;
+    const cx<T>* src0;      // if non-null: the source of node jn == 0 of link l is src0 + l src0_lstride
+    long long src0_lstride;
     long long N;
     int logN;
     int N1, logN1;
-    long long ncols;     // nodes * N1 columns in this launch
-    const NodeC* nodes;  // MPA: constants of the launch's node 0, 1, ...
-    NodeC flow;          // SS: constants of the linear step
+    long long ncols;        // nl * npl * N1 columns in this launch
+    int npl;                // nodes per link in this launch
+    const NodeC* nodes;     // MPA: constants of link l, node jn at nodes[loff[l] + jn]
+    const int* loff;
+    NodeC flow;             // SS: constants of the linear step
 };
 
 template <typename T> struct KRParams {
@@ -138,11 +146,13 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
         bmap<LAYOUT_COL, L, G, XA::R0>(tid + q * NT, j, g);
         const long long col = col0 + g;
         const bool ok = col < p.ncols;
-        const long long node = ok ? (col >> p.logN1) : 0;
+        const int node = ok ? (int)(col >> p.logN1) : 0;
+        const int l = node / p.npl, jn = node - l * p.npl;
         const long long c = col & N1m;
-        const C* src = p.src + node * p.src_stride + c;
+        const C* src = (p.src0 && jn == 0) ? p.src0 + l * p.src0_lstride + c
+                                           : p.src + l * p.src_lstride + jn * p.src_stride + c;
         NodeC nc;
-        if constexpr (MODE == KC_MPA_PRE) nc = p.nodes[node];
+        if constexpr (MODE == KC_MPA_PRE) nc = p.nodes[p.loff[l] + jn];
         unsigned long long th[XA::R0];
         if constexpr (FAST && MODE == KC_MPA_PRE)
             phase_run<XA::R0>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::R0), nc, th);
@@ -198,11 +208,12 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
         bmap<LAYOUT_COL, L, G, RO>(tid + q * NT, j, g);
         const long long col = col0 + g;
         if (col >= p.ncols) continue;
-        const long long node = col >> p.logN1;
+        const int node = (int)(col >> p.logN1);
+        const int l = node / p.npl, jn = node - l * p.npl;
         const long long c = col & N1m;
-        C* dst = p.dst + node * p.dst_stride + c;
+        C* dst = p.dst + l * p.dst_lstride + jn * p.dst_stride + c;
         NodeC nc;
-        if constexpr (MODE == KC_MPA_POST) nc = p.nodes[node];
+        if constexpr (MODE == KC_MPA_POST) nc = p.nodes[p.loff[l] + jn];
         unsigned long long th[RO];
         if constexpr (FAST && MODE == KC_MPA_POST)
             phase_run<RO>(c + (long long)j * p.N1, (long long)p.N1 * (L / RO), nc, th);
@@ -559,16 +570,17 @@ __global__ void __launch_bounds__(KCWGeom<L>::NT, 1) kcw_kernel(const KCWParams 
 //   mode 1: step 7: state <- psi_M exp(i beta(w, z0+L) + int G) * gain, psi0c <- state
 //   mode 2: out <- psi_M (FP64, no step 7)
 template <typename T> struct ScanParams {
-    cx<T>* psi;
+    cx<T>* psi;          // link l's node j at psi + (l (M+1) + j) N
     long long N;
     int M;
-    const cx<T>* psi0c;  // psi_0 in the working precision
-    double2* state;      // FP64 psi_0 in, A_hat(z0+L) out (mode 1)
+    const cx<T>* psi0c;  // psi_0 in the working precision, link l at + l N
+    double2* state;      // FP64 psi_0 in, A_hat(z0+L) out (mode 1), link l at + l N
     cx<T>* psi0c_out;    // mode 1: working-precision copy of the new state
     double2* out;        // mode 2
     int mode;
-    NodeC nodeM;
-    double gain;
+    const NodeC* nodes;  // node M of link l: nodes[loff[l] + M]
+    const int* loff;
+    const double* gain;  // amplifier gain at the interval end, per link
     unsigned int* err;
 };
 
@@ -577,12 +589,15 @@ __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
     typedef cx<T> C;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.N) return;
-    const C v0 = p.psi[k];
+    const int l = blockIdx.y;
+    const long long lo = (long long)l * p.N;
+    cx<T>* psi = p.psi + lo * (p.M + 1);
+    const C v0 = psi[k];
     T rx = T(0.5) * v0.x, ry = T(0.5) * v0.y, cxx = T(0), cyy = T(0);
-    const C p0 = p.psi0c[k];
+    const C p0 = p.psi0c[lo + k];
     C vl = v0;
     for (int j = 1; j <= p.M; ++j) {
-        C* q = p.psi + (long long)j * p.N + k;
+        C* q = psi + (long long)j * p.N + k;
         vl = *q;
         if (p.mode == 0) {
             // psi_0 + i (R + V_j/2), R = running sum (compensation removed)
@@ -601,18 +616,19 @@ __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
     // psi_M = psi_0 + i (R_M - V_M/2) in FP64
     const double sx = ((double)rx - (double)cxx) - 0.5 * (double)vl.x;
     const double sy = ((double)ry - (double)cyy) - 0.5 * (double)vl.y;
-    const double2 s0 = p.state[k];
+    const double2 s0 = p.state[lo + k];
     const double2 psiM = make_double2(s0.x - sy, s0.y + sx);
     if (p.mode == 2) {
-        p.out[k] = psiM;
+        p.out[lo + k] = psiM;
         return;
     }
     // step 7 and the lumped gain
-    const double2 ph = expi_turns<double>(phase_q64(signed_k(k, p.N), p.nodeM));
-    const double g = p.nodeM.pre * p.gain;
+    const NodeC nodeM = p.nodes[p.loff[l] + p.M];
+    const double2 ph = expi_turns<double>(phase_q64(signed_k(k, p.N), nodeM));
+    const double g = nodeM.pre * p.gain[l];
     const double2 a = make_double2(g * (psiM.x * ph.x - psiM.y * ph.y), g * (psiM.x * ph.y + psiM.y * ph.x));
-    p.state[k] = a;
-    p.psi0c_out[k] = mkc((T)a.x, (T)a.y);
+    p.state[lo + k] = a;
+    p.psi0c_out[lo + k] = mkc((T)a.x, (T)a.y);
     if (!(isfinite(a.x) && isfinite(a.y))) atomicOr(p.err, 1u);
 }
 

@@ -33,7 +33,7 @@ template <typename T> constexpr int kr_log_max() { return sizeof(T) == 4 ? 14 : 
 
 template <typename T> cudaError_t kc_launch(int mode, int logL, const KCParams<T>& p, cudaStream_t st);
 template <typename T> cudaError_t kr_launch(int mode, int logL, const KRParams<T>& p, cudaStream_t st);
-template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, cudaStream_t st);
+template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int links, cudaStream_t st);
 template <typename T> cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long C, cudaStream_t st);
 template <typename T> cudaError_t to_state_launch(const cx<T>* in, double2* state, cx<T>* copy, long long N, cudaStream_t st);
 template <typename T> cudaError_t from_state_launch(const double2* state, cx<T>* out, long long N, cudaStream_t st);

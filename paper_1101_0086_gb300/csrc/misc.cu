@@ -108,15 +108,15 @@ void prof_reset() {
 
 static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, cudaStream_t st) {
+template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int p_links, cudaStream_t st) {
     const bool pr = g_prof_on.load(std::memory_order_relaxed);
     if (pr) prof_begin(st);
-    scan_kernel<T><<<blocks_for(p.N, 256), 256, 0, st>>>(p);
+    scan_kernel<T><<<dim3(blocks_for(p.N, 256), (unsigned)p_links), 256, 0, st>>>(p);
     if (pr) {
         const double cs = (double)sizeof(cx<T>), n = (double)p.N;
-        double b = (p.M + 1) * n * cs + n * cs;  // V_0..V_M and psi_0
-        if (p.mode == 0) b += p.M * n * cs;      // psi^{(n+1)}_1..M
-        else b += n * 16.0 + (p.mode == 1 ? n * (16.0 + cs) : n * 16.0);  // FP64 state in, result out
+        double b = ((p.M + 1) * n * cs + n * cs) * p_links;  // V_0..V_M and psi_0
+        if (p.mode == 0) b += p.M * n * cs * p_links;  // psi^{(n+1)}_1..M
+        else b += (n * 16.0 + (p.mode == 1 ? n * (16.0 + cs) : n * 16.0)) * p_links;  // FP64 state in, result out
         prof_end(PK_SCAN, st, b);
     }
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -144,8 +144,8 @@ template <typename T> cudaError_t from_state_launch(const double2* state, cx<T>*
     return cudaGetLastError();
 }
 
-template cudaError_t scan_launch<float>(const ScanParams<float>&, cudaStream_t);
-template cudaError_t scan_launch<double>(const ScanParams<double>&, cudaStream_t);
+template cudaError_t scan_launch<float>(const ScanParams<float>&, int, cudaStream_t);
+template cudaError_t scan_launch<double>(const ScanParams<double>&, int, cudaStream_t);
 template cudaError_t transpose_launch<float>(const float2*, float2*, long long, long long, cudaStream_t);
 template cudaError_t transpose_launch<double>(const double2*, double2*, long long, long long, cudaStream_t);
 template cudaError_t to_state_launch<float>(const float2*, double2*, float2*, long long, cudaStream_t);

@@ -8,190 +8,90 @@
 #include <string>
 #include <vector>
 
-#include "launch.h"
-#include "mpa.h"
+#include "host.h"
 
 using namespace mpa;
 
-namespace {
-
+namespace mpa {
+namespace host {
 thread_local std::string g_cuda_err;
-
 int cuda_fail(cudaError_t e) {
     g_cuda_err = cudaGetErrorString(e);
     return MPA_ERR_CUDA;
 }
+}  // namespace host
+}  // namespace mpa
 
-#define MPA_TRY(expr)                              \
-    do {                                           \
-        cudaError_t _e = (expr);                   \
-        if (_e != cudaSuccess) return cuda_fail(_e); \
-    } while (0)
+using namespace mpa::host;
 
-constexpr double kPi = 3.14159265358979323846264338327950288;
+namespace mpa {
+namespace host {
 
-// ----------------------------------------------------------- fiber map
-struct HostMap {
-    std::vector<mpa_segment> seg;
-    double gamma = 0, z_a = 0, period = 0, length = 0;
-
-    int init(const mpa_fiber_map* m) {
-        if (!m || !m->segments || m->n_segments < 1 || m->n_periods < 1) return MPA_ERR_INVALID_ARG;
-        if (!(m->gamma_per_km >= 0.0) || !std::isfinite(m->gamma_per_km) || !std::isfinite(m->z_a_km))
-            return MPA_ERR_INVALID_ARG;
-        seg.assign(m->segments, m->segments + m->n_segments);
-        for (const auto& s : seg) {
-            if (!(s.length_km > 0.0) || !std::isfinite(s.beta2_ps2_per_km) || !std::isfinite(s.beta3_ps3_per_km) ||
-                !std::isfinite(s.sigma_per_W_km))
-                return MPA_ERR_INVALID_ARG;
-            period += s.length_km;
-        }
-        gamma = m->gamma_per_km;
-        z_a = m->z_a_km;
-        length = period * m->n_periods;
-        return MPA_OK;
-    }
-    static double coef(const mpa_segment& s, int col) {
-        return col == 1 ? s.beta2_ps2_per_km : col == 2 ? s.beta3_ps3_per_km : s.sigma_per_W_km;
-    }
-    // int_za^zb of a coefficient: shift za into the first period, then sum
-    // coefficient x overlap over the segment copies that [za, zb] covers.
-    double integ(double za, double zb, int col) const {
-        if (!(zb > za)) return 0.0;
-        const double shift = std::floor(za / period) * period;
-        const double u = za - shift, v = zb - shift;
-        double acc = 0.0;
-        for (long p = 0; (double)p * period < v; ++p) {
-            double a = (double)p * period;
-            for (const auto& s : seg) {
-                const double b = a + s.length_km;
-                const double lo = a > u ? a : u, hi = b < v ? b : v;
-                if (hi > lo) acc += coef(s, col) * (hi - lo);
-                a = b;
-            }
-        }
-        return acc;
-    }
-    // coefficient just left (side < 0) or right (side > 0) of z
-    double side(double z, int col, int sgn) const {
-        const double zz = z + (sgn > 0 ? 1e-9 : -1e-9) * period;
-        double u = zz - std::floor(zz / period) * period;
-        double a = 0.0;
-        for (size_t i = 0; i < seg.size(); ++i) {
-            a += seg[i].length_km;
-            if (u < a || i + 1 == seg.size()) return coef(seg[i], col);
-        }
-        return coef(seg.back(), col);
-    }
-    // amplifiers k z_a (k >= 1) in (za, zb]
-    long amps(double za, double zb) const {
-        if (!(z_a > 0.0)) return 0;
-        const double tol = 1e-9 * z_a;
-        long ka = (long)std::floor((za + tol) / z_a), kb = (long)std::floor((zb + tol) / z_a);
-        if (ka < 0) ka = 0;
-        return kb > ka ? kb - ka : 0;
-    }
-};
-
-// x mod 1 as a 128-bit binary fraction (exact whenever the FP64 value x has
-// no bits below 2^-128).
-void frac_q128(double x, unsigned long long* hi, unsigned long long* lo) {
-    typedef unsigned __int128 u128;
-    u128 q = 0;
-    if (x != 0.0 && std::isfinite(x)) {
-        const double ax = std::fabs(x);
-        int e = 0;
-        const double m = std::frexp(ax, &e);  // ax = m 2^e, m in [0.5, 1)
-        const unsigned long long mant = (unsigned long long)std::ldexp(m, 53);
-        const int sh = e - 53 + 128;  // ax 2^128 = mant 2^sh
-        if (sh >= 128) q = 0;
-        else if (sh >= 0) q = (u128)mant << sh;
-        else if (sh > -64) q = (u128)(mant >> (-sh));
-        if (x < 0) q = (u128)0 - q;
-    }
-    *hi = (unsigned long long)(q >> 64);
-    *lo = (unsigned long long)q;
-}
-
-// Phase constants of beta(w, .) over an integral (I2, I3) for window T:
-// theta = k'^2 pi I2/T^2 + k'^3 2 pi^2 I3/(3 T^3) turns.
-void phase_consts(double I2, double I3, double T, NodeC* c) {
-    frac_q128(kPi * I2 / (T * T), &c->a_hi, &c->a_lo);
-    frac_q128(2.0 * kPi * kPi * I3 / (3.0 * T * T * T), &c->b_hi, &c->b_lo);
-}
-
-bool whole(double x, double* r) {
-    const double n = std::nearbyint(x);
-    *r = n;
-    return std::fabs(x - n) <= 1e-9 * (std::fabs(x) > 1.0 ? std::fabs(x) : 1.0);
-}
-
-int ilog2(long long n) {
-    int l = 0;
-    while ((1ll << l) < n) ++l;
-    return l;
-}
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-struct Split {
-    int logN, logN1, logN2;
-    long long N, N1, N2;
-};
-
-int split_n(long long N, int prec, Split* s) {
-    if (N < 256 || (N & (N - 1)) != 0) return MPA_ERR_UNSUPPORTED_N;
-    s->logN = ilog2(N);
-    if (s->logN > (prec == MPA_FP32 ? 25 : 24)) return MPA_ERR_UNSUPPORTED_N;
-    s->logN2 = s->logN / 2 < KC_LOG_MAX ? s->logN / 2 : KC_LOG_MAX;
-    s->logN1 = s->logN - s->logN2;
-    const int rmax = prec == MPA_FP32 ? kr_log_max<float>() : kr_log_max<double>();
-    if (s->logN2 < KC_LOG_MIN || s->logN1 > rmax) return MPA_ERR_UNSUPPORTED_N;
-    s->N = N;
-    s->N1 = 1ll << s->logN1;
-    s->N2 = 1ll << s->logN2;
-    return MPA_OK;
-}
-
-// ------------------------------------------------ natural-order transforms
-// Forward: natural A(t) in `data` -> natural spectrum in `out` (may alias
-// scratch); data viewed as N1 x N2 (rows n1), transposed into scratch.
+// One level-synchronous interval for nl links stored link-major (link l's
+// node j at psi + (l (M+1) + j) N, its psi_0 at psi0c + l N, its FP64 state
+// at state + l N).  loff[l] points link l's node constants for this
+// interval; gain[l] is its amplifier gain at the interval end (device).
+// Every iteration covers nodes 0..M of every link; node 0 always reads
+// psi_0, so V_0 (identical at every iteration) is simply recomputed.
 template <typename T>
-int fft_forward(const Split& s, const cx<T>* data, cx<T>* scratch, cudaStream_t st) {
-    MPA_TRY(transpose_launch<T>(data, scratch, s.N1, s.N2, st));
-    KRParams<T> r{scratch, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
-    MPA_TRY(kr_launch<T>(KR_FWD, s.logN1, r, st));
-    KCParams<T> c{};
-    c.src = scratch;
-    c.dst = scratch;
-    c.N = s.N;
-    c.logN = s.logN;
-    c.N1 = (int)s.N1;
-    c.logN1 = s.logN1;
-    c.ncols = s.N1;
-    MPA_TRY(kc_launch<T>(KC_FWD, s.logN2, c, st));
+int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi0c, double2* state,
+               const NodeC* nodes, const int* loff, const double* gain, unsigned int* err, int scan_mode,
+               double2* out, cudaStream_t st) {
+    const long long N = s.N;
+    const int npl = M + 1;
+    for (int n = 0; n < n_iter; ++n) {
+        // steps 2-4 at every node (one launch per pass for all links)
+        KCParams<T> c{};
+        c.src = n == 0 ? psi0c : psi;
+        c.src_stride = n == 0 ? 0 : N;
+        c.src_lstride = n == 0 ? N : (long long)npl * N;
+        c.src0 = psi0c;
+        c.src0_lstride = N;
+        c.dst = psi;
+        c.dst_stride = N;
+        c.dst_lstride = (long long)npl * N;
+        c.N = N;
+        c.logN = s.logN;
+        c.N1 = (int)s.N1;
+        c.logN1 = s.logN1;
+        c.ncols = (long long)nl * npl * s.N1;
+        c.npl = npl;
+        c.nodes = nodes;
+        c.loff = loff;
+        MPA_TRY(kc_launch<T>(KC_MPA_PRE, s.logN2, c, st));
+        KRParams<T> r{psi, (long long)nl * npl * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
+        MPA_TRY(kr_launch<T>(KR_MPA, s.logN1, r, st));
+        c.src = psi;
+        c.src_stride = N;
+        c.src_lstride = (long long)npl * N;
+        c.src0 = nullptr;
+        MPA_TRY(kc_launch<T>(KC_MPA_POST, s.logN2, c, st));
+        // step 5 (Eq. (6)); on the last iteration fused with step 7
+        ScanParams<T> q{};
+        q.psi = psi;
+        q.N = N;
+        q.M = M;
+        q.psi0c = psi0c;
+        q.state = state;
+        q.psi0c_out = psi0c;
+        q.out = out;
+        q.mode = (n == n_iter - 1) ? scan_mode : 0;
+        q.nodes = nodes;
+        q.loff = loff;
+        q.gain = gain;
+        q.err = err;
+        MPA_TRY(scan_launch<T>(q, nl, st));
+    }
     return MPA_OK;
 }
 
-// Inverse: natural spectrum in `spec` (overwritten) -> natural A(t) in `out`.
-template <typename T>
-int fft_inverse(const Split& s, cx<T>* spec, cx<T>* out, cudaStream_t st) {
-    KCParams<T> c{};
-    c.src = spec;
-    c.dst = spec;
-    c.N = s.N;
-    c.logN = s.logN;
-    c.N1 = (int)s.N1;
-    c.logN1 = s.logN1;
-    c.ncols = s.N1;
-    MPA_TRY(kc_launch<T>(KC_INV, s.logN2, c, st));
-    KRParams<T> r{spec, s.N2, s.N, s.logN, (int)s.N2, (T)(1.0 / (double)s.N), T(0)};
-    MPA_TRY(kr_launch<T>(KR_INV, s.logN1, r, st));
-    MPA_TRY(transpose_launch<T>(spec, out, s.N2, s.N1, st));
-    return MPA_OK;
-}
+template int mpa_levels<float>(const Split&, int, int, int, float2*, float2*, double2*, const NodeC*, const int*,
+                               const double*, unsigned int*, int, double2*, cudaStream_t);
+template int mpa_levels<double>(const Split&, int, int, int, double2*, double2*, double2*, const NodeC*, const int*,
+                                const double*, unsigned int*, int, double2*, cudaStream_t);
 
-}  // namespace
+}  // namespace host
+}  // namespace mpa
 
 // ------------------------------------------------------------------ plan
 struct mpa_plan {
@@ -202,7 +102,7 @@ struct mpa_plan {
     int n_types;                // distinct interval starts within the DM period
     std::vector<NodeC> nodes;   // n_types x (M+1)
     size_t csize;               // bytes per complex sample
-    size_t off_psi, off_state, off_psi0c, off_nodes, off_err, ws_need;
+    size_t off_psi, off_state, off_psi0c, off_nodes, off_err, off_toff, off_gains, ws_need;
     // wavefront schedule (FP32): S = n_iter slots of B node buffers
     bool wf = false;
     int B = 0;
@@ -228,52 +128,15 @@ int interval_type(const mpa_plan* p, double z0, int* t) {
 }
 
 template <typename T>
-int run_interval(mpa_plan* p, int type, double gain, int scan_mode, double2* out, cudaStream_t st) {
-    const Split& s = p->sp;
-    const long long N = s.N;
-    cx<T>* psi = reinterpret_cast<cx<T>*>(p->ws + p->off_psi);
-    double2* state = reinterpret_cast<double2*>(p->ws + p->off_state);
-    cx<T>* psi0c = reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c);
-    const NodeC* nodes = reinterpret_cast<const NodeC*>(p->ws + p->off_nodes) + (size_t)type * (p->M + 1);
-    unsigned int* err = reinterpret_cast<unsigned int*>(p->ws + p->off_err);
-    for (int n = 0; n < p->n_iter; ++n) {
-        // steps 2-4 for every node of the interval; node 0 (psi_0 never
-        // changes, so V_0 is the same for every iteration) only on the first.
-        const int j0 = n == 0 ? 0 : 1;
-        const long long nn = p->M + 1 - j0;
-        KCParams<T> c{};
-        c.src = n == 0 ? psi0c : psi + N;
-        c.src_stride = n == 0 ? 0 : N;
-        c.dst = psi + (long long)j0 * N;
-        c.dst_stride = N;
-        c.N = N;
-        c.logN = s.logN;
-        c.N1 = (int)s.N1;
-        c.logN1 = s.logN1;
-        c.ncols = nn * s.N1;
-        c.nodes = nodes + j0;
-        MPA_TRY(kc_launch<T>(KC_MPA_PRE, s.logN2, c, st));
-        KRParams<T> r{psi + (long long)j0 * N, nn * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
-        MPA_TRY(kr_launch<T>(KR_MPA, s.logN1, r, st));
-        c.src = psi + (long long)j0 * N;
-        c.src_stride = N;
-        MPA_TRY(kc_launch<T>(KC_MPA_POST, s.logN2, c, st));
-        // step 5 (Eq. (6)); on the last iteration fused with step 7
-        ScanParams<T> q{};
-        q.psi = psi;
-        q.N = N;
-        q.M = p->M;
-        q.psi0c = psi0c;
-        q.state = state;
-        q.psi0c_out = psi0c;
-        q.out = out;
-        q.mode = (n == p->n_iter - 1) ? scan_mode : 0;
-        q.nodeM = p->nodes[(size_t)type * (p->M + 1) + p->M];
-        q.gain = gain;
-        q.err = err;
-        MPA_TRY(scan_launch<T>(q, st));
-    }
-    return MPA_OK;
+int run_interval(mpa_plan* p, int type, long n_amp, int scan_mode, double2* out, cudaStream_t st) {
+    const int* toff = reinterpret_cast<const int*>(p->ws + p->off_toff);
+    const double* gains = reinterpret_cast<const double*>(p->ws + p->off_gains);
+    if (n_amp < 0 || n_amp >= kMaxAmpsPerInterval) return MPA_ERR_GRID;
+    return mpa_levels<T>(p->sp, p->M, p->n_iter, 1, reinterpret_cast<cx<T>*>(p->ws + p->off_psi),
+                         reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c),
+                         reinterpret_cast<double2*>(p->ws + p->off_state),
+                         reinterpret_cast<const NodeC*>(p->ws + p->off_nodes), toff + type, gains + n_amp,
+                         reinterpret_cast<unsigned int*>(p->ws + p->off_err), scan_mode, out, st);
 }
 
 // Wavefront schedule of one interval (FP32): node blocks of B move through
@@ -305,7 +168,9 @@ int run_interval_wf(mpa_plan* p, int type, double gain, double2* out, cudaStream
         c.N1 = (int)s.N1;
         c.logN1 = s.logN1;
         c.ncols = (long long)count * s.N1;
+        c.npl = count;
         c.nodes = nodes + first;
+        c.loff = reinterpret_cast<const int*>(p->ws + p->off_toff);  // entry 0 is offset 0
         return kc_launch<float>(mode, s.logN2, c, st);
     };
     auto kr = [&](float2* data, int count) {
@@ -371,14 +236,14 @@ int propagate_t(mpa_plan* p, void* field, double z_from, double z_to, cudaStream
     if (!whole(z_from / L, &qf) || !whole((z_to - z_from) / L, &ni)) return MPA_ERR_GRID;
     const long n_int = (long)ni;
     std::vector<int> types((size_t)n_int);
-    std::vector<double> gains((size_t)n_int);
+    std::vector<long> amps((size_t)n_int);
     for (long q = 0; q < n_int; ++q) {
         const double z0 = z_from + L * (double)q;
         if (p->map.amps(z0, z0 + L - 1e-6 * L) != 0) return MPA_ERR_GRID;
         int t;
         if (interval_type(p, z0, &t) != MPA_OK) return MPA_ERR_GRID;
         types[(size_t)q] = t;
-        gains[(size_t)q] = std::exp((double)p->map.amps(z0, z0 + L) * p->map.z_a * p->map.gamma);
+        amps[(size_t)q] = p->map.amps(z0, z0 + L);
     }
     cx<T>* f = reinterpret_cast<cx<T>*>(field);
     cx<T>* psi = reinterpret_cast<cx<T>*>(p->ws + p->off_psi);
@@ -389,8 +254,9 @@ int propagate_t(mpa_plan* p, void* field, double z_from, double z_to, cudaStream
     if (rc) return rc;
     MPA_TRY(to_state_launch<T>(psi, state, sizeof(T) == 4 ? psi0c : nullptr, s.N, st));
     for (long q = 0; q < n_int; ++q) {
-        rc = p->wf ? run_interval_wf(p, types[(size_t)q], gains[(size_t)q], nullptr, st)
-                   : run_interval<T>(p, types[(size_t)q], gains[(size_t)q], 1, nullptr, st);
+        rc = p->wf ? run_interval_wf(p, types[(size_t)q], std::exp((double)amps[(size_t)q] * p->map.z_a * p->map.gamma),
+                                     nullptr, st)
+                   : run_interval<T>(p, types[(size_t)q], amps[(size_t)q], 1, nullptr, st);
         if (rc) return rc;
     }
     // A(z_to) = F^-1[A_hat]
@@ -410,7 +276,7 @@ int interval_t(mpa_plan* p, const void* psi0, void* psiM, double z0, cudaStream_
     MPA_TRY(cudaMemcpyAsync(state, psi0, (size_t)p->sp.N * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     if (sizeof(T) == 4) MPA_TRY(from_state_launch<T>(state, psi0c, p->sp.N, st));
     if (p->wf) return run_interval_wf(p, t, 1.0, reinterpret_cast<double2*>(psiM), st);
-    return run_interval<T>(p, t, 1.0, 2, reinterpret_cast<double2*>(psiM), st);
+    return run_interval<T>(p, t, 0, 2, reinterpret_cast<double2*>(psiM), st);
 }
 
 template <typename T>
@@ -535,7 +401,9 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
         p->off_psi0c = align256(p->off_state + N * sizeof(double2));
         p->off_psi = p->off_work;  // scratch of the entry/exit transforms
         p->off_nodes = align256(p->off_psi0c + N * sizeof(float2));
-        p->off_err = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
+        p->off_toff = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
+        p->off_gains = align256(p->off_toff + (size_t)p->n_types * sizeof(int));
+        p->off_err = align256(p->off_gains + kMaxAmpsPerInterval * sizeof(double));
         p->ws_need = align256(p->off_err + sizeof(unsigned int));
         *out = p;
         return MPA_OK;
@@ -547,7 +415,9 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
     if (p->prec == MPA_FP64) p->off_psi0c = p->off_state;  // the FP64 state is its own working copy
     const size_t after_psi0c = p->prec == MPA_FP32 ? p->off_psi0c + psi0c_bytes : p->off_state + N * sizeof(double2);
     p->off_nodes = align256(after_psi0c);
-    p->off_err = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
+    p->off_toff = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
+    p->off_gains = align256(p->off_toff + (size_t)p->n_types * sizeof(int));
+    p->off_err = align256(p->off_gains + kMaxAmpsPerInterval * sizeof(double));
     p->ws_need = align256(p->off_err + sizeof(unsigned int));
     *out = p;
     return MPA_OK;
@@ -566,6 +436,12 @@ int mpa_plan_set_workspace(mpa_plan* p, void* ws, size_t bytes) {
     p->ws_bytes = bytes;
     MPA_TRY(cudaMemcpy(p->ws + p->off_nodes, p->nodes.data(), p->nodes.size() * sizeof(NodeC),
                        cudaMemcpyHostToDevice));
+    std::vector<int> toff((size_t)p->n_types);
+    for (int t = 0; t < p->n_types; ++t) toff[(size_t)t] = t * (p->M + 1);
+    MPA_TRY(cudaMemcpy(p->ws + p->off_toff, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    double gains[kMaxAmpsPerInterval];
+    for (int a = 0; a < kMaxAmpsPerInterval; ++a) gains[a] = std::exp((double)a * p->map.z_a * p->map.gamma);
+    MPA_TRY(cudaMemcpy(p->ws + p->off_gains, gains, sizeof(gains), cudaMemcpyHostToDevice));
     MPA_TRY(cudaMemset(p->ws + p->off_err, 0, sizeof(unsigned int)));
     return MPA_OK;
 }
@@ -665,7 +541,7 @@ const char* mpa_status_string(int status) {
     return "unknown status";
 }
 
-const char* mpa_last_cuda_error(void) { return g_cuda_err.c_str(); }
+const char* mpa_last_cuda_error(void) { return mpa::host::g_cuda_err.c_str(); }
 
 int64_t mpa_kernel_launches(void) { return (int64_t)g_launches.load(); }
 

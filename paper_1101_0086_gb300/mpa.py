@@ -42,10 +42,16 @@ class _PlanParams(ctypes.Structure):
                 ("schedule", ctypes.c_int32)]
 
 
+class _Link(ctypes.Structure):
+    _fields_ = [("map", _FiberMap), ("N", ctypes.c_int64), ("T_ps", ctypes.c_double), ("z_to_km", ctypes.c_double),
+                ("field", ctypes.c_void_p)]
+
+
 EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
            "mpa_interval", "mpa_plan_status", "mpa_plan_destroy", "ss_workspace_size", "ss_propagate",
            "mpa_fft", "mpa_status_string", "mpa_last_cuda_error", "mpa_kernel_launches", "mpa_profile",
-           "mpa_profile_read", "mpa_profile_kind_name", "mpa_fft_noalloc")
+           "mpa_profile_read", "mpa_profile_kind_name", "mpa_fft_noalloc", "mpa_batch_create",
+           "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate", "mpa_batch_destroy")
 
 
 def library_path() -> str:
@@ -72,6 +78,14 @@ def lib() -> ctypes.CDLL:
         L.ss_propagate.argtypes = [ctypes.POINTER(_FiberMap), i64, dbl, dbl, i32, vp, dbl, dbl, vp, ctypes.c_size_t, vp]
         L.mpa_fft.argtypes = [i64, i32, i32, vp, vp, ctypes.c_size_t, vp]
         L.mpa_fft_noalloc.argtypes = [i64, i32, i32, vp, vp]
+        L.mpa_batch_create.argtypes = [ctypes.POINTER(_Link), i32, dbl, i32, i32, i32, ctypes.POINTER(vp)]
+        L.mpa_batch_workspace_size.argtypes = [vp, szp]
+        L.mpa_batch_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+        L.mpa_batch_propagate.argtypes = [vp, i32, vp]
+        L.mpa_batch_destroy.argtypes = [vp]
+        L.mpa_batch_destroy.restype = None
+        for f in ("mpa_batch_create", "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate"):
+            getattr(L, f).restype = ctypes.c_int
         L.mpa_fft_noalloc.restype = ctypes.c_int
         L.mpa_status_string.argtypes = [ctypes.c_int]
         L.mpa_status_string.restype = ctypes.c_char_p
@@ -180,6 +194,50 @@ class Plan:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib().mpa_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent links propagated together (``mpa_batch_*``): links of equal
+    N share launches, groups of different N run as parallel branches of one
+    CUDA graph.  ``links`` is a list of (fiber, T_ps, z_to_km, field) with
+    CUDA fields of the batch precision, updated in place by ``propagate``."""
+
+    def __init__(self, links, L_km: float, M: int, n_iter: int, precision="fp32", device="cuda"):
+        L = lib()
+        self.prec = _prec(precision)
+        self.dtype = _cdtype(self.prec)
+        keep = []
+        arr = (_Link * len(links))()
+        for i, (fiber, T_ps, z_to, field) in enumerate(links):
+            ptr = _field_ptr(field, self.dtype, field.numel(), "Batch")
+            fm, segs = _fiber_struct(fiber)
+            keep.append(segs)
+            arr[i] = _Link(fm, field.numel(), float(T_ps), float(z_to), ptr)
+        self._keep = keep
+        self.fields = [l[3] for l in links]
+        h = ctypes.c_void_p()
+        _check(L.mpa_batch_create(arr, len(links), float(L_km), int(M), int(n_iter), self.prec, ctypes.byref(h)),
+               "mpa_batch_create")
+        self._h = h
+        n = ctypes.c_size_t()
+        _check(L.mpa_batch_workspace_size(h, ctypes.byref(n)), "mpa_batch_workspace_size")
+        self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=device)
+        _check(L.mpa_batch_set_workspace(h, ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel()),
+               "mpa_batch_set_workspace")
+
+    def propagate(self, use_graph: bool = True, stream=None) -> None:
+        _check(lib().mpa_batch_propagate(self._h, 1 if use_graph else 0, _stream(stream)), "mpa_batch_propagate")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().mpa_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

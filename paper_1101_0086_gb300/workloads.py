@@ -230,3 +230,45 @@ def chirped_gaussian(N: int, T_ps: float, t0_ps: float, peak_mW: float, chirp: f
     tc = 0.5 * T_ps if centre_ps is None else centre_ps
     d = (t - tc + 0.5 * T_ps) % T_ps - 0.5 * T_ps
     return math.sqrt(peak_mW * 1e-3) * np.exp(-(1.0 + 1j * chirp) * d * d / (2.0 * t0_ps * t0_ps))
+
+
+@dataclasses.dataclass(frozen=True)
+class LinkSpec:
+    """One link of a batch: its own window, channels, power, sigma and length."""
+
+    N: int
+    T_ps: float
+    n_channels: int
+    peak_mW: float
+    sigma: float
+    spans: int
+    seed: int
+
+    @property
+    def fiber(self) -> FiberMap:
+        return dm_map(self.spans, sigma=self.sigma)
+
+    @property
+    def length_km(self) -> float:
+        return 50.0 * self.spans
+
+    def field(self) -> np.ndarray:
+        # slots of 100 ps sampled at 256 points: the 16-channel comb (+-375 GHz)
+        # stays well inside the +-1.28 THz band of the grid
+        return wdm_field(self.N, self.T_ps, self.n_channels, 50.0, self.N // 256, 30.0, self.peak_mW, "qpsk",
+                         self.seed)
+
+
+def batch_links(n_links: int = 256, seed: int = 3, log2_n=(12, 18), spans=(1, 20)) -> List[LinkSpec]:
+    """Seeded batch of independent links: N uniform in 2^12..2^18, channel
+    count in {2, 4, 8, 16}, 1-20 DM spans, sigma uniform in [1.0, 1.6] /W/km,
+    launch (peak) power uniform in [0.5, 4] mW; all on the benchmark DM map."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_links):
+        logn = int(rng.integers(log2_n[0], log2_n[1] + 1))
+        N = 1 << logn
+        out.append(LinkSpec(N=N, T_ps=100.0 * (N // 256), n_channels=int(rng.choice([2, 4, 8, 16])),
+                            peak_mW=float(rng.uniform(0.5, 4.0)), sigma=float(rng.uniform(1.0, 1.6)),
+                            spans=int(rng.integers(spans[0], spans[1] + 1)), seed=1000 + i))
+    return out

@@ -206,3 +206,44 @@ def test_largest_workload_sampled_interval_and_split_step(M):
     ref_ss = oracle.ss(A0, w.fiber, w.T_ps, 0.0, 0.1, 0.05)
     got_ss = host(M.ss_propagate(dev(A0, "fp64"), w.fiber, w.T_ps, 0.05, 0.0, 0.1))
     assert oracle.rel_l2(got_ss, ref_ss) < TOL["fp64"]
+
+
+# ------------------------------------------------------ batched links
+def _batch_specs():
+    from paper_1101_0086_gb300.workloads import batch_links
+    return batch_links(n_links=7, seed=5, log2_n=(12, 14), spans=(1, 3))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_equals_single_link_plans(M, prec):
+    # every link of a batch gets exactly what a plan of its own computes
+    specs = _batch_specs()
+    L, Mn, n_iter = 5.0, 20, 3
+    fields = [dev(s.field(), prec) for s in specs]
+    b = M.Batch([(s.fiber, s.T_ps, s.length_km, f) for s, f in zip(specs, fields)], L, Mn, n_iter, precision=prec)
+    b.propagate(use_graph=False)
+    for s, f in zip(specs, fields):
+        plan = M.Plan(s.fiber, s.N, s.T_ps, L, Mn, n_iter, precision=prec)
+        ref = host(plan.propagate(dev(s.field(), prec), 0.0, s.length_km))
+        assert oracle.rel_l2(host(f), ref) < (1e-13 if prec == "fp64" else 1e-6)
+
+
+def test_batch_graph_replay_and_oracle(M):
+    specs = _batch_specs()
+    L, Mn, n_iter = 5.0, 20, 3
+    fa = [dev(s.field(), "fp32") for s in specs]
+    fb = [dev(s.field(), "fp32") for s in specs]
+    a = M.Batch([(s.fiber, s.T_ps, s.length_km, f) for s, f in zip(specs, fa)], L, Mn, n_iter)
+    b = M.Batch([(s.fiber, s.T_ps, s.length_km, f) for s, f in zip(specs, fb)], L, Mn, n_iter)
+    for _ in range(2):  # first graph call captures (and runs directly), the second replays
+        a.propagate(use_graph=True)
+        b.propagate(use_graph=False)
+    for x, y in zip(fa, fb):
+        assert oracle.rel_l2(host(x), host(y)) < 1e-6
+    # one link of the batch against the oracle (one propagation)
+    s = specs[0]
+    f = dev(s.field(), "fp32")
+    c = M.Batch([(s.fiber, s.T_ps, s.length_km, f)], L, Mn, n_iter)
+    c.propagate(use_graph=True)
+    ref = oracle.mpa(s.field(), s.fiber, s.T_ps, 0.0, s.length_km, L, Mn, n_iter)
+    assert oracle.rel_l2(host(f), ref) < TOL["fp32"]
