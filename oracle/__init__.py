@@ -7,16 +7,23 @@ radix-2 FFT, FP64 phases from their definition, the literal MPA steps 1-7
 with the full (M+1) x N node array (Eq. (6)), and the composite split-step
 of Eq. (4).  It shares no code with the CUDA library.
 
+The adjoints (``mpa_adjoint``, ``ss_adjoint``) are the reverse mode of the
+same discrete methods, for gradients of a real loss with respect to the
+input field and the per-segment sigma and beta2.
+
 Parity unpinned: none -- every function here is pinned by the CPU tests
 (brute-force DFT, sigma=0 closed form, L2 conservation, the sech soliton,
-the accuracy theory of Eqs. (5)-(7)).
+the accuracy theory of Eqs. (5)-(7); the adjoints by central finite
+differences of the forward methods, the sigma=0 linear adjoint, exact
+gradients of a conserved quantity, and the scaling identity of the cubic
+term).
 """
 from __future__ import annotations
 
 import ctypes
 import os
 import subprocess
-from typing import Optional, Tuple
+from typing import NamedTuple, Optional, Tuple
 
 import numpy as np
 
@@ -55,7 +62,15 @@ def _load() -> ctypes.CDLL:
         lib.oracle_mpa_interval.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
-        for f in (lib.oracle_fft, lib.oracle_mpa, lib.oracle_ss, lib.oracle_mpa_interval):
+        lib.oracle_mpa_adjoint.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp,
+                                           ctypes.c_int]
+        lib.oracle_ss_adjoint.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, dp, dp, dp, dp, dp, dp]
+        for f in (lib.oracle_fft, lib.oracle_mpa, lib.oracle_ss, lib.oracle_mpa_interval, lib.oracle_mpa_adjoint,
+                  lib.oracle_ss_adjoint):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -120,6 +135,48 @@ def ss(field, fiber, T_ps: float, z_from: float, z_to: float, dz: float) -> np.n
                            a.size, float(T_ps), float(z_from), float(z_to), float(dz), _dp(a.view(np.float64)))
     _check(rc, "ss")
     return a
+
+
+class Gradients(NamedTuple):
+    """Reverse-mode results: gradient of the input field, dl/dsigma and
+    dl/dbeta2 per physical segment (period-major), and the forward output."""
+    field: np.ndarray
+    sigma: np.ndarray
+    beta2: np.ndarray
+    out: np.ndarray
+
+
+def _adj_buffers(field, grad_out, fiber):
+    a = _cfield(field)
+    g = _cfield(grad_out)
+    n_phys = fiber.n_periods * len(fiber.segments)
+    return a, g, np.empty_like(a), np.empty(n_phys), np.empty(n_phys), np.empty_like(a)
+
+
+def mpa_adjoint(field, grad_out, fiber, T_ps: float, z_from: float, z_to: float, L: float, M: int, n_tot: int,
+                n_threads: int = 0) -> Gradients:
+    """Reverse mode of :func:`mpa` for a real loss with output gradient
+    grad_out (dl/dRe + i dl/dIm)."""
+    a, g, gi, gs, gb, out = _adj_buffers(field, grad_out, fiber)
+    rows = _rows(fiber)
+    rc = _load().oracle_mpa_adjoint(_dp(rows), rows.shape[0], fiber.gamma_per_km, fiber.z_a_km, fiber.n_periods,
+                                    a.size, float(T_ps), float(z_from), float(z_to), float(L), int(M), int(n_tot),
+                                    _dp(a.view(np.float64)), _dp(g.view(np.float64)), _dp(gi.view(np.float64)),
+                                    _dp(gs), _dp(gb), _dp(out.view(np.float64)), int(n_threads))
+    _check(rc, "mpa_adjoint")
+    return Gradients(gi, gs, gb, out)
+
+
+def ss_adjoint(field, grad_out, fiber, T_ps: float, z_from: float, z_to: float, dz: float) -> Gradients:
+    """Reverse mode of :func:`ss`."""
+    a, g, gi, gs, gb, out = _adj_buffers(field, grad_out, fiber)
+    rows = _rows(fiber)
+    rc = _load().oracle_ss_adjoint(_dp(rows), rows.shape[0], fiber.gamma_per_km, fiber.z_a_km, fiber.n_periods,
+                                   a.size, float(T_ps), float(z_from), float(z_to), float(dz),
+                                   _dp(a.view(np.float64)), _dp(g.view(np.float64)), _dp(gi.view(np.float64)),
+                                   _dp(gs), _dp(gb), _dp(out.view(np.float64)))
+    _check(rc, "ss_adjoint")
+    return Gradients(gi, gs, gb, out)
 
 
 def rel_l2(a, b) -> float:

@@ -56,6 +56,24 @@ int oracle_mpa_interval(const double* seg_rows, int n_seg, double gamma, double 
                         long N, double T, double z0, double L, int M, int n_tot,
                         const double* psi0, double* psiM, int n_threads);
 
+/* Reverse mode of oracle_mpa for a real loss l of the output field.  Given
+ * the input field and g_out = dl/dRe A_out + i dl/dIm A_out, writes the
+ * gradient of the input field (same convention), and dl/dsigma and
+ * dl/dbeta2 of every physical segment (n_periods x n_seg values, segment s
+ * of period p at p n_seg + s), and the output field if field_out != NULL.
+ * Forward with a checkpoint per interval; each interval's levels are
+ * recomputed and walked backwards (MPA steps 7..2, Eq. (6)). */
+int oracle_mpa_adjoint(const double* seg_rows, int n_seg, double gamma, double z_a, int n_periods,
+                       long N, double T, double z_from, double z_to, double L, int M, int n_tot,
+                       const double* field_in, const double* grad_out, double* grad_in,
+                       double* grad_sigma, double* grad_beta2, double* field_out, int n_threads);
+
+/* Reverse mode of oracle_ss (Eq. (4)), same arguments and conventions. */
+int oracle_ss_adjoint(const double* seg_rows, int n_seg, double gamma, double z_a, int n_periods,
+                      long N, double T, double z_from, double z_to, double dz,
+                      const double* field_in, const double* grad_out, double* grad_in,
+                      double* grad_sigma, double* grad_beta2, double* field_out);
+
 #ifdef __cplusplus
 }
 #endif
