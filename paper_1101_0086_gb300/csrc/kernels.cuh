@@ -100,8 +100,14 @@ template <typename T> __device__ __forceinline__ void kahan_add(T& s, T& c, T v)
     s = t;
 }
 
+#ifndef MPA_KC_MINB
+#define MPA_KC_MINB 2
+#endif
+#ifndef MPA_KR_MINB
+#define MPA_KR_MINB 2
+#endif
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MPA_KC_MINB : 1)
     kc_kernel(const KCParams<T> p) {
     typedef cx<T> C;
     typedef KCGeom<T, L> Gm;
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? 2 
 }
 
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MPA_KR_MINB : 1)
     kr_kernel(const KRParams<T> p) {
     typedef cx<T> C;
     typedef KRGeom<T, L> Gm;
