@@ -137,6 +137,45 @@ MPA_API int mpa_plan_status(mpa_plan* plan, mpa_stream stream);
 
 MPA_API void mpa_plan_destroy(mpa_plan* plan);
 
+/* ---- Reverse mode (gradients of a real loss) ----------------------------
+ * The reverse mode of the discrete method that mpa_propagate runs (MPA steps
+ * 2-7 with Eq. (6), walked backwards), for a real loss l of the output field
+ * A_out.  A gradient of a complex quantity x is dl/dRe x + i dl/dIm x (the
+ * convention of torch's complex autograd).  Parameters are those of the
+ * physical segments: segment s of period p is index p n_segments + s, for
+ * n_periods x n_segments values (mpa_plan_n_segments).  The paper has no
+ * adjoint; this is the gradient of its method (beta2 and sigma enter through
+ * the phases beta(w, z_j) and sigma(z_j) of Eq. (6) and step 7).
+ *
+ * Memory: a checkpoint of A_hat (complex128) at every interval start, then,
+ * for one interval at a time, the node spectra of every level (2 n_iter
+ * buffers of (M+1) N samples) and two more node buffers.  Level-schedule
+ * plans only (MPA_SCHEDULE_WAVEFRONT plans are rejected with
+ * MPA_ERR_INVALID_ARG), and N >= 2^13 (MPA_ERR_UNSUPPORTED_N).
+ * The workspace is caller-owned device memory, 256-byte aligned. */
+MPA_API int mpa_plan_n_segments(const mpa_plan* plan, int32_t* n);
+MPA_API int mpa_adjoint_workspace_size(const mpa_plan* plan, double z_from_km, double z_to_km, size_t* bytes);
+
+/* mpa_propagate that also stores the checkpoints of [z_from, z_to] in the
+ * adjoint workspace (for a later mpa_adjoint with field_in = NULL). */
+MPA_API int mpa_propagate_checkpointed(mpa_plan* plan, void* field, double z_from_km, double z_to_km,
+                                       void* adj_workspace, size_t adj_bytes, mpa_stream stream);
+
+/* Gradients of l through mpa_propagate over [z_from, z_to].
+ *   field_in   the input field A(z_from) (device, precision's complex type), or
+ *              NULL: reuse the checkpoints of the last mpa_propagate_checkpointed
+ *              over the same range with the same workspace.
+ *   grad_out   dl/dA_out (device, N samples); not modified.
+ *   grad_in    receives dl/dA_in (device, N samples).
+ *   grad_sigma, grad_beta2   HOST arrays of n_periods x n_segments doubles
+ *              (either may be NULL); when any is given the call synchronises
+ *              the stream before returning.
+ * Errors: MPA_ERR_GRID as mpa_propagate; MPA_ERR_WORKSPACE if adj_bytes is
+ * below mpa_adjoint_workspace_size or the pointer is misaligned. */
+MPA_API int mpa_adjoint(mpa_plan* plan, const void* field_in, const void* grad_out, void* grad_in,
+                        double z_from_km, double z_to_km, void* adj_workspace, size_t adj_bytes,
+                        double* grad_sigma, double* grad_beta2, mpa_stream stream);
+
 /* Many independent links propagated together (no counterpart in the paper;
  * the batching of independent problems of the MPA node transforms).  Each
  * link has its own fiber map, N, window and length z_to (from z = 0, a

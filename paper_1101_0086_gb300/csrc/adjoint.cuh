@@ -1,0 +1,385 @@
+// Kernels of the reverse mode of one MPA interval (the adjoint of MPA steps
+// 2-7, Eq. (6)), for the gradient of a real loss l.  A gradient g of a
+// complex quantity x is dl/dRe x + i dl/dIm x (dl = Re(conj(g) dx)).
+//
+// Reverse of one level n, node j (forward: P = psi_j e^{i beta_j} pre_j,
+// A = F^-1[P], U = |A|^2 A, V_j = sigma_j dz F[U] e^{-i beta_j} / pre_j):
+//   KCA_G (column pass)  g_V_j  -> q = e^{+i beta_j} (dz / pre_j) g_V_j -> inverse column DFT
+//                        and the beta2 term sum_k (w_k^2/2) Im(conj(g_V) V)
+//   KC_MPA_PRE           psi_j  -> the inverse column DFT of P (as in the forward pass)
+//   KRA (row pass)       inverse row DFTs of both: A = (.)/N, g_U' = unnormalised (the
+//                        gradient of U over sigma_j, F^H = N F^-1);
+//                        g_A = sigma_j (2 |A|^2 g_U' + A^2 conj(g_U')) -> forward row DFT,
+//                        and the sigma term Re sum_n conj(g_U') U
+//   KCA_P (column pass)  forward column DFT -> g_psi_j = e^{-i beta_j} (pre_j / N) F[g_A]
+//                        and the beta2 term -sum_k (w_k^2/2) Im(conj(g_psi) psi)
+//   RSCAN                step 5 reversed: g_V_j = -i (w_j sum_{l>j} g_psi_l + [j>0] g_psi_j / 2),
+//                        w_0 = 1/2, w_j = 1; every g_psi_l also adds to the gradient of psi_0.
+//                        Its top form starts from the gradient of the interval output
+//                        (step 7 and the gain reversed) and adds that step's beta2 term.
+// Each tile of a column or row pass lies inside one node (the plan checks
+// G <= N1 and G <= N2), so every tile leaves one partial sum per reduction.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace mpa {
+
+enum { KCA_G = 0, KCA_P = 1 };
+enum { RSCAN_LEVEL = 0, RSCAN_TOP = 1, RSCAN_SUM = 2 };
+
+// Per-node constants of the reverse pass: dz / exp(int_{z0}^{z_j} G) and sigma(z_j).
+struct AdjC {
+    double dzp;
+    double sig;
+};
+
+template <typename T> struct KCAParams {
+    cx<T>* g;              // node j at g + j N, in/out
+    const cx<T>* aux;      // KCA_G: V_j; KCA_P: psi_j; node j at aux + j aux_stride
+    long long aux_stride;  // 0: every node reads aux
+    long long N;
+    int logN;
+    int N1, logN1;
+    long long ncols;       // (M+1) N1
+    const NodeC* nodes;    // this interval's node constants
+    const AdjC* adj;
+    double wscale;         // (2 pi / T)^2 / 2
+    double* part;          // one partial sum per tile
+};
+
+template <typename T> struct KRAParams {
+    const cx<T>* a;  // rows after the inverse column pass of P (KC MPA_PRE)
+    cx<T>* g;        // rows after KCA_G; overwritten with the forward row pass of g_A
+    long long nrows;
+    long long N;
+    int logN;
+    int N2;
+    T inv_n;
+    const AdjC* adj;
+    double* part;
+};
+
+template <typename T> struct RScanParams {
+    cx<T>* g;            // (M+1) x N
+    double2* gs0;        // gradient of psi_0 (accumulated)
+    long long N;
+    int M;
+    int mode;
+    const double2* gX;   // RSCAN_TOP: gradient of the interval output
+    const double2* X;    // RSCAN_TOP: the interval output
+    NodeC nodeM;         // RSCAN_TOP: step-7 phase
+    double scaleM;       // RSCAN_TOP: exp(-gamma L) times the gain
+    double wscale;
+    double* part;        // RSCAN_TOP: one partial sum per block
+};
+
+// Sum of v over the block (every thread passes its value; the result is
+// valid in thread 0).
+template <int NT> __device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NT / 32; ++i) s += red[i];
+    }
+    return s;
+}
+
+// Im(conj(a) b)
+template <typename C> __device__ __forceinline__ auto im_conj_mul(C a, C b) { return a.x * b.y - a.y * b.x; }
+
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) kca_kernel(const KCAParams<T> p) {
+    typedef cx<T> C;
+    typedef KCGeom<T, L> Gm;
+    typedef Tiling<T> P;
+    constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
+    constexpr bool INV = (MODE == KCA_G);
+    typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_COL, P::PSH, true> XF;
+    typedef Xform<T, L, G, NT, P::RMAX, -1, LAYOUT_COL, P::PSH, false> XI;
+    typedef typename std::conditional<INV, XI, XF>::type XA;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[NT / 32];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    C* olo = tlo + TwDims<L>::NLO;
+    C* ohi = olo + G * Gm::OLO;
+    const int tid = threadIdx.x;
+    const long long col0 = (long long)blockIdx.x * G;
+    const int N1m = p.N1 - 1;
+    constexpr bool FAST = sizeof(T) == 4;
+    const int node = (int)(col0 >> p.logN1);
+    const NodeC nc = p.nodes[node];
+    const AdjC ac = p.adj[node];
+    const C* aux = p.aux + (long long)node * p.aux_stride;
+    C* gn = p.g + (long long)node * p.N;
+
+    tw_init<T, L>(thi, tlo, tid, NT);
+    if constexpr (INV) {
+        for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
+            const int g = i % G, m = i / G;
+            const long long k1 = (col0 + g) & N1m;
+            if (m < Gm::OLO) olo[m * G + g] = expi_ratio<T>(-k1 * m, p.logN);
+            else ohi[(m - Gm::OLO) * G + g] = expi_ratio<T>(-k1 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+        }
+    }
+    __syncthreads();
+
+    double acc = 0.0;
+    C vin[XA::Q0][XA::R0];
+#pragma unroll
+    for (int q = 0; q < XA::Q0; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, XA::R0>(tid + q * NT, j, g);
+        const long long c = (col0 + g) & N1m;
+        unsigned long long th[XA::R0];
+        if constexpr (FAST && INV) phase_run<XA::R0>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::R0), nc, th);
+#pragma unroll
+        for (int r = 0; r < XA::R0; ++r) {
+            const long long idx = c + (long long)(j + r * (L / XA::R0)) * p.N1;
+            C v = gn[idx];
+            if constexpr (INV) {
+                const long long kk = signed_k(idx, p.N);
+                acc += (double)(kk * kk) * (double)im_conj_mul(v, aux[idx]);
+                C ph;
+                if constexpr (FAST) ph = expi_turns_poly(th[r]);
+                else ph = expi_turns<T>(phase_q64(kk, nc));
+                v = cscale(cmul(v, ph), (T)ac.dzp);
+            }
+            vin[q][r] = v;
+        }
+    }
+
+    C vout[XA::QL][XA::RL];
+    XA::run(vin, vout, s, thi, tlo);
+
+    const T post = (T)(nc.pre / (double)p.N);
+#pragma unroll
+    for (int q = 0; q < XA::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, XA::RL>(tid + q * NT, j, g);
+        const long long c = (col0 + g) & N1m;
+        unsigned long long th[XA::RL];
+        if constexpr (FAST && !INV) phase_run<XA::RL>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::RL), nc, th);
+#pragma unroll
+        for (int r = 0; r < XA::RL; ++r) {
+            const int row = j + r * (L / XA::RL);
+            const long long idx = c + (long long)row * p.N1;
+            C v = vout[q][r];
+            if constexpr (INV) {
+                C w = olo[(row & (Gm::OLO - 1)) * G + g];
+                if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
+                v = cmul(v, w);
+            } else {
+                const long long kk = signed_k(idx, p.N);
+                C ph;
+                if constexpr (FAST) ph = expi_turns_poly(th[r]);
+                else ph = expi_turns<T>(phase_q64(kk, nc));
+                v = cscale(cmul(v, cconj(ph)), post);
+                acc -= (double)(kk * kk) * (double)im_conj_mul(v, aux[idx]);
+            }
+            gn[idx] = v;
+        }
+    }
+    const double tot = block_sum<NT>(acc, red);
+    if (tid == 0) p.part[blockIdx.x] = tot * p.wscale;
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) kra_kernel(const KRAParams<T> p) {
+    typedef cx<T> C;
+    typedef KRGeom<T, L> Gm;
+    typedef Tiling<T, 1> P;
+    constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
+    typedef Xform<T, L, G, NT, P::RMAX, -1, LAYOUT_ROW, P::PSH, false> XI;
+    typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_ROW, P::PSH, true> XF;
+    static_assert(XI::RL == XF::R0, "inverse/forward junction radix");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[NT / 32];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    C* olo = tlo + TwDims<L>::NLO;
+    C* ohi = olo + G * Gm::OLO;
+    const int tid = threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * G;
+    const T sig = (T)p.adj[row0 / p.N2].sig;
+
+    tw_init<T, L>(thi, tlo, tid, NT);
+    for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
+        const int g = i / (Gm::OLO + Gm::OHI), m = i % (Gm::OLO + Gm::OHI);
+        const long long n2 = (row0 + g) & (p.N2 - 1);
+        if (m < Gm::OLO) olo[g * Gm::OLO + m] = expi_ratio<T>(n2 * m, p.logN);
+        else ohi[g * Gm::OHI + (m - Gm::OLO)] = expi_ratio<T>(n2 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+    }
+    __syncthreads();
+
+    // A(t) and the unnormalised inverse of q, on the same element layout
+    C va[XI::QL][XI::RL], vg[XI::QL][XI::RL];
+    {
+        C vin[XI::Q0][XI::R0];
+#pragma unroll
+        for (int q = 0; q < XI::Q0; ++q) {
+            int j, g;
+            bmap<LAYOUT_ROW, L, G, XI::R0>(tid + q * NT, j, g);
+            const C* src = p.a + (row0 + g) * L;
+#pragma unroll
+            for (int r = 0; r < XI::R0; ++r) vin[q][r] = src[j + r * (L / XI::R0)];
+        }
+        XI::run(vin, va, s, thi, tlo);
+    }
+    {
+        C vin[XI::Q0][XI::R0];
+#pragma unroll
+        for (int q = 0; q < XI::Q0; ++q) {
+            int j, g;
+            bmap<LAYOUT_ROW, L, G, XI::R0>(tid + q * NT, j, g);
+            const C* src = p.g + (row0 + g) * L;
+#pragma unroll
+            for (int r = 0; r < XI::R0; ++r) vin[q][r] = src[j + r * (L / XI::R0)];
+        }
+        XI::run(vin, vg, s, thi, tlo);
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < XI::QL; ++q) {
+#pragma unroll
+        for (int r = 0; r < XI::RL; ++r) {
+            const C a = cscale(va[q][r], p.inv_n);
+            const C gu = vg[q][r];
+            const T pw = a.x * a.x + a.y * a.y;
+            acc += (double)(pw * (gu.x * a.x + gu.y * a.y));  // Re(conj(g_U') U)
+            const C a2 = mkc(a.x * a.x - a.y * a.y, T(2) * a.x * a.y);
+            const C t = cmul(a2, cconj(gu));
+            vg[q][r] = mkc(sig * (T(2) * pw * gu.x + t.x), sig * (T(2) * pw * gu.y + t.y));
+        }
+    }
+    C vout[XF::QL][XF::RL];
+    XF::run(vg, vout, s, thi, tlo);
+#pragma unroll
+    for (int q = 0; q < XF::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XF::RL>(tid + q * NT, j, g);
+        C* dst = p.g + (row0 + g) * L;
+#pragma unroll
+        for (int r = 0; r < XF::RL; ++r) {
+            const int l = j + r * (L / XF::RL);
+            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+            if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
+            dst[l] = cmul(vout[q][r], w);
+        }
+    }
+    const double tot = block_sum<NT>(acc, red);
+    if (tid == 0) p.part[blockIdx.x] = tot;
+}
+
+// Step 5 reversed for every frequency (see the header comment), and its
+// top and closing forms.
+template <typename T>
+__global__ void __launch_bounds__(256) rscan_kernel(const RScanParams<T> p) {
+    typedef cx<T> C;
+    __shared__ double red[8];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (k < p.N) {
+        C* g = p.g;
+        if (p.mode == RSCAN_TOP) {
+            // A_hat(z0+L) = psi_M e^{i beta_M} pre_M gain: g_psi_M = conj(e^{i beta_M} pre_M gain) g_X
+            const long long kk = signed_k(k, p.N);
+            const double2 ph = expi_turns<double>(phase_q64(kk, p.nodeM));
+            const double2 gx = p.gX[k], x = p.X[k];
+            const double2 gm = make_double2(p.scaleM * (ph.x * gx.x + ph.y * gx.y),
+                                            p.scaleM * (ph.x * gx.y - ph.y * gx.x));
+            acc = -(double)(kk * kk) * (gx.x * x.y - gx.y * x.x);
+            double2 s0 = p.gs0[k];
+            p.gs0[k] = make_double2(s0.x + gm.x, s0.y + gm.y);
+            // g_V_j = -i w_j g_psi_M with w_0 = w_M = 1/2
+            const C full = mkc((T)gm.y, (T)(-gm.x)), half = mkc((T)(0.5 * gm.y), (T)(-0.5 * gm.x));
+            g[k] = half;
+            for (int j = 1; j < p.M; ++j) g[(long long)j * p.N + k] = full;
+            g[(long long)p.M * p.N + k] = half;
+        } else if (p.mode == RSCAN_LEVEL) {
+            T tx = T(0), ty = T(0), cx_ = T(0), cy_ = T(0);  // sum_{l>j} g_psi_l (compensated in FP32)
+            double sx = 0.0, sy = 0.0;
+            for (int j = p.M; j >= 0; --j) {
+                C* q = g + (long long)j * p.N + k;
+                const C gl = *q;
+                sx += (double)gl.x;
+                sy += (double)gl.y;
+                const T ux = tx - cx_, uy = ty - cy_;
+                const T ax = j == 0 ? T(0.5) * ux : ux + T(0.5) * gl.x;
+                const T ay = j == 0 ? T(0.5) * uy : uy + T(0.5) * gl.y;
+                *q = mkc(ay, -ax);
+                if (j > 0) {
+                    if constexpr (sizeof(T) == 4) {
+                        kahan_add(tx, cx_, gl.x);
+                        kahan_add(ty, cy_, gl.y);
+                    } else {
+                        tx += gl.x;
+                        ty += gl.y;
+                    }
+                }
+            }
+            double2 s0 = p.gs0[k];
+            p.gs0[k] = make_double2(s0.x + sx, s0.y + sy);
+        } else {
+            double sx = 0.0, sy = 0.0;
+            for (int j = 0; j <= p.M; ++j) {
+                const C gl = g[(long long)j * p.N + k];
+                sx += (double)gl.x;
+                sy += (double)gl.y;
+            }
+            double2 s0 = p.gs0[k];
+            p.gs0[k] = make_double2(s0.x + sx, s0.y + sy);
+        }
+    }
+    if (p.mode == RSCAN_TOP) {
+        const double tot = block_sum<256>(acc, red);
+        if (threadIdx.x == 0) p.part[blockIdx.x] = tot * p.wscale;
+    }
+}
+
+// Eq. (6) partial sums of one level into a separate buffer (the forward scan
+// of level n without step 7), node 0 receiving psi_0: the same arithmetic
+// and order as the forward scan, so the recomputed levels equal the
+// forward pass's.
+template <typename T>
+__global__ void __launch_bounds__(256) scan_store_kernel(const cx<T>* __restrict__ v, cx<T>* __restrict__ psi,
+                                                         const cx<T>* __restrict__ psi0c, long long N, int M) {
+    typedef cx<T> C;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const C v0 = v[k];
+    T rx = T(0.5) * v0.x, ry = T(0.5) * v0.y, cxx = T(0), cyy = T(0);
+    const C p0 = psi0c[k];
+    psi[k] = p0;
+    for (int j = 1; j <= M; ++j) {
+        const C vl = v[(long long)j * N + k];
+        const T sx = (rx - cxx) + T(0.5) * vl.x, sy = (ry - cyy) + T(0.5) * vl.y;
+        psi[(long long)j * N + k] = mkc(p0.x - sy, p0.y + sx);
+        if constexpr (sizeof(T) == 4) {
+            kahan_add(rx, cxx, vl.x);
+            kahan_add(ry, cyy, vl.y);
+        } else {
+            rx += vl.x;
+            ry += vl.y;
+        }
+    }
+}
+
+// state = scale * in (FP64).
+template <typename T>
+__global__ void __launch_bounds__(256) scale_to_state_kernel(const cx<T>* in, double2* state, double scale,
+                                                             long long N) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const cx<T> v = in[k];
+    state[k] = make_double2(scale * (double)v.x, scale * (double)v.y);
+}
+
+}  // namespace mpa

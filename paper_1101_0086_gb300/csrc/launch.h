@@ -15,7 +15,7 @@ extern std::atomic<long long> g_launches;
 // default; enabled through mpa_profile).
 enum {
     PK_KC_MPA_PRE = 0, PK_KC_MPA_POST, PK_KC_SS, PK_KC_FFT, PK_KR_MPA, PK_KR_SS, PK_KR_FFT, PK_SCAN, PK_AUX,
-    PK_KCW, PK_COUNT
+    PK_KCW, PK_KC_ADJ, PK_KR_ADJ, PK_ADJ_AUX, PK_COUNT
 };
 extern std::atomic<bool> g_prof_on;
 void prof_begin(cudaStream_t st);

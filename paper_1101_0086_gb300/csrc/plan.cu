@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "host.h"
+#include "plan.h"
 
 using namespace mpa;
 
@@ -93,25 +93,8 @@ template int mpa_levels<double>(const Split&, int, int, int, double2*, double2*,
 }  // namespace host
 }  // namespace mpa
 
-// ------------------------------------------------------------------ plan
-struct mpa_plan {
-    HostMap map;
-    Split sp;
-    double T, L;
-    int M, n_iter, prec;
-    int n_types;                // distinct interval starts within the DM period
-    std::vector<NodeC> nodes;   // n_types x (M+1)
-    size_t csize;               // bytes per complex sample
-    size_t off_psi, off_state, off_psi0c, off_nodes, off_err, off_toff, off_gains, ws_need;
-    // wavefront schedule (FP32): S = n_iter slots of B node buffers
-    bool wf = false;
-    int B = 0;
-    size_t off_work = 0, off_y0 = 0, off_R = 0, off_C = 0, off_D = 0;
-    unsigned char* ws = nullptr;
-    size_t ws_bytes = 0;
-};
-
-namespace {
+namespace mpa {
+namespace host {
 
 int interval_type(const mpa_plan* p, double z0, int* t) {
     if (p->n_types == 1) {
@@ -138,6 +121,13 @@ int run_interval(mpa_plan* p, int type, long n_amp, int scan_mode, double2* out,
                          reinterpret_cast<const NodeC*>(p->ws + p->off_nodes), toff + type, gains + n_amp,
                          reinterpret_cast<unsigned int*>(p->ws + p->off_err), scan_mode, out, st);
 }
+template int run_interval<float>(mpa_plan*, int, long, int, double2*, cudaStream_t);
+template int run_interval<double>(mpa_plan*, int, long, int, double2*, cudaStream_t);
+
+}  // namespace host
+}  // namespace mpa
+
+namespace {
 
 // Wavefront schedule of one interval (FP32): node blocks of B move through
 // the n_iter levels one step at a time; at step s level n works on block
@@ -561,7 +551,8 @@ int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* byte
 
 const char* mpa_profile_kind_name(int kind) {
     static const char* names[PK_COUNT] = {"kc_mpa_pre", "kc_mpa_post", "kc_ss_step", "kc_fft", "kr_mpa",
-                                          "kr_ss", "kr_fft", "scan", "aux", "kc_wavefront"};
+                                          "kr_ss", "kr_fft", "scan", "aux", "kc_wavefront",
+                                          "kc_adjoint", "kr_adjoint", "adjoint_aux"};
     return (kind >= 0 && kind < PK_COUNT) ? names[kind] : nullptr;
 }
 

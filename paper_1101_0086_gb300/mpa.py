@@ -51,7 +51,8 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "mpa_interval", "mpa_plan_status", "mpa_plan_destroy", "ss_workspace_size", "ss_propagate",
            "mpa_fft", "mpa_status_string", "mpa_last_cuda_error", "mpa_kernel_launches", "mpa_profile",
            "mpa_profile_read", "mpa_profile_kind_name", "mpa_fft_noalloc", "mpa_batch_create",
-           "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate", "mpa_batch_destroy")
+           "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate", "mpa_batch_destroy",
+           "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint")
 
 
 def library_path() -> str:
@@ -97,9 +98,15 @@ def lib() -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_double)]
         L.mpa_profile_read.restype = ctypes.c_int
         L.mpa_profile_kind_name.argtypes = [ctypes.c_int]
+        L.mpa_plan_n_segments.argtypes = [vp, ctypes.POINTER(i32)]
+        L.mpa_adjoint_workspace_size.argtypes = [vp, dbl, dbl, szp]
+        L.mpa_propagate_checkpointed.argtypes = [vp, vp, dbl, dbl, vp, ctypes.c_size_t, vp]
+        dptr = ctypes.POINTER(ctypes.c_double)
+        L.mpa_adjoint.argtypes = [vp, vp, vp, vp, dbl, dbl, vp, ctypes.c_size_t, dptr, dptr, vp]
         L.mpa_profile_kind_name.restype = ctypes.c_char_p
         for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
-                  "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft"):
+                  "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft",
+                  "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -183,6 +190,63 @@ class Plan:
                "mpa_interval")
         return out
 
+    @property
+    def n_segments(self) -> int:
+        """Physical segments of the link (n_periods x segments per period)."""
+        n = ctypes.c_int32()
+        _check(lib().mpa_plan_n_segments(self._h, ctypes.byref(n)), "mpa_plan_n_segments")
+        return int(n.value)
+
+    def adjoint_workspace_bytes(self, z_from_km: float, z_to_km: float) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().mpa_adjoint_workspace_size(self._h, float(z_from_km), float(z_to_km), ctypes.byref(n)),
+               "mpa_adjoint_workspace_size")
+        return int(n.value)
+
+    def _adj_ws(self, z_from_km, z_to_km, workspace):
+        # a caller's workspace goes to the library as is (it checks the size)
+        if workspace is None:
+            need = self.adjoint_workspace_bytes(z_from_km, z_to_km)
+            workspace = torch.empty(need, dtype=torch.uint8, device=self.workspace.device)
+        return workspace
+
+    def propagate_checkpointed(self, field: torch.Tensor, z_from_km: float, z_to_km: float,
+                               adj_workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """``mpa_propagate`` that also keeps the interval checkpoints in the
+        adjoint workspace (returned) for a later :meth:`adjoint` without the input."""
+        ws = self._adj_ws(z_from_km, z_to_km, adj_workspace)
+        ptr = _field_ptr(field, self.dtype, self.N, "propagate_checkpointed")
+        _check(lib().mpa_propagate_checkpointed(self._h, ptr, float(z_from_km), float(z_to_km),
+                                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+               "mpa_propagate_checkpointed")
+        return ws
+
+    def adjoint(self, grad_out: torch.Tensor, z_from_km: float, z_to_km: float,
+                field_in: Optional[torch.Tensor] = None, adj_workspace: Optional[torch.Tensor] = None,
+                params: bool = True, stream=None):
+        """Reverse mode (``mpa_adjoint``): returns (dl/dA_in, dl/dsigma, dl/dbeta2)
+        for the output gradient grad_out; the last two are float64 numpy arrays
+        per physical segment (None unless ``params``).  Without ``field_in`` the
+        checkpoints of the last :meth:`propagate_checkpointed` in
+        ``adj_workspace`` are used."""
+        import numpy as np
+        if field_in is None and adj_workspace is None:
+            raise ValueError("adjoint: give field_in or the workspace of propagate_checkpointed")
+        ws = self._adj_ws(z_from_km, z_to_km, adj_workspace)
+        go = _field_ptr(grad_out, self.dtype, self.N, "adjoint grad_out")
+        fi = _field_ptr(field_in, self.dtype, self.N, "adjoint field_in") if field_in is not None else None
+        gi = torch.empty_like(grad_out)
+        gs = gb = None
+        ps = pb = None
+        if params:
+            gs = np.zeros(self.n_segments)
+            gb = np.zeros(self.n_segments)
+            ps = gs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            pb = gb.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().mpa_adjoint(self._h, fi, go, ctypes.c_void_p(gi.data_ptr()), float(z_from_km), float(z_to_km),
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), ps, pb, _stream(stream)), "mpa_adjoint")
+        return gi, gs, gb
+
     def status(self, stream=None) -> bool:
         """False if a NaN/Inf was produced since the last call (synchronises)."""
         rc = lib().mpa_plan_status(self._h, _stream(stream))
@@ -201,6 +265,36 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class MPAFunction(torch.autograd.Function):
+    """Differentiable MPA propagation through the hand-written reverse mode.
+
+    ``MPAFunction.apply(field, sigma, beta2, plan, z_from_km, z_to_km)``
+    returns ``plan.propagate`` of a copy of ``field``.  ``sigma`` and
+    ``beta2`` are float64 tensors of the plan's per-physical-segment
+    coefficients (``plan.n_segments`` values, period-major); they must hold
+    the values the plan was created with, and they receive dl/dsigma and
+    dl/dbeta2 when they require gradients.  The forward pass stores the
+    interval checkpoints; the backward pass is ``mpa_adjoint``."""
+
+    @staticmethod
+    def forward(ctx, field, sigma, beta2, plan, z_from_km, z_to_km):
+        out = field.detach().clone()
+        ws = plan.propagate_checkpointed(out, z_from_km, z_to_km)
+        ctx.plan, ctx.ws, ctx.z = plan, ws, (z_from_km, z_to_km)
+        ctx.param_shape = (sigma.shape, sigma.dtype, sigma.device, beta2.shape, beta2.dtype, beta2.device)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        plan = ctx.plan
+        want_p = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+        gi, gs, gb = plan.adjoint(grad_out.contiguous(), ctx.z[0], ctx.z[1], adj_workspace=ctx.ws, params=want_p)
+        ss, sd, sdev, bs, bd, bdev = ctx.param_shape
+        g_sig = torch.as_tensor(gs, dtype=sd, device=sdev).reshape(ss) if (want_p and ctx.needs_input_grad[1]) else None
+        g_b2 = torch.as_tensor(gb, dtype=bd, device=bdev).reshape(bs) if (want_p and ctx.needs_input_grad[2]) else None
+        return gi, g_sig, g_b2, None, None, None
 
 
 class Batch:

@@ -202,11 +202,18 @@ def _wl2() -> Workload:
                     dm_map(100, beta3=0.08), 0.05, 5.0, 142, 3)
 
 
-WORKLOADS = {"0": _wl0, "1": _wl1, "2": _wl2}
+def _wl4() -> Workload:
+    # gradients: 16 ch @ 50 GHz, 512 QPSK symbols per channel in 100 ps slots,
+    # N=2^20, 20 spans (1000 km); the method settings of the 2^20 link
+    return Workload("wdm16_qpsk512_n2p20_1000km", 1 << 20, 51200.0, 16, 50.0, 512, 30.0, 2.0, "qpsk", 4,
+                    dm_map(20), 0.05, 5.0, 142, 3)
+
+
+WORKLOADS = {"0": _wl0, "1": _wl1, "2": _wl2, "4": _wl4}
 
 
 def workload(key: str) -> Workload:
-    """Named workload by index ("0", "1", "2") or by name."""
+    """Named workload by index ("0", "1", "2", "4") or by name."""
     if key in WORKLOADS:
         return WORKLOADS[key]()
     for f in WORKLOADS.values():

@@ -1,0 +1,218 @@
+"""GPU parity of the reverse mode (``mpa_adjoint``) against the FP64 CPU
+oracle's adjoint, plus properties that hold at any size: central finite
+differences of the GPU's own FP64 forward pass and the scaling identity of
+the cubic term (sigma -> c sigma, A -> A / sqrt(c) maps the output to
+output / sqrt(c), so sum_P sigma_P dl/dsigma_P - Re<g_A, A>/2 = -Re<g_out, out>/2).
+
+Tolerances: FP64 runs 1e-10 (rel. L2 of the field gradient) and 1e-9 (each
+parameter gradient relative to the largest); FP32 runs 1e-4 and 1e-3."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_0086_gb300.workloads import FiberMap, Segment, dm_map, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL_FIELD = {"fp64": 1e-10, "fp32": 1e-4}
+TOL_PARAM = {"fp64": 1e-9, "fp32": 1e-3}
+Z, L, MN, NIT = 2.0, 0.5, 10, 3
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    from paper_1101_0086_gb300 import build as B
+    from paper_1101_0086_gb300 import mpa
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    B.build()
+    mpa.lib()
+    return mpa
+
+
+def dev(x, prec):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex64 if prec == "fp32" else np.complex128)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def toy_fiber(flat=False, d_sigma=None, d_beta2=None):
+    """Two segments per 1 km period (sigma and beta2 differ), 2 periods,
+    loss restored by an amplifier at the end of each period."""
+    segs = [Segment(0.6, -1.0, 0.1, 1.0), Segment(0.4, 2.0, 0.05, 0.7)]
+    if not flat:
+        return FiberMap(tuple(segs), 0.05, 1.0, 2)
+    segs = segs * 2
+    for P, d in (d_sigma or {}).items():
+        s = segs[P]
+        segs[P] = Segment(s.length_km, s.beta2_ps2_per_km, s.beta3_ps3_per_km, s.sigma_per_W_km + d)
+    for P, d in (d_beta2 or {}).items():
+        s = segs[P]
+        segs[P] = Segment(s.length_km, s.beta2_ps2_per_km + d, s.beta3_ps3_per_km, s.sigma_per_W_km)
+    return FiberMap(tuple(segs), 0.05, 1.0, 1)
+
+
+def toy_field(N, seed=3):
+    """Gaussian pulses (t0 = 1.5 ps, 0.5 W) at seeded positions and phases on
+    a 0.05 ps grid."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    T = 0.05 * N
+    t = np.arange(N) * (T / N)
+    A = np.zeros(N, dtype=np.complex128)
+    for _ in range(max(4, N // 4096)):
+        c, ph = rng.uniform(0, T), rng.uniform(0, 2 * np.pi)
+        d = (t - c + 0.5 * T) % T - 0.5 * T
+        A += np.sqrt(0.5) * np.exp(-d * d / (2 * 1.5 ** 2) + 1j * ph)
+    return A, T
+
+
+def target(N, seed=9):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return 0.1 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
+
+
+def param_err(got, ref):
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("logn", [13, 16])
+def test_adjoint_matches_oracle(M, prec, logn):
+    N = 1 << logn
+    A0, T = toy_field(N)
+    fib = toy_fiber()
+    out = oracle.mpa(A0, fib, T, 0.0, Z, L, MN, NIT)
+    g_out = 2 * (out - target(N))
+    ref = oracle.mpa_adjoint(A0, g_out, fib, T, 0.0, Z, L, MN, NIT)
+    plan = M.Plan(fib, N, T, L, MN, NIT, precision=prec)
+    gi, gs, gb = plan.adjoint(dev(g_out, prec), 0.0, Z, field_in=dev(A0, prec))
+    assert oracle.rel_l2(host(gi), ref.field) < TOL_FIELD[prec]
+    assert param_err(gs, ref.sigma) < TOL_PARAM[prec]
+    assert param_err(gb, ref.beta2) < TOL_PARAM[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpointed_forward_and_reuse(M, prec):
+    import torch
+    N = 1 << 13
+    A0, T = toy_field(N, seed=4)
+    fib = toy_fiber()
+    plan = M.Plan(fib, N, T, L, MN, NIT, precision=prec)
+    a = dev(A0, prec)
+    b = a.clone()
+    plan.propagate(a, 0.0, Z)
+    ws = plan.propagate_checkpointed(b, 0.0, Z)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)  # same kernels, same order
+    g_out = dev(2 * (host(b) - target(N)), prec)
+    g1, s1, b1 = plan.adjoint(g_out, 0.0, Z, adj_workspace=ws)
+    g2, s2, b2 = plan.adjoint(g_out, 0.0, Z, field_in=dev(A0, prec))
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    assert np.array_equal(s1, s2) and np.array_equal(b1, b2)
+
+
+def test_adjoint_matches_gpu_central_differences_fp64(M):
+    """Directional and per-segment central differences (h = 1e-6 relative) of
+    the GPU's FP64 forward pass, without the oracle."""
+    import torch
+    N = 1 << 13
+    A0, T = toy_field(N, seed=5)
+    tgt = target(N)
+
+    def run(fib, A):
+        plan = M.Plan(fib, N, T, L, MN, NIT, precision="fp64")
+        x = dev(A, "fp64")
+        plan.propagate(x, 0.0, Z)
+        return host(x)
+
+    def loss(out):
+        return float(np.sum(np.abs(out - tgt) ** 2))
+
+    fib = toy_fiber()
+    out = run(fib, A0)
+    plan = M.Plan(fib, N, T, L, MN, NIT, precision="fp64")
+    gi, gs, gb = plan.adjoint(dev(2 * (out - tgt), "fp64"), 0.0, Z, field_in=dev(A0, "fp64"))
+    gi = host(gi)
+    rng = np.random.Generator(np.random.PCG64(17))
+    v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    h = 1e-6 * np.linalg.norm(A0) / np.linalg.norm(v)
+    fd = (loss(run(fib, A0 + h * v)) - loss(run(fib, A0 - h * v))) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gi, v))) <= 1e-6 * abs(fd)
+    floor = 1e-8 * max(1.0, loss(out))
+    for P in (0, 3):
+        for kind, g in (("sigma", gs), ("beta2", gb)):
+            d = {P: 1e-6}
+            m = {P: -1e-6}
+            fp = toy_fiber(True, d_sigma=d) if kind == "sigma" else toy_fiber(True, d_beta2=d)
+            fm = toy_fiber(True, d_sigma=m) if kind == "sigma" else toy_fiber(True, d_beta2=m)
+            fdp = (loss(run(fp, A0)) - loss(run(fm, A0))) / 2e-6
+            assert abs(fdp - g[P]) <= 1e-6 * abs(fdp) + floor, (kind, P, fdp, g[P])
+
+
+def test_autograd_function(M):
+    import torch
+    N = 1 << 13
+    A0, T = toy_field(N, seed=6)
+    fib = toy_fiber()
+    plan = M.Plan(fib, N, T, L, MN, NIT, precision="fp64")
+    field = dev(A0, "fp64").requires_grad_(True)
+    segs = list(fib.segments) * fib.n_periods
+    sigma = torch.tensor([s.sigma_per_W_km for s in segs], dtype=torch.float64, requires_grad=True)
+    beta2 = torch.tensor([s.beta2_ps2_per_km for s in segs], dtype=torch.float64, requires_grad=True)
+    tgt = dev(target(N), "fp64")
+    out = M.MPAFunction.apply(field, sigma, beta2, plan, 0.0, Z)
+    loss = torch.mean(torch.abs(out - tgt) ** 2)
+    loss.backward()
+    g_out = (2.0 / N) * (out.detach() - tgt)
+    gi, gs, gb = plan.adjoint(g_out, 0.0, Z, field_in=dev(A0, "fp64"))
+    torch.cuda.synchronize()
+    assert torch.allclose(field.grad, gi, rtol=0, atol=1e-14 * float(gi.abs().max()))
+    assert np.allclose(sigma.grad.numpy(), gs, rtol=1e-12, atol=0)
+    assert np.allclose(beta2.grad.numpy(), gb, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradient_workload_scaling_identity(M, prec):
+    """The 2^20 16-channel gradient workload over its first span (10
+    intervals of 5 km, M = 142, 3 iterations), loss = mean |A_out - A_in|^2,
+    checked by the scaling identity of the cubic term (exact for the discrete
+    method at any size)."""
+    import torch
+    w = workload("4")
+    fib = dm_map(1)
+    A0 = w.field()
+    plan = M.Plan(fib, w.N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision=prec)
+    a = dev(A0, prec)
+    out = a.clone()
+    ws = plan.propagate_checkpointed(out, 0.0, 50.0)
+    g_out = (2.0 / w.N) * (out - a)
+    gi, gs, gb = plan.adjoint(g_out, 0.0, 50.0, adj_workspace=ws)
+    torch.cuda.synchronize()
+    sig = np.array([s.sigma_per_W_km for s in fib.segments] * fib.n_periods)
+    gi_h, a_h, go_h, out_h = host(gi), host(a), host(g_out), host(out)
+    lhs = float(sig @ gs - 0.5 * np.real(np.vdot(gi_h, a_h)))
+    rhs = float(-0.5 * np.real(np.vdot(go_h, out_h)))
+    scale = float(np.abs(sig * gs).sum() + 0.5 * np.abs(np.vdot(gi_h, a_h)) + abs(rhs))
+    assert abs(lhs - rhs) <= (1e-9 if prec == "fp64" else 1e-4) * scale
+    assert np.all(np.isfinite(gb)) and np.abs(gb).max() > 0
+
+
+def test_adjoint_argument_errors(M):
+    import torch
+    N = 1 << 12
+    A0, T = toy_field(N)
+    plan = M.Plan(toy_fiber(), N, T, L, MN, NIT, precision="fp64")
+    with pytest.raises(M.MPAError, match="unsupported N"):
+        plan.adjoint_workspace_bytes(0.0, Z)
+    plan = M.Plan(toy_fiber(), 1 << 13, 0.05 * (1 << 13), L, MN, NIT, precision="fp64")
+    with pytest.raises(M.MPAError, match="z-grid"):
+        plan.adjoint_workspace_bytes(0.0, 0.75)
+    g = torch.zeros(1 << 13, dtype=torch.complex128, device="cuda")
+    with pytest.raises(M.MPAError, match="workspace"):
+        plan.adjoint(g, 0.0, Z, field_in=g, adj_workspace=torch.empty(256, dtype=torch.uint8, device="cuda"))
