@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpa", choices=["mpa", "reference"])
-    ap.add_argument("--workload", default="1")
+    ap.add_argument("--workload", default="1",
+                    help="1: the 2^20 link (default); 0, 2: the other single links; 3: 256 batched links; "
+                         "4: gradients of the 2^20 16-channel link")
     ap.add_argument("--km", type=float, default=None, help="propagate this many km per step (default: whole link)")
     ap.add_argument("--ss-km", type=float, default=25.0, help="km of split-step timed as the comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -381,11 +383,195 @@ def run_mpa(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------------- batched links (workload 3)
+def run_batch(args, world, rank, local):
+    """256 independent links (N in 2^12..2^18, 1-20 spans, per-link sigma and
+    power) propagated by one batch: the CUDA graph of all groups against a
+    sequential loop of single-link plans over a subset of the links."""
+    import numpy as np
+    import torch
+
+    from paper_1101_0086_gb300 import build as B
+    from paper_1101_0086_gb300 import mpa
+    from paper_1101_0086_gb300.workloads import batch_links
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    mpa.lib()
+    specs = batch_links()
+    L, Mn, nit = 5.0, 142, 3
+    src = [torch.from_numpy(s.field().astype(np.complex64)).cuda() for s in specs]
+    fields = [x.clone() for x in src]
+    batch = mpa.Batch([(s.fiber, s.T_ps, s.length_km, f) for s, f in zip(specs, fields)], L, Mn, nit, "fp32")
+    units = float(sum(s.N * s.length_km for s in specs))
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        for f, x in zip(fields, src):
+            f.copy_(x)
+
+    for _ in range(args.warmup):
+        reset()
+        batch.propagate(True, stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    l0 = mpa.kernel_launches()
+    t = 0.0
+    for _ in range(args.steps):
+        reset()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        batch.propagate(True, stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        t += s.elapsed_time(e) / 1e3
+    launches = mpa.kernel_launches() - l0
+    ck = clocks.stop()
+    value = units * args.steps / t
+    # sequential per-link loop on every 8th link (same plans as a user would make)
+    sub = specs[::8]
+    plans = [mpa.Plan(s.fiber, s.N, s.T_ps, L, Mn, nit, "fp32") for s in sub]
+    xs = [torch.from_numpy(s.field().astype(np.complex64)).cuda() for s in sub]
+    for p, x, sp in zip(plans, xs, sub):
+        p.propagate(x.clone(), 0.0, sp.length_km, stream)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for p, x, sp in zip(plans, xs, sub):
+        p.propagate(x, 0.0, sp.length_km, stream)
+    e.record(stream)
+    torch.cuda.synchronize()
+    ts = s.elapsed_time(e) / 1e3
+    seq = float(sum(sp.N * sp.length_km for sp in sub)) / ts
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch256_n2p12-2p18", "links": len(specs), "mode_km_per_step": units,
+                       "L_km": L, "M": Mn, "n_iter": nit, "method": "MPA FP32, batched links, CUDA graph",
+                       "l2": "inputs reset between steps (working set > L2)"},
+            "sequential_subset": {"value": seq, "unit": UNIT, "links": len(sub)},
+            "batch_over_sequential": value / seq, "clocks": ck, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------ gradients (workload 4)
+def run_grad(args, world, rank, local):
+    """Gradient of l = mean |D^-1 A_out - A_in|^2 (D: the exact linear flow of
+    the link, so D^-1 is ideal dispersion compensation) with respect to the
+    input field and sigma and beta2 of every physical segment, through the
+    MPA (FP32) and split-step (FP32, FP64) reverse modes.  One step = forward
+    with checkpoints, loss, reverse pass."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_1101_0086_gb300 import build as B
+    from paper_1101_0086_gb300 import mpa
+    from paper_1101_0086_gb300.workloads import FiberMap, Segment, workload
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    mpa.lib()
+    w = workload("4")
+    km = w.length_km if args.km is None else float(args.km)
+    n_spans = int(round(km / w.fiber.period_km))
+    fib = dataclasses.replace(w.fiber, n_periods=n_spans)
+    N = w.N
+    A0 = w.field()
+    stream = torch.cuda.current_stream()
+
+    def linear_map(sign):
+        segs = tuple(Segment(s.length_km, sign * s.beta2_ps2_per_km, sign * s.beta3_ps3_per_km, 0.0)
+                     for s in fib.segments)
+        return FiberMap(segs, 0.0, 0.0, n_spans)
+
+    comp, disp = linear_map(-1.0), linear_map(+1.0)  # D^-1 and D^H^-1 = D (the flow is unitary at span ends)
+    lin_ws = {}
+
+    def lin(x, fm):
+        key = x.dtype
+        if key not in lin_ws:
+            lin_ws[key] = torch.empty(mpa.ss_workspace_bytes(N, x.dtype), dtype=torch.uint8, device="cuda")
+        return mpa.ss_propagate(x, fm, w.T_ps, km, 0.0, km, lin_ws[key], stream)  # one exact linear step
+
+    def loss_grad(a, out):
+        r = lin(out.clone(), comp) - a
+        loss = torch.mean(torch.abs(r) ** 2)
+        g_out = lin((2.0 / N) * r, disp)
+        return loss, g_out, (2.0 / N) * r
+
+    res = {}
+    methods = [("mpa", "fp32"), ("ss", "fp32")] + ([("ss", "fp64")] if km <= 100.0 else [])
+    for meth, prec in methods:
+        dt = torch.complex64 if prec == "fp32" else torch.complex128
+        a = torch.from_numpy(A0).to(dt).cuda()
+        if meth == "mpa":
+            plan = mpa.Plan(fib, N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision=prec)
+            ws = torch.empty(plan.adjoint_workspace_bytes(0.0, km), dtype=torch.uint8, device="cuda")
+        else:
+            ssw = torch.empty(mpa.ss_workspace_bytes(N, prec), dtype=torch.uint8, device="cuda")
+
+        def step():
+            out = a.clone()
+            if meth == "mpa":
+                plan.propagate_checkpointed(out, 0.0, km, ws, stream)
+                loss, g_out, direct = loss_grad(a, out)
+                gi, gs, gb = plan.adjoint(g_out, 0.0, km, adj_workspace=ws, stream=stream)
+            else:
+                mpa.ss_propagate(out, fib, w.T_ps, w.ss_dz_km, 0.0, km, ssw, stream)
+                loss, g_out, direct = loss_grad(a, out)
+                gi, gs, gb = mpa.ss_adjoint(a, g_out, fib, w.T_ps, w.ss_dz_km, 0.0, km, stream=stream)
+            return loss, gi - direct, gs, gb, out, g_out
+
+        reps = args.steps if meth == "mpa" else 1
+        for _ in range(1 if meth == "mpa" else 0):
+            step()
+        torch.cuda.synchronize()
+        l0 = mpa.kernel_launches()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            loss, gi, gs, gb, out, g_out = step()
+        e.record(stream)
+        torch.cuda.synchronize()
+        t = s.elapsed_time(e) / 1e3 / reps
+        # scaling identity of the cubic term (exact for both discrete methods):
+        # sum sigma dl/dsigma - Re<g_A, A>/2 = -Re<g_out, out>/2, with the
+        # direct dependence of l on A_in taken out of g_A
+        gi_prop = (gi.to(torch.complex128) + (2.0 / N) * (lin(out.clone(), comp) - a).to(torch.complex128))
+        sig = np.array([sg.sigma_per_W_km for sg in fib.segments] * fib.n_periods)
+        lhs = float(sig @ gs) - 0.5 * float(torch.real(torch.vdot(gi_prop, a.to(torch.complex128))))
+        rhs = -0.5 * float(torch.real(torch.vdot(g_out.to(torch.complex128), out.to(torch.complex128))))
+        res[f"{meth}_{prec}"] = {"value": N * km / t, "unit": UNIT, "s_per_gradient": t, "loss": float(loss),
+                                 "scaling_identity_residual": abs(lhs - rhs) / max(abs(rhs), 1e-300),
+                                 "launches_per_gradient": (mpa.kernel_launches() - l0) / reps,
+                                 "grad_sigma_first": [float(x) for x in gs[:2]],
+                                 "grad_beta2_first": [float(x) for x in gb[:2]]}
+    line = {"metric": "gradient evaluations in mode*km/s (forward with checkpoints + loss + reverse pass)",
+            "value": res["mpa_fp32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "N": N, "km": km, "n_segments": 2 * n_spans,
+                       "loss": "mean |D^-1 A_out - A_in|^2, D = exact linear flow"},
+            "methods": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload == "3":
+        return run_batch(args, world, rank, local)
+    if args.workload == "4":
+        return run_grad(args, world, rank, local)
     return run_mpa(args, world, rank, local)
 
 

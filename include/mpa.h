@@ -219,6 +219,24 @@ MPA_API int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, doubl
                  void* field, double z_from_km, double z_to_km, void* workspace, size_t ws_bytes,
                  mpa_stream stream);
 
+/* Reverse mode of ss_propagate (the split-step of Eq. (4)) for a real loss,
+ * in the conventions of mpa_adjoint: given the input field and grad_out =
+ * dl/dA_out (device, N samples each, the precision's complex type), writes
+ * dl/dA_in to grad_in and, when given, the per-physical-segment dl/dsigma
+ * and dl/dbeta2 to HOST arrays of n_periods x n_segments doubles (the call
+ * then synchronises the stream).  The forward pass is repeated with a
+ * checkpoint every ckpt_steps steps (<= 0: about sqrt of the step count);
+ * each checkpoint segment is recomputed with the field before every
+ * nonlinear step and the spectrum after every linear step kept.  Memory:
+ * (checkpoints + 2 ckpt_steps + 3) N samples.  N >= 2^13.  The paper has
+ * no adjoint; this is the gradient of Eq. (4) as ss_propagate computes it. */
+MPA_API int ss_adjoint_workspace_size(const mpa_fiber_map* map, int64_t N, int32_t precision, double dz_km,
+                                      double z_from_km, double z_to_km, int32_t ckpt_steps, size_t* bytes);
+MPA_API int ss_adjoint(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision,
+                       const void* field_in, const void* grad_out, void* grad_in, double z_from_km, double z_to_km,
+                       int32_t ckpt_steps, void* workspace, size_t ws_bytes, double* grad_sigma, double* grad_beta2,
+                       mpa_stream stream);
+
 /* Discrete Fourier transform of N values in place, in the convention above:
  * sign = +1: F (no scaling), sign = -1: F^-1 (scaled by 1/N).  The MPA uses
  * these transforms in steps 3 and 4.  Workspace: ss_workspace_size bytes. */

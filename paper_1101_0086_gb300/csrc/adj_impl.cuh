@@ -59,6 +59,88 @@ cudaError_t kra_one(const KRAParams<T>& p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename T, int L, int MODE>
+cudaError_t ssc_one(const SSCParams<T>& p, cudaStream_t st) {
+    typedef KCGeom<T, L> Gm;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ssc_kernel<T, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Gm::smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (p.N1 % Gm::G != 0) return cudaErrorInvalidValue;
+    const bool prof = g_prof_on.load(std::memory_order_relaxed);
+    if (prof) prof_begin(st);
+    ssc_kernel<T, L, MODE><<<(unsigned)(p.N1 / Gm::G), Gm::NT, Gm::smem_bytes, st>>>(p);
+    if (prof) prof_end(PK_KC_ADJ, st, 3.0 * (double)p.N * sizeof(cx<T>));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <typename T, int L, int MODE>
+cudaError_t ssr_one(const SSRParams<T>& p, cudaStream_t st) {
+    typedef KRGeom<T, L> Gm;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ssr_kernel<T, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Gm::smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (p.nrows % Gm::G != 0) return cudaErrorInvalidValue;
+    const bool prof = g_prof_on.load(std::memory_order_relaxed);
+    if (prof) prof_begin(st);
+    ssr_kernel<T, L, MODE><<<(unsigned)(p.nrows / Gm::G), Gm::NT, Gm::smem_bytes, st>>>(p);
+    if (prof) prof_end(PK_KR_ADJ, st, 3.0 * (double)p.nrows * L * sizeof(cx<T>));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <typename T, int L>
+cudaError_t ssc_mode(int mode, const SSCParams<T>& p, cudaStream_t st) {
+    return mode == SS_STORE ? ssc_one<T, L, SS_STORE>(p, st) : ssc_one<T, L, SS_REV>(p, st);
+}
+template <typename T, int L>
+cudaError_t ssr_mode(int mode, const SSRParams<T>& p, cudaStream_t st) {
+    return mode == SS_STORE ? ssr_one<T, L, SS_STORE>(p, st) : ssr_one<T, L, SS_REV>(p, st);
+}
+
+template <typename T>
+cudaError_t ssc_any(int mode, int logL, const SSCParams<T>& p, cudaStream_t st) {
+    switch (logL) {
+        case 4: return ssc_mode<T, 16>(mode, p, st);
+        case 5: return ssc_mode<T, 32>(mode, p, st);
+        case 6: return ssc_mode<T, 64>(mode, p, st);
+        case 7: return ssc_mode<T, 128>(mode, p, st);
+        case 8: return ssc_mode<T, 256>(mode, p, st);
+        case 9: return ssc_mode<T, 512>(mode, p, st);
+        case 10: return ssc_mode<T, 1024>(mode, p, st);
+        case 11: return ssc_mode<T, 2048>(mode, p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t ssr_any(int mode, int logL, const SSRParams<T>& p, cudaStream_t st) {
+    switch (logL) {
+        case 4: return ssr_mode<T, 16>(mode, p, st);
+        case 5: return ssr_mode<T, 32>(mode, p, st);
+        case 6: return ssr_mode<T, 64>(mode, p, st);
+        case 7: return ssr_mode<T, 128>(mode, p, st);
+        case 8: return ssr_mode<T, 256>(mode, p, st);
+        case 9: return ssr_mode<T, 512>(mode, p, st);
+        case 10: return ssr_mode<T, 1024>(mode, p, st);
+        case 11: return ssr_mode<T, 2048>(mode, p, st);
+        case 12: return ssr_mode<T, 4096>(mode, p, st);
+        case 13: return ssr_mode<T, 8192>(mode, p, st);
+        case 14:
+            if constexpr (sizeof(T) == 4) return ssr_mode<T, 16384>(mode, p, st);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t kca_any(int mode, int logL, const KCAParams<T>& p, cudaStream_t st) {
     switch (logL) {
@@ -184,6 +266,12 @@ cudaError_t scale_to_state_any(const cx<T>* in, double2* state, double scale, lo
     cudaError_t scale_to_state_launch<T>(const cx<T>* in, double2* state, double scale, long long N,          \
                                          cudaStream_t st) {                                                    \
         return adj::scale_to_state_any<T>(in, state, scale, N, st);                                            \
+    }                                                                                                          \
+    template <> cudaError_t ssc_launch<T>(int mode, int logL, const SSCParams<T>& p, cudaStream_t st) {        \
+        return adj::ssc_any<T>(mode, logL, p, st);                                                             \
+    }                                                                                                          \
+    template <> cudaError_t ssr_launch<T>(int mode, int logL, const SSRParams<T>& p, cudaStream_t st) {        \
+        return adj::ssr_any<T>(mode, logL, p, st);                                                             \
     }                                                                                                          \
     template <> int kca_tile_cols<T>(int logL) { return adj::kca_cols<T>(logL); }                              \
     template <> int kra_tile_rows<T>(int logL) { return adj::kra_rows<T>(logL); }                              \

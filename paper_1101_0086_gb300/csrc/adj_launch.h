@@ -15,6 +15,9 @@ template <typename T>
 cudaError_t scale_to_state_launch(const cx<T>* in, double2* state, double scale, long long N, cudaStream_t st);
 cudaError_t reduce_parts_launch(const double* part, int per, int n, double* acc, cudaStream_t st);
 
+template <typename T> cudaError_t ssc_launch(int mode, int logL, const SSCParams<T>& p, cudaStream_t st);
+template <typename T> cudaError_t ssr_launch(int mode, int logL, const SSRParams<T>& p, cudaStream_t st);
+
 // Tile widths of the reverse passes (columns per column tile, rows per row tile).
 template <typename T> int kca_tile_cols(int logL);
 template <typename T> int kra_tile_rows(int logL);

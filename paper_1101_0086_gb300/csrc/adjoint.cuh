@@ -372,6 +372,223 @@ __global__ void __launch_bounds__(256) scan_store_kernel(const cx<T>* __restrict
     }
 }
 
+// ---------------------------------------------------------------- split-step
+// Reverse mode of the split-step of Eq. (4) on the same four-step layout as
+// its forward kernels (kc_kernel KC_SS_STEP, kr_kernel KR_SS).
+//   SSC (column pass)  STORE: forward column DFT -> X' = X exp(i beta) pre (kept, natural
+//                      order) -> inverse column DFT, exactly as KC_SS_STEP.
+//                      REV: forward column DFT -> g; the beta2 term -sum_k (w_k^2/2) Im(conj(g) X')
+//                      -> g conj(exp(i beta)) pre -> inverse column DFT.
+//   SSR (row pass)     STORE: inverse row DFT -> t = (.)/N (kept) -> t exp(i s |t|^2) -> forward,
+//                      exactly as KR_SS.
+//                      REV: inverse row DFT -> g~ = (.)/N (the gradient of y over N);
+//                      y = t e^{i s |t|^2}, c = -Im(conj(g~) y):
+//                      g~_t = e^{-i s |t|^2} g~ + 2 c s t, the sigma term N sum c |t|^2 -> forward.
+enum { SS_STORE = 0, SS_REV = 1 };
+
+template <typename T> struct SSCParams {
+    cx<T>* data;     // N samples, work layout, in/out
+    cx<T>* xs;       // X' of this linear step (natural order): written by STORE, read by REV
+    long long N;
+    int logN;
+    int N1, logN1;
+    NodeC flow;      // STORE: exp(i beta) and pre of the step; REV: the negated phase
+    double pre;      // the real factor applied (STORE: flow.pre; REV: flow.pre, / N on the output side)
+    double wscale;   // (2 pi / T)^2 / 2, times the factor the incoming gradient still lacks (1/N on the output side)
+    double* part;
+};
+
+template <typename T> struct SSRParams {
+    cx<T>* data;  // N1-sample rows, in/out
+    cx<T>* ts;    // t of this nonlinear step (work layout): written by STORE, read by REV
+    long long nrows;
+    long long N;
+    int logN;
+    int N2;
+    T inv_n;
+    T rot;        // int sigma over the step
+    double scale; // REV: factor of the sigma partial sums (N)
+    double* part;
+};
+
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) ssc_kernel(const SSCParams<T> p) {
+    typedef cx<T> C;
+    typedef KCGeom<T, L> Gm;
+    typedef Tiling<T> P;
+    constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
+    typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_COL, P::PSH, true> XF;
+    typedef Xform<T, L, G, NT, P::RMAX, -1, LAYOUT_COL, P::PSH, false> XI;
+    static_assert(XF::RL == XI::R0, "forward/inverse junction radix");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[NT / 32];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    C* olo = tlo + TwDims<L>::NLO;
+    C* ohi = olo + G * Gm::OLO;
+    const int tid = threadIdx.x;
+    const long long col0 = (long long)blockIdx.x * G;
+    const int N1m = p.N1 - 1;
+    constexpr bool FAST = sizeof(T) == 4;
+
+    tw_init<T, L>(thi, tlo, tid, NT);
+    for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
+        const int g = i % G, m = i / G;
+        const long long k1 = (col0 + g) & N1m;
+        if (m < Gm::OLO) olo[m * G + g] = expi_ratio<T>(-k1 * m, p.logN);
+        else ohi[(m - Gm::OLO) * G + g] = expi_ratio<T>(-k1 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+    }
+    __syncthreads();
+
+    C vin[XF::Q0][XF::R0];
+#pragma unroll
+    for (int q = 0; q < XF::Q0; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, XF::R0>(tid + q * NT, j, g);
+        const long long c = (col0 + g) & N1m;
+#pragma unroll
+        for (int r = 0; r < XF::R0; ++r) vin[q][r] = p.data[c + (long long)(j + r * (L / XF::R0)) * p.N1];
+    }
+    C vm[XF::QL][XF::RL];
+    XF::run(vin, vm, s, thi, tlo);
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < XF::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, XF::RL>(tid + q * NT, j, g);
+        const long long c = (col0 + g) & N1m;
+        unsigned long long th[XF::RL];
+        if constexpr (FAST) phase_run<XF::RL>(c + (long long)j * p.N1, (long long)p.N1 * (L / XF::RL), p.flow, th);
+#pragma unroll
+        for (int r = 0; r < XF::RL; ++r) {
+            const long long idx = c + (long long)(j + r * (L / XF::RL)) * p.N1;
+            C ph;
+            if constexpr (FAST) ph = expi_turns_poly(th[r]);
+            else ph = expi_turns<T>(phase_q64(signed_k(idx, p.N), p.flow));
+            if constexpr (MODE == SS_REV) {
+                const long long kk = signed_k(idx, p.N);
+                acc -= (double)(kk * kk) * (double)im_conj_mul(vm[q][r], p.xs[idx]);
+            }
+            vm[q][r] = cscale(cmul(vm[q][r], ph), (T)p.pre);
+            if constexpr (MODE == SS_STORE) p.xs[idx] = vm[q][r];
+        }
+    }
+    C vout[XI::QL][XI::RL];
+    XI::run(vm, vout, s, thi, tlo);
+#pragma unroll
+    for (int q = 0; q < XI::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_COL, L, G, XI::RL>(tid + q * NT, j, g);
+        const long long c = (col0 + g) & N1m;
+#pragma unroll
+        for (int r = 0; r < XI::RL; ++r) {
+            const int row = j + r * (L / XI::RL);
+            C w = olo[(row & (Gm::OLO - 1)) * G + g];
+            if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
+            p.data[c + (long long)row * p.N1] = cmul(vout[q][r], w);
+        }
+    }
+    if constexpr (MODE == SS_REV) {
+        const double tot = block_sum<NT>(acc, red);
+        if (tid == 0) p.part[blockIdx.x] = tot * p.wscale;
+    }
+}
+
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) ssr_kernel(const SSRParams<T> p) {
+    typedef cx<T> C;
+    typedef KRGeom<T, L> Gm;
+    typedef Tiling<T, 1> P;
+    constexpr int G = Gm::G, TE = Gm::TE, NT = Gm::NT;
+    typedef Xform<T, L, G, NT, P::RMAX, -1, LAYOUT_ROW, P::PSH, false> XI;
+    typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_ROW, P::PSH, true> XF;
+    static_assert(XI::RL == XF::R0, "inverse/forward junction radix");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[NT / 32];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    C* olo = tlo + TwDims<L>::NLO;
+    C* ohi = olo + G * Gm::OLO;
+    const int tid = threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * G;
+
+    tw_init<T, L>(thi, tlo, tid, NT);
+    for (int i = tid; i < G * (Gm::OLO + Gm::OHI); i += NT) {
+        const int g = i / (Gm::OLO + Gm::OHI), m = i % (Gm::OLO + Gm::OHI);
+        const long long n2 = (row0 + g) & (p.N2 - 1);
+        if (m < Gm::OLO) olo[g * Gm::OLO + m] = expi_ratio<T>(n2 * m, p.logN);
+        else ohi[g * Gm::OHI + (m - Gm::OLO)] = expi_ratio<T>(n2 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+    }
+    __syncthreads();
+
+    C vin[XI::Q0][XI::R0];
+#pragma unroll
+    for (int q = 0; q < XI::Q0; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XI::R0>(tid + q * NT, j, g);
+        const C* src = p.data + (row0 + g) * L;
+#pragma unroll
+        for (int r = 0; r < XI::R0; ++r) vin[q][r] = src[j + r * (L / XI::R0)];
+    }
+    C vm[XI::QL][XI::RL];
+    XI::run(vin, vm, s, thi, tlo);
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < XI::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XI::RL>(tid + q * NT, j, g);
+        C* tr = p.ts + (row0 + g) * L;
+#pragma unroll
+        for (int r = 0; r < XI::RL; ++r) {
+            const int l = j + r * (L / XI::RL);
+            if constexpr (MODE == SS_STORE) {
+                C a = cscale(vm[q][r], p.inv_n);
+                tr[l] = a;
+                const T pw = a.x * a.x + a.y * a.y;
+                T sn, cs;
+                if constexpr (sizeof(T) == 4) sincosf(p.rot * pw, &sn, &cs);
+                else sincos(p.rot * pw, &sn, &cs);
+                vm[q][r] = cmul(a, mkc(cs, sn));
+            } else {
+                const C gy = cscale(vm[q][r], p.inv_n);
+                const C t = tr[l];
+                const T pw = t.x * t.x + t.y * t.y;
+                T sn, cs;
+                if constexpr (sizeof(T) == 4) sincosf(p.rot * pw, &sn, &cs);
+                else sincos(p.rot * pw, &sn, &cs);
+                const C e = mkc(cs, sn);
+                const C y = cmul(t, e);
+                const T c = -im_conj_mul(gy, y);
+                acc += (double)(c * pw);
+                const C a = cmul(gy, cconj(e));
+                const T f = T(2) * c * p.rot;
+                vm[q][r] = mkc(a.x + f * t.x, a.y + f * t.y);
+            }
+        }
+    }
+    C vout[XF::QL][XF::RL];
+    XF::run(vm, vout, s, thi, tlo);
+#pragma unroll
+    for (int q = 0; q < XF::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XF::RL>(tid + q * NT, j, g);
+        C* dst = p.data + (row0 + g) * L;
+#pragma unroll
+        for (int r = 0; r < XF::RL; ++r) {
+            const int l = j + r * (L / XF::RL);
+            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+            if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
+            dst[l] = cmul(vout[q][r], w);
+        }
+    }
+    if constexpr (MODE == SS_REV) {
+        const double tot = block_sum<NT>(acc, red);
+        if (tid == 0) p.part[blockIdx.x] = tot * p.scale;
+    }
+}
+
 // state = scale * in (FP64).
 template <typename T>
 __global__ void __launch_bounds__(256) scale_to_state_kernel(const cx<T>* in, double2* state, double scale,

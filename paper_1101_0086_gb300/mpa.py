@@ -52,7 +52,8 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "mpa_fft", "mpa_status_string", "mpa_last_cuda_error", "mpa_kernel_launches", "mpa_profile",
            "mpa_profile_read", "mpa_profile_kind_name", "mpa_fft_noalloc", "mpa_batch_create",
            "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate", "mpa_batch_destroy",
-           "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint")
+           "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
+           "ss_adjoint_workspace_size", "ss_adjoint")
 
 
 def library_path() -> str:
@@ -103,10 +104,14 @@ def lib() -> ctypes.CDLL:
         L.mpa_propagate_checkpointed.argtypes = [vp, vp, dbl, dbl, vp, ctypes.c_size_t, vp]
         dptr = ctypes.POINTER(ctypes.c_double)
         L.mpa_adjoint.argtypes = [vp, vp, vp, vp, dbl, dbl, vp, ctypes.c_size_t, dptr, dptr, vp]
+        L.ss_adjoint_workspace_size.argtypes = [ctypes.POINTER(_FiberMap), i64, i32, dbl, dbl, dbl, i32, szp]
+        L.ss_adjoint.argtypes = [ctypes.POINTER(_FiberMap), i64, dbl, dbl, i32, vp, vp, vp, dbl, dbl, i32, vp,
+                                 ctypes.c_size_t, dptr, dptr, vp]
         L.mpa_profile_kind_name.restype = ctypes.c_char_p
         for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
                   "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft",
-                  "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint"):
+                  "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
+           "ss_adjoint_workspace_size", "ss_adjoint"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -361,6 +366,37 @@ def ss_propagate(field: torch.Tensor, fiber, T_ps: float, dz_km: float, z_from_k
                               float(z_to_km), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                               _stream(stream)), "ss_propagate")
     return field
+
+
+def ss_adjoint(field_in: torch.Tensor, grad_out: torch.Tensor, fiber, T_ps: float, dz_km: float, z_from_km: float,
+               z_to_km: float, ckpt_steps: int = 0, workspace: Optional[torch.Tensor] = None, params: bool = True,
+               stream=None):
+    """Reverse mode of :func:`ss_propagate` (``ss_adjoint``): returns
+    (dl/dA_in, dl/dsigma, dl/dbeta2), the last two float64 numpy arrays per
+    physical segment (None unless ``params``)."""
+    import numpy as np
+    L = lib()
+    prec = _prec(field_in.dtype)
+    N = field_in.numel()
+    fm, segs = _fiber_struct(fiber)
+    if workspace is None:
+        n = ctypes.c_size_t()
+        _check(L.ss_adjoint_workspace_size(ctypes.byref(fm), N, prec, float(dz_km), float(z_from_km), float(z_to_km),
+                                           int(ckpt_steps), ctypes.byref(n)), "ss_adjoint_workspace_size")
+        workspace = torch.empty(int(n.value), dtype=torch.uint8, device=field_in.device)
+    fi = _field_ptr(field_in, _cdtype(prec), N, "ss_adjoint field_in")
+    go = _field_ptr(grad_out, _cdtype(prec), N, "ss_adjoint grad_out")
+    gi = torch.empty_like(grad_out)
+    gs = gb = ps = pb = None
+    if params:
+        n_phys = len(fiber.segments) * fiber.n_periods
+        gs, gb = np.zeros(n_phys), np.zeros(n_phys)
+        ps = gs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        pb = gb.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(L.ss_adjoint(ctypes.byref(fm), N, float(T_ps), float(dz_km), prec, fi, go, ctypes.c_void_p(gi.data_ptr()),
+                        float(z_from_km), float(z_to_km), int(ckpt_steps), ctypes.c_void_p(workspace.data_ptr()),
+                        workspace.numel(), ps, pb, _stream(stream)), "ss_adjoint")
+    return gi, gs, gb
 
 
 def fft(data: torch.Tensor, sign: int, workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
