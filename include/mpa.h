@@ -67,15 +67,20 @@ enum { MPA_SCHEDULE_AUTO = 0, MPA_SCHEDULE_LEVEL = 1, MPA_SCHEDULE_WAVEFRONT = 2
 
 typedef void* mpa_stream; /* cudaStream_t */
 
-/* One piece of the dispersion-management period with constant coefficients. */
+/* One piece of the dispersion-management period with constant coefficients.
+ * gain_per_km is a distributed amplitude gain g of the piece (e.g. a
+ * Raman-pumped span; the paper notes that distributed amplification can be
+ * included in G): between lumped amplifiers G(z) = g(z) - gamma. */
 typedef struct {
     double length_km;
     double beta2_ps2_per_km;
     double beta3_ps3_per_km;
     double sigma_per_W_km;
+    double gain_per_km;
 } mpa_segment;
 
-/* Periodic fiber map (Eq. (1): beta2, beta3 periodic in z; sigma per segment).
+/* Periodic fiber map (Eq. (1): beta2, beta3 periodic in z; sigma and the
+ * distributed gain per segment).
  * segments[0..n_segments) form one period, repeated n_periods times.
  * Lumped amplifiers at z_k = k z_a_km, k >= 1, multiply the field by
  * exp(z_a gamma) when the propagation crosses z_k (z_k in (z_from, z_to]).

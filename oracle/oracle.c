@@ -4,7 +4,8 @@
  * path links or calls this file.
  *
  * Paper passages followed:
- *   Eq. (1)            the NLSE, G(z) = -gamma + (e^{z_a gamma}-1) sum delta(z - z_k)
+ *   Eq. (1)            the NLSE, G(z) = -gamma + g(z) + (e^{z_a gamma}-1) sum delta(z - z_k),
+ *                      g(z) a distributed gain that is constant on each segment
  *   text after Eq. (1) Fourier transform with exp(+i omega t); interaction
  *                      picture A_hat = psi_hat exp(i beta + int G); beta(omega, z)
  *   Eq. (2)            integral equation for psi_hat
@@ -79,8 +80,11 @@ int oracle_fft(double* x, long N, int sign) { return fft_c((cplx*)x, N, sign); }
 
 /* ------------------------------------------------------------ fiber map */
 
+/* columns of a segment row: length, beta2, beta3, sigma, distributed gain */
+#define NCOL 5
+
 typedef struct {
-    const double* rows; /* n_seg x {length, beta2, beta3, sigma} */
+    const double* rows; /* n_seg x {length, beta2, beta3, sigma, gain} */
     int n_seg;
     double gamma, z_a;
     int n_periods;
@@ -89,11 +93,12 @@ typedef struct {
 
 static fmap make_map(const double* rows, int n_seg, double gamma, double z_a, int n_periods) {
     fmap m = {rows, n_seg, gamma, z_a, n_periods, 0.0};
-    for (int s = 0; s < n_seg; s++) m.period += rows[4 * s];
+    for (int s = 0; s < n_seg; s++) m.period += rows[NCOL * s];
     return m;
 }
 
-/* int_za^zb of coefficient column col (1 = beta2, 2 = beta3, 3 = sigma):
+/* int_za^zb of coefficient column col (1 = beta2, 2 = beta3, 3 = sigma,
+ * 4 = distributed gain):
  * sum over every segment copy of coefficient x overlap length. */
 static double integrate(const fmap* m, double za, double zb, int col) {
     if (zb <= za) return 0.0;
@@ -102,10 +107,10 @@ static double integrate(const fmap* m, double za, double zb, int col) {
     for (long p = p0; p <= p1; p++) {
         double off = (double)p * m->period;
         for (int s = 0; s < m->n_seg; s++) {
-            double a = off, b = off + m->rows[4 * s];
+            double a = off, b = off + m->rows[NCOL * s];
             off = b;
             double lo = a > za ? a : za, hi = b < zb ? b : zb;
-            if (hi > lo) acc += m->rows[4 * s + col] * (hi - lo);
+            if (hi > lo) acc += m->rows[NCOL * s + col] * (hi - lo);
         }
     }
     return acc;
@@ -118,11 +123,11 @@ static double coef_side(const fmap* m, double z, int col, int side) {
     double u = zz - floor(zz / m->period) * m->period;
     double off = 0.0;
     for (int s = 0; s < m->n_seg; s++) {
-        double b = off + m->rows[4 * s];
-        if (u < b || s == m->n_seg - 1) return m->rows[4 * s + col];
+        double b = off + m->rows[NCOL * s];
+        if (u < b || s == m->n_seg - 1) return m->rows[NCOL * s + col];
         off = b;
     }
-    return m->rows[4 * (m->n_seg - 1) + col];
+    return m->rows[NCOL * (m->n_seg - 1) + col];
 }
 
 /* Number of amplifiers z_k = k z_a (k >= 1) with za < z_k <= zb. */
@@ -132,6 +137,12 @@ static long n_amps(const fmap* m, double za, double zb) {
     long ka = (long)floor((za + tol) / m->z_a), kb = (long)floor((zb + tol) / m->z_a);
     if (ka < 0) ka = 0;
     return kb > ka ? kb - ka : 0;
+}
+
+/* int_za^zb G without the lumped amplifiers: -gamma (zb - za) plus the
+ * distributed gain of the segments (G of Eq. (1) between the z_k). */
+static double int_G(const fmap* m, double za, double zb) {
+    return -m->gamma * (zb - za) + integrate(m, za, zb, 4);
 }
 
 static double omega_of(long k, long N, double T) {
@@ -146,7 +157,7 @@ static double beta_of(double w, double I2, double I3) { return 0.5 * w * w * I2 
  * Eq. (2), continued across amplifiers). */
 static void linear_flow(const fmap* m, cplx* X, long N, double T, double za, double zb) {
     double I2 = integrate(m, za, zb, 1), I3 = integrate(m, za, zb, 2);
-    double g = exp(-m->gamma * (zb - za) + (double)n_amps(m, za, zb) * m->z_a * m->gamma);
+    double g = exp(int_G(m, za, zb) + (double)n_amps(m, za, zb) * m->z_a * m->gamma);
     for (long k = 0; k < N; k++) {
         double b = beta_of(omega_of(k, N, T), I2, I3);
         X[k] *= g * (cos(b) + I * sin(b));
@@ -178,14 +189,14 @@ static int mpa_interval(const fmap* m, long N, double T, double z0, double L, in
         return 3;
     }
     /* per-node quantities: z_j = z0 + j dz, beta relative to z0, the loss
-     * factor exp(int_{z0}^{z_j} G) = exp(-gamma (z_j - z0)) and sigma(z_j)
+     * factor exp(int_{z0}^{z_j} G) (loss and distributed gain) and sigma(z_j)
      * (average of the one-sided values where a segment boundary falls on an
      * interior node, the inner one-sided value at the interval ends). */
     for (int j = 0; j <= M; j++) {
         double zj = z0 + dz * (double)j;
         I2[j] = integrate(m, z0, zj, 1);
         I3[j] = integrate(m, z0, zj, 2);
-        loss[j] = exp(-m->gamma * (zj - z0));
+        loss[j] = exp(int_G(m, z0, zj));
         if (j == 0) sig[j] = coef_side(m, zj, 3, +1);
         else if (j == M) sig[j] = coef_side(m, zj, 3, -1);
         else sig[j] = 0.5 * (coef_side(m, zj, 3, -1) + coef_side(m, zj, 3, +1));
@@ -276,7 +287,7 @@ int oracle_mpa(const double* seg_rows, int n_seg, double gamma, double z_a, int 
         /* step 7: A_hat(z0 + L) = psi_M exp(i beta(omega, z0 + L) + int G),
          * then the lumped gain when z0 + L is an amplifier location */
         double I2 = integrate(&m, z0, z0 + L, 1), I3 = integrate(&m, z0, z0 + L, 2);
-        double g = exp(-m.gamma * L + (double)n_amps(&m, z0, z0 + L) * m.z_a * m.gamma);
+        double g = exp(int_G(&m, z0, z0 + L) + (double)n_amps(&m, z0, z0 + L) * m.z_a * m.gamma);
         for (long k = 0; k < N; k++) {
             double b = beta_of(omega_of(k, N, T), I2, I3);
             X[k] = psiM[k] * (cos(b) + I * sin(b)) * g;
@@ -344,7 +355,7 @@ static void add_overlaps(const fmap* m, double za, double zb, double w, double* 
     for (int p = 0; p < m->n_periods; p++) {
         double off = (double)p * m->period;
         for (int s = 0; s < m->n_seg; s++) {
-            double a = off, b = off + m->rows[4 * s];
+            double a = off, b = off + m->rows[NCOL * s];
             off = b;
             double lo = a > za ? a : za, hi = b < zb ? b : zb;
             if (hi > lo) g[p * m->n_seg + s] += w * (hi - lo);
@@ -360,7 +371,7 @@ static int seg_at(const fmap* m, double z, int side) {
     double u = zz - (double)p * m->period, off = 0.0;
     int s = m->n_seg - 1;
     for (int i = 0; i < m->n_seg; i++) {
-        off += m->rows[4 * i];
+        off += m->rows[NCOL * i];
         if (u < off) { s = i; break; }
     }
     if (p < 0 || p >= m->n_periods) return -1;
@@ -396,7 +407,7 @@ static int mpa_interval_adjoint(const fmap* m, long N, double T, double z0, doub
             double zj = z0 + dz * (double)j;
             I2[j] = integrate(m, z0, zj, 1);
             I3[j] = integrate(m, z0, zj, 2);
-            loss[j] = exp(-m->gamma * (zj - z0));
+            loss[j] = exp(int_G(m, z0, zj));
             if (j == 0) sig[j] = coef_side(m, zj, 3, +1);
             else if (j == M) sig[j] = coef_side(m, zj, 3, -1);
             else sig[j] = 0.5 * (coef_side(m, zj, 3, -1) + coef_side(m, zj, 3, +1));
@@ -446,7 +457,7 @@ static int mpa_interval_adjoint(const fmap* m, long N, double T, double z0, doub
         /* output of the interval: step 7 on psi^{(n_tot)}_M, then the gain */
         const cplx* Vl = V + nn * (size_t)(n_tot - 1);
         double I2L = integrate(m, z0, z0 + L, 1), I3L = integrate(m, z0, z0 + L, 2);
-        double g = exp(-m->gamma * L + (double)n_amps(m, z0, z0 + L) * m->z_a * m->gamma);
+        double g = exp(int_G(m, z0, z0 + L) + (double)n_amps(m, z0, z0 + L) * m->z_a * m->gamma);
         double srec = 0.0;
         memset(gp, 0, sizeof(cplx) * nn);
         for (long k = 0; k < N; k++) {
@@ -579,7 +590,7 @@ int oracle_mpa_adjoint(const double* seg_rows, int n_seg, double gamma, double z
         err = mpa_interval(&m, N, T, z0, L, M, n_tot, X, Y, n_threads);
         if (err) break;
         double I2 = integrate(&m, z0, z0 + L, 1), I3 = integrate(&m, z0, z0 + L, 2);
-        double gg = exp(-m.gamma * L + (double)n_amps(&m, z0, z0 + L) * m.z_a * m.gamma);
+        double gg = exp(int_G(&m, z0, z0 + L) + (double)n_amps(&m, z0, z0 + L) * m.z_a * m.gamma);
         for (long k = 0; k < N; k++) {
             double b = beta_of(omega_of(k, N, T), I2, I3);
             Y[k] *= (cos(b) + I * sin(b)) * gg;
@@ -664,7 +675,7 @@ int oracle_ss_adjoint(const double* seg_rows, int n_seg, double gamma, double z_
         /* linear step over [ls[2k], ls[2k+1]]: y = H x */
         double a = ls[2 * k], b = ls[2 * k + 1];
         double I2 = integrate(&m, a, b, 1), I3 = integrate(&m, a, b, 2);
-        double gg = exp(-m.gamma * (b - a) + (double)n_amps(&m, a, b) * m.z_a * m.gamma);
+        double gg = exp(int_G(&m, a, b) + (double)n_amps(&m, a, b) * m.z_a * m.gamma);
         /* y = H x with x the spectrum before the step: recompute it */
         cplx* x = (cplx*)malloc(sizeof(cplx) * (size_t)N);
         if (!x) { free(traj); free(X); free(ls); free(sk); return 3; }

@@ -14,12 +14,14 @@
  *   inverse  F^-1[X]_n  = (1/N) sum_k X_k exp(-2 pi i k n / N)
  *   omega_k  = 2 pi k' / T, k' = k for k < N/2, k - N otherwise
  *   beta(omega, za, zb) = omega^2/2 int_za^zb beta2 + omega^3/6 int_za^zb beta3
- *   G = -gamma between amplifiers; amplifier k (z_k = k z_a, k >= 1) multiplies
+ *   G = -gamma + g between amplifiers (g: the distributed gain of the
+ *   segment); amplifier k (z_k = k z_a, k >= 1) multiplies
  *   the field by exp(z_a gamma) when the propagation crosses z_k, i.e. for
  *   z_k in (z_from, z_to].
  *
  * Fields are interleaved complex128 (re, im) arrays of length 2N.
- * Segment rows are n_seg x 4 doubles: length_km, beta2, beta3, sigma.
+ * Segment rows are n_seg x 5 doubles: length_km, beta2, beta3, sigma,
+ * gain (distributed amplitude gain, 1/km).
  *
  * Return codes: 0 ok; 1 N not a power of two >= 2; 2 z-grid inconsistent
  * (interval count not whole, amplifier strictly inside an MPA interval, or

@@ -246,7 +246,7 @@ cudaError_t scale_to_state_any(const cx<T>* in, double2* state, double scale, lo
 }  // namespace adj
 }  // namespace mpa
 
-#define MPA_ADJ_INSTANTIATE(T)                                                                                 \
+#define MPA_ADJ_INSTANTIATE_MPA(T)                                                                             \
     namespace mpa {                                                                                            \
     template <> cudaError_t kca_launch<T>(int mode, int logL, const KCAParams<T>& p, cudaStream_t st) {        \
         return adj::kca_any<T>(mode, logL, p, st);                                                             \
@@ -267,12 +267,16 @@ cudaError_t scale_to_state_any(const cx<T>* in, double2* state, double scale, lo
                                          cudaStream_t st) {                                                    \
         return adj::scale_to_state_any<T>(in, state, scale, N, st);                                            \
     }                                                                                                          \
+    template <> int kca_tile_cols<T>(int logL) { return adj::kca_cols<T>(logL); }                              \
+    template <> int kra_tile_rows<T>(int logL) { return adj::kra_rows<T>(logL); }                              \
+    }
+
+#define MPA_ADJ_INSTANTIATE_SS(T)                                                                              \
+    namespace mpa {                                                                                            \
     template <> cudaError_t ssc_launch<T>(int mode, int logL, const SSCParams<T>& p, cudaStream_t st) {        \
         return adj::ssc_any<T>(mode, logL, p, st);                                                             \
     }                                                                                                          \
     template <> cudaError_t ssr_launch<T>(int mode, int logL, const SSRParams<T>& p, cudaStream_t st) {        \
         return adj::ssr_any<T>(mode, logL, p, st);                                                             \
     }                                                                                                          \
-    template <> int kca_tile_cols<T>(int logL) { return adj::kca_cols<T>(logL); }                              \
-    template <> int kra_tile_rows<T>(int logL) { return adj::kra_rows<T>(logL); }                              \
     }

@@ -132,7 +132,7 @@ std::vector<AdjC> adj_table(const mpa_plan* p) {
             else if (j == M) sig = p->map.side(u0 + zr, 3, -1);
             else sig = 0.5 * (p->map.side(u0 + zr, 3, -1) + p->map.side(u0 + zr, 3, +1));
             AdjC& c = v[(size_t)t * (M + 1) + j];
-            c.dzp = dz / std::exp(-p->map.gamma * zr);
+            c.dzp = dz / std::exp(p->map.G(u0, u0 + zr));
             c.sig = sig;
         }
     }

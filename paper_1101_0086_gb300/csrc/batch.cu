@@ -215,7 +215,7 @@ int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_
                     const double zr = (j == M) ? L_km : dz * j;
                     NodeC c{};
                     phase_consts(k.map.integ(u0, u0 + zr, 1), k.map.integ(u0, u0 + zr, 2), k.T, &c);
-                    c.pre = std::exp(-k.map.gamma * zr);
+                    c.pre = std::exp(k.map.G(u0, u0 + zr));
                     double sig;
                     if (j == 0) sig = k.map.side(u0, 3, +1);
                     else if (j == M) sig = k.map.side(u0 + zr, 3, -1);

@@ -40,7 +40,7 @@ struct HostMap {
         seg.assign(m->segments, m->segments + m->n_segments);
         for (const auto& s : seg) {
             if (!(s.length_km > 0.0) || !std::isfinite(s.beta2_ps2_per_km) || !std::isfinite(s.beta3_ps3_per_km) ||
-                !std::isfinite(s.sigma_per_W_km))
+                !std::isfinite(s.sigma_per_W_km) || !std::isfinite(s.gain_per_km))
                 return MPA_ERR_INVALID_ARG;
             period += s.length_km;
         }
@@ -49,8 +49,10 @@ struct HostMap {
         length = period * m->n_periods;
         return MPA_OK;
     }
+    // col 1: beta2, 2: beta3, 3: sigma, 4: distributed gain
     static double coef(const mpa_segment& s, int col) {
-        return col == 1 ? s.beta2_ps2_per_km : col == 2 ? s.beta3_ps3_per_km : s.sigma_per_W_km;
+        return col == 1 ? s.beta2_ps2_per_km : col == 2 ? s.beta3_ps3_per_km : col == 3 ? s.sigma_per_W_km
+                                                                                       : s.gain_per_km;
     }
     // int_za^zb of a coefficient: shift za into the first period, then sum
     // coefficient x overlap over the segment copies that [za, zb] covers.
@@ -81,6 +83,8 @@ struct HostMap {
         }
         return coef(seg.back(), col);
     }
+    // int_za^zb G without the lumped amplifiers: the distributed gain minus gamma
+    double G(double za, double zb) const { return integ(za, zb, 4) - gamma * (zb - za); }
     // amplifiers k z_a (k >= 1) in (za, zb]
     long amps(double za, double zb) const {
         if (!(z_a > 0.0)) return 0;

@@ -281,7 +281,7 @@ int ss_t(const HostMap& m, const Split& s, double T_ps, double dz, void* field, 
     auto flow = [&](double za, double zb) {
         NodeC c{};
         phase_consts(m.integ(za, zb, 1), m.integ(za, zb, 2), T_ps, &c);
-        c.pre = std::exp(-m.gamma * (zb - za) + (double)m.amps(za, zb) * m.z_a * m.gamma);
+        c.pre = std::exp(m.G(za, zb) + (double)m.amps(za, zb) * m.z_a * m.gamma);
         c.post = 1.0;
         return c;
     };
@@ -357,7 +357,7 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
             const double zr = (j == M) ? p->L : dz * j;
             NodeC& c = p->nodes[(size_t)t * (M + 1) + j];
             phase_consts(p->map.integ(u0, u0 + zr, 1), p->map.integ(u0, u0 + zr, 2), p->T, &c);
-            c.pre = std::exp(-p->map.gamma * zr);
+            c.pre = std::exp(p->map.G(u0, u0 + zr));
             double sig;
             if (j == 0) sig = p->map.side(u0, 3, +1);
             else if (j == M) sig = p->map.side(u0 + zr, 3, -1);

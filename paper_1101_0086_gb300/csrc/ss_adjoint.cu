@@ -110,7 +110,7 @@ int ss_adjoint_t(const HostMap& m, const Split& s, double T_ps, double dz, const
         NodeC c{};
         const double I2 = m.integ(za, zb, 1), I3 = m.integ(za, zb, 2);
         phase_consts(conj ? -I2 : I2, conj ? -I3 : I3, T_ps, &c);
-        c.pre = std::exp(-m.gamma * (zb - za) + (double)m.amps(za, zb) * m.z_a * m.gamma);
+        c.pre = std::exp(m.G(za, zb) + (double)m.amps(za, zb) * m.z_a * m.gamma);
         c.post = 1.0;
         return c;
     };

@@ -28,7 +28,8 @@ class MPAError(RuntimeError):
 
 class _Segment(ctypes.Structure):
     _fields_ = [("length_km", ctypes.c_double), ("beta2_ps2_per_km", ctypes.c_double),
-                ("beta3_ps3_per_km", ctypes.c_double), ("sigma_per_W_km", ctypes.c_double)]
+                ("beta3_ps3_per_km", ctypes.c_double), ("sigma_per_W_km", ctypes.c_double),
+                ("gain_per_km", ctypes.c_double)]
 
 
 class _FiberMap(ctypes.Structure):

@@ -45,6 +45,7 @@ class Segment:
     beta2_ps2_per_km: float
     beta3_ps3_per_km: float
     sigma_per_W_km: float
+    gain_per_km: float = 0.0  # distributed amplitude gain g: G = g - gamma between amplifiers
 
 
 @dataclasses.dataclass(frozen=True)
@@ -69,9 +70,10 @@ class FiberMap:
         return self.period_km * self.n_periods
 
     def as_rows(self) -> np.ndarray:
-        """Segments as an (n, 4) float64 array: length, beta2, beta3, sigma."""
+        """Segments as an (n, 5) float64 array: length, beta2, beta3, sigma, gain."""
         return np.array(
-            [[s.length_km, s.beta2_ps2_per_km, s.beta3_ps3_per_km, s.sigma_per_W_km] for s in self.segments],
+            [[s.length_km, s.beta2_ps2_per_km, s.beta3_ps3_per_km, s.sigma_per_W_km, s.gain_per_km]
+             for s in self.segments],
             dtype=np.float64,
         )
 

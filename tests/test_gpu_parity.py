@@ -140,6 +140,29 @@ def test_grid_errors_are_reported(M):
         plan.propagate(dev(np.zeros(1 << 10), "fp64"), 0.0, 2.0)
 
 
+# ------------------------------------------------- distributed gain
+def gain_map():
+    # distributed gain on the first segment and extra loss on the second
+    # (G = g - gamma of Eq. (1)), a dispersion jump inside the 2-km intervals
+    from paper_1101_0086_gb300.workloads import gamma_from_db_per_km
+    return FiberMap((Segment(7.0, -21.7, 0.1, 1.3, 0.03), Segment(3.0, 85.0, 0.1, 1.1, -0.01)),
+                    gamma_from_db_per_km(0.2), 10.0, 4)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_distributed_gain_matches_oracle(M, prec):
+    fib = gain_map()
+    N, T = 1 << 12, 3200.0
+    A0 = wdm_field(N, T, 3, 50.0, 32, 30.0, 10.0, "qpsk", seed=7)
+    ref = oracle.mpa(A0, fib, T, 0.0, 30.0, 1.0, 20, 3)
+    plan = M.Plan(fib, N, T, 1.0, 20, 3, precision=prec)
+    got = host(plan.propagate(dev(A0, prec), 0.0, 30.0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+    ref = oracle.ss(A0, fib, T, 0.0, 30.0, 0.1)
+    got = host(M.ss_propagate(dev(A0, prec), fib, T, 0.1, 0.0, 30.0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+
+
 # ------------------------------------------------------------ split-step
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("logn", [10, 14])

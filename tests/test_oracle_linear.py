@@ -103,3 +103,31 @@ def test_inconsistent_grids_are_rejected():
         oracle.ss(A0, fm, T, 0.0, 200.0, 1.0)  # beyond the end of the link
     with pytest.raises(ValueError):
         oracle.fft(np.ones(12), +1)  # N not a power of two
+
+
+def test_distributed_gain_linear_flow_and_energy():
+    """A distributed gain g on a segment enters G = g - gamma (Eq. (1)): with
+    sigma = 0 both methods give the closed-form flow times exp(int G), and
+    with sigma != 0, gamma = 0 and no lumped amplifiers the split-step (a
+    unitary linear step times exp(int g), a modulus-preserving kick) scales
+    the energy by exactly exp(2 int g)."""
+    N, T = 1024, 400.0
+    g = gamma_from_db_per_km(0.2)
+    segs = (Segment(45.0, -21.7, 0.1, 0.0, 0.03), Segment(5.0, 190.0, 0.1, 0.0, -0.01))
+    fm = FiberMap(segs, g, 50.0, 4)
+    A0 = chirped_gaussian(N, T, 8.0, 1.0, chirp=-0.7, centre_ps=150.0)
+    z1 = 130.0
+    I2 = 2 * (45.0 * -21.7 + 5.0 * 190.0) + 30.0 * -21.7
+    I3 = 130.0 * 0.1
+    Ig = 2 * (45.0 * 0.03 + 5.0 * -0.01) + 30.0 * 0.03
+    gain = math.exp(-g * z1 + Ig) * math.exp(2 * 50.0 * g)
+    ref = closed_form_linear(A0, T, I2, I3, gain)
+    assert oracle.rel_l2(oracle.ss(A0, fm, T, 0.0, z1, 1.0), ref) < 1e-12
+    assert oracle.rel_l2(oracle.mpa(A0, fm, T, 0.0, z1, 10.0, 7, 3), ref) < 1e-12
+    segs = (Segment(3.0, -20.0, 0.1, 1.3, 0.04), Segment(1.0, 60.0, 0.1, 1.3, -0.02))
+    fm = FiberMap(segs, 0.0, 0.0, 3)
+    A1 = chirped_gaussian(N, T, 8.0, 30.0, centre_ps=200.0)
+    out = oracle.ss(A1, fm, T, 0.0, 10.0, 0.05)
+    Ig = 2 * (3.0 * 0.04 - 1.0 * 0.02) + 2.0 * 0.04
+    ratio = np.vdot(out, out).real / np.vdot(A1, A1).real
+    assert abs(ratio / math.exp(2 * Ig) - 1) < 1e-12

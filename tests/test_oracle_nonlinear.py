@@ -86,3 +86,20 @@ def test_mpa_and_ss_converge_to_the_same_wdm_solution():
     e_mpa = oracle.rel_l2(m2, mpa_x)
     assert e_ss > 1e-7 and e_mpa > 1e-7  # the comparison is not vacuous
     assert oracle.rel_l2(mpa_x, ss_x) < 0.25 * e_ss
+
+
+def test_mpa_and_split_step_agree_with_distributed_gain():
+    """With a distributed gain (G = g - gamma, Eq. (1)) both discretisations
+    converge to the same field: the MPA-SS difference at fine steps is far
+    below the difference at coarse steps, and it shrinks like dz^2."""
+    N, T = 512, 400.0
+    segs = (Segment(3.0, -20.0, 0.1, 1.3, 0.05), Segment(1.0, 60.0, 0.1, 1.3, -0.03))
+    fm = FiberMap(segs, 0.02, 4.0, 2)
+    A0 = chirped_gaussian(N, T, 10.0, 40.0, centre_ps=200.0)
+    d = []
+    for M, dz in ((40, 0.1), (80, 0.05)):
+        mpa = oracle.mpa(A0, fm, T, 0.0, 8.0, 4.0, M, 6)
+        ss = oracle.ss(A0, fm, T, 0.0, 8.0, dz)
+        d.append(oracle.rel_l2(mpa, ss))
+    assert d[1] < d[0] / 3.0
+    assert d[1] < 1e-3
