@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, split-step and CPU legs (profiling runs)")
     ap.add_argument("--schedule", default="auto", choices=["auto", "level", "wavefront"])
+    ap.add_argument("--log2-n2", type=int, default=0,
+                    help="four-step column length 2^l (default: mpa_plan_autotune chooses, before the timed region)")
     return ap.parse_args()
 
 
@@ -118,20 +120,20 @@ def peaks():
 
 
 def source_hash() -> str:
-    """Hash of the sources that define the FP32 column-pass kernel whose ncu
-    DRAM counters the roofline line quotes (kernel templates, device helpers
-    and the FP32 column-pass instantiations)."""
+    """Hash of the sources that define the FP32 column- and row-pass kernels
+    whose ncu DRAM counters the roofline line quotes (kernel templates,
+    device helpers and the FP32 instantiations)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1101_0086_gb300", "csrc")
-    for f in ("device.cuh", "kernels.cuh", "kc_f32.cu"):
+    for f in ("device.cuh", "kernels.cuh", "kc_f32.cu", "kr_f32.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
+def ncu_traffic(kernel: str, workload: str, split: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel sources."""
+    it was taken on the current kernel sources with the same four-step split."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -139,7 +141,7 @@ def ncu_traffic(kernel: str, workload: str):
     except (OSError, ValueError):
         return None
     e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash() or e.get("workload") != workload:
+    if not e or e.get("source_hash") != source_hash() or e.get("workload") != workload or e.get("split") != split:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -233,6 +235,12 @@ def run_mpa(args, world, rank, local):
     src = torch.from_numpy(A0.astype(np.complex64)).cuda()
     f = torch.empty_like(src)
     plan = mpa.Plan(w.fiber, N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32", schedule=args.schedule)
+    # plan-time tuning of the four-step split (like an FFT library's planning)
+    if args.log2_n2 > 0:
+        plan.set_split(args.log2_n2)
+        log2_n2 = args.log2_n2
+    else:
+        log2_n2 = plan.autotune()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -275,7 +283,8 @@ def run_mpa(args, world, rank, local):
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     kern = {k: {"ms_total": round(v[0], 3), "launches": v[1], "share": round(v[0] / sum(x[0] for x in prof.values()), 4),
                 "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1)} for k, v in prof.items()}
-    traffic = ncu_traffic(dom_name, w.name)
+    split = f"N1 x N2 = 2^{int(np.log2(N)) - log2_n2} x 2^{log2_n2}"
+    traffic = ncu_traffic(dom_name, w.name, split)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom_name,
                 "algorithmic_bytes_per_launch": dom_bytes / dom_n, "peak_source": peak_src}
@@ -286,6 +295,7 @@ def run_mpa(args, world, rank, local):
             "config": {"workload": w.name, "N": N, "km_per_step": km, "channels": w.n_channels,
                        "symbols_per_channel": w.n_symbols, "L_km": w.mpa_L_km, "M": w.mpa_M,
                        "n_iter": w.mpa_n_iter, "method": "MPA FP32 (FP64 state)", "schedule": args.schedule,
+                       "split": split,
                        "l2": "flushed between steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": roofline, "kernels": kern, "clocks": ck, "gpu_launches": launches,

@@ -136,6 +136,23 @@ MPA_API int mpa_propagate(mpa_plan* plan, void* field, double z_from_km, double 
  * (a multiple of L).  Exposed for step-level parity checks. */
 MPA_API int mpa_interval(mpa_plan* plan, const void* psi0, void* psiM, double z0_km, mpa_stream stream);
 
+/* Picks the four-step split N = N1 x N2 of the plan's transforms by timing:
+ * one interval (MPA steps 2-7) is run on the GPU for every admissible
+ * column length N2 = 2^l (l within 3 of log2(N)/2, both passes supported,
+ * and the reverse-mode tiling kept valid) and the fastest is kept.
+ * Overwrites the plan's working buffers (call it before propagating) and
+ * synchronises the stream.  *log2_n2 (may be NULL) receives the choice.
+ * The split changes only the order of FP32 rounding, not the method.
+ * Level-schedule plans only (a WAVEFRONT plan is left unchanged).  The paper
+ * has no counterpart; this is the library's own tuning. */
+MPA_API int mpa_plan_autotune(mpa_plan* plan, mpa_stream stream, int32_t* log2_n2);
+
+/* Sets the split to column length 2^log2_n2 without timing (e.g. a value an
+ * earlier mpa_plan_autotune chose).  MPA_ERR_UNSUPPORTED_N if the passes or
+ * the reverse-mode tiling do not support it; a WAVEFRONT plan accepts only
+ * its current split.  Host-only. */
+MPA_API int mpa_plan_set_split(mpa_plan* plan, int32_t log2_n2);
+
 /* Returns MPA_ERR_NONFINITE if any propagate since the last call produced a
  * NaN/Inf (synchronises the stream), else MPA_OK; clears the flag. */
 MPA_API int mpa_plan_status(mpa_plan* plan, mpa_stream stream);

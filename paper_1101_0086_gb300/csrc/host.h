@@ -136,16 +136,40 @@ inline int ilog2(long long n) {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+#ifndef MPA_LOGN2_SHIFT
+#define MPA_LOGN2_SHIFT 0
+#endif
+
 struct Split {
     int logN, logN1, logN2;
     long long N, N1, N2;
 };
 
+// The split with column length 2^logN2 (0 if the passes do not support it).
+inline int split_with(long long N, int prec, int logN2, Split* s) {
+    if (N < 256 || (N & (N - 1)) != 0) return MPA_ERR_UNSUPPORTED_N;
+    s->logN = ilog2(N);
+    s->logN2 = logN2;
+    s->logN1 = s->logN - logN2;
+    const int rmax = prec == MPA_FP32 ? kr_log_max<float>() : kr_log_max<double>();
+    if (logN2 < KC_LOG_MIN || logN2 > KC_LOG_MAX || s->logN1 < KR_LOG_MIN || s->logN1 > rmax)
+        return MPA_ERR_UNSUPPORTED_N;
+    s->N = N;
+    s->N1 = 1ll << s->logN1;
+    s->N2 = 1ll << s->logN2;
+    return MPA_OK;
+}
+
 inline int split_n(long long N, int prec, Split* s) {
     if (N < 256 || (N & (N - 1)) != 0) return MPA_ERR_UNSUPPORTED_N;
     s->logN = ilog2(N);
     if (s->logN > (prec == MPA_FP32 ? 25 : 24)) return MPA_ERR_UNSUPPORTED_N;
-    s->logN2 = s->logN / 2 < KC_LOG_MAX ? s->logN / 2 : KC_LOG_MAX;
+    // column length N2 = 2^logN2: about sqrt(N), shifted towards longer rows
+    // by MPA_LOGN2_SHIFT (rows are contiguous, columns strided)
+    int l2 = s->logN / 2 - MPA_LOGN2_SHIFT;
+    if (l2 < KC_LOG_MIN) l2 = KC_LOG_MIN;
+    if (l2 > KC_LOG_MAX) l2 = KC_LOG_MAX;
+    s->logN2 = l2;
     s->logN1 = s->logN - s->logN2;
     const int rmax = prec == MPA_FP32 ? kr_log_max<float>() : kr_log_max<double>();
     if (s->logN2 < KC_LOG_MIN || s->logN1 > rmax) return MPA_ERR_UNSUPPORTED_N;

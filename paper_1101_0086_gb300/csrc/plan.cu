@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "adj_launch.h"
 #include "plan.h"
 
 using namespace mpa;
@@ -434,6 +435,83 @@ int mpa_plan_set_workspace(mpa_plan* p, void* ws, size_t bytes) {
     MPA_TRY(cudaMemcpy(p->ws + p->off_gains, gains, sizeof(gains), cudaMemcpyHostToDevice));
     MPA_TRY(cudaMemset(p->ws + p->off_err, 0, sizeof(unsigned int)));
     return MPA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The split with column length 2^l if every pass (and the reverse-mode
+// tiling, one node per tile, for N >= 2^13) supports it.
+bool admissible_split(const mpa_plan* p, int l, Split* s) {
+    if (split_with(p->sp.N, p->prec, l, s) != MPA_OK) return false;
+    if (s->logN >= 13) {
+        const bool f32 = p->prec == MPA_FP32;
+        const int gc = f32 ? kca_tile_cols<float>(s->logN2) : kca_tile_cols<double>(s->logN2);
+        const int gr = f32 ? kra_tile_rows<float>(s->logN1) : kra_tile_rows<double>(s->logN1);
+        if (gc <= 0 || gr <= 0 || gc > s->N1 || gr > s->N2) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpa_plan_set_split(mpa_plan* p, int32_t log2_n2) {
+    if (!p) return MPA_ERR_INVALID_ARG;
+    if (p->wf) return log2_n2 == p->sp.logN2 ? MPA_OK : MPA_ERR_UNSUPPORTED_N;
+    Split s;
+    if (!admissible_split(p, log2_n2, &s)) return MPA_ERR_UNSUPPORTED_N;
+    p->sp = s;
+    return MPA_OK;
+}
+
+int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
+    if (!p) return MPA_ERR_INVALID_ARG;
+    if (!p->ws) return MPA_ERR_WORKSPACE;
+    if (log2_n2) *log2_n2 = p->sp.logN2;
+    if (p->wf) return MPA_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const Split keep = p->sp;
+    const size_t N = (size_t)keep.N;
+    const bool f32 = p->prec == MPA_FP32;
+    cudaEvent_t e0, e1;
+    MPA_TRY(cudaEventCreate(&e0));
+    MPA_TRY(cudaEventCreate(&e1));
+    Split best = keep;
+    float best_ms = -1.f;
+    int rc = MPA_OK;
+    for (int l = keep.logN / 2 - 3; l <= keep.logN / 2 + 3 && rc == MPA_OK; ++l) {
+        Split s;
+        if (!admissible_split(p, l, &s)) continue;
+        p->sp = s;
+        // a zero field: the timing does not depend on the values
+        if (cudaMemsetAsync(p->ws + p->off_state, 0, N * sizeof(double2), st) != cudaSuccess ||
+            (f32 && cudaMemsetAsync(p->ws + p->off_psi0c, 0, N * sizeof(float2), st) != cudaSuccess)) {
+            rc = cuda_fail(cudaGetLastError());
+            break;
+        }
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && rc == MPA_OK; ++rep) {  // rep 0 warms up (first launches, attributes)
+            if (cudaEventRecord(e0, st) != cudaSuccess) { rc = MPA_ERR_CUDA; break; }
+            rc = f32 ? run_interval<float>(p, 0, 0, 1, nullptr, st) : run_interval<double>(p, 0, 0, 1, nullptr, st);
+            if (rc == MPA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = cuda_fail(cudaGetLastError());
+        }
+        if (rc == MPA_OK && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->sp = best;
+    if (rc != MPA_OK) p->sp = keep;
+    if (log2_n2) *log2_n2 = p->sp.logN2;
+    MPA_TRY(cudaMemsetAsync(p->ws + p->off_err, 0, sizeof(unsigned int), st));
+    return rc;
 }
 
 int mpa_propagate(mpa_plan* p, void* field, double z_from_km, double z_to_km, mpa_stream stream) {

@@ -54,7 +54,7 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "mpa_profile_read", "mpa_profile_kind_name", "mpa_fft_noalloc", "mpa_batch_create",
            "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate", "mpa_batch_destroy",
            "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
-           "ss_adjoint_workspace_size", "ss_adjoint")
+           "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split")
 
 
 def library_path() -> str:
@@ -108,11 +108,13 @@ def lib() -> ctypes.CDLL:
         L.ss_adjoint_workspace_size.argtypes = [ctypes.POINTER(_FiberMap), i64, i32, dbl, dbl, dbl, i32, szp]
         L.ss_adjoint.argtypes = [ctypes.POINTER(_FiberMap), i64, dbl, dbl, i32, vp, vp, vp, dbl, dbl, i32, vp,
                                  ctypes.c_size_t, dptr, dptr, vp]
+        L.mpa_plan_autotune.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        L.mpa_plan_set_split.argtypes = [vp, i32]
         L.mpa_profile_kind_name.restype = ctypes.c_char_p
         for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
                   "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft",
                   "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
-           "ss_adjoint_workspace_size", "ss_adjoint"):
+                  "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -195,6 +197,17 @@ class Plan:
         _check(lib().mpa_interval(self._h, p0, ctypes.c_void_p(out.data_ptr()), float(z0_km), _stream(stream)),
                "mpa_interval")
         return out
+
+    def autotune(self, stream=None) -> int:
+        """``mpa_plan_autotune``: time every admissible four-step split on the
+        GPU and keep the fastest; returns log2 of the chosen column length."""
+        l2 = ctypes.c_int32()
+        _check(lib().mpa_plan_autotune(self._h, _stream(stream), ctypes.byref(l2)), "mpa_plan_autotune")
+        return int(l2.value)
+
+    def set_split(self, log2_n2: int) -> None:
+        """``mpa_plan_set_split``: use column length 2^log2_n2 (no timing)."""
+        _check(lib().mpa_plan_set_split(self._h, int(log2_n2)), "mpa_plan_set_split")
 
     @property
     def n_segments(self) -> int:

@@ -111,3 +111,21 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mpa, "_lib", None)
     with pytest.raises(mpa.MPAError):
         mpa.lib()
+
+
+def test_split_selection_is_validated_on_the_host(L):
+    """mpa_plan_set_split accepts every column length both passes (and the
+    reverse-mode tiling) support, and rejects the others, without a GPU."""
+    fib = dm_map(4)
+    L.mpa_plan_set_split.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    for prec in (0, 1):
+        rc, h = _plan(L, fib, 1 << 20, 102400.0, 5.0, 142, 3, prec=prec)
+        assert rc == 0
+        ok = [l for l in range(2, 14) if L.mpa_plan_set_split(h, l) == 0]
+        assert 10 in ok and 8 in ok           # the square split and a longer-row one
+        assert min(ok) >= 4 and max(ok) <= 11  # column pass 2^4..2^11
+        assert L.mpa_plan_set_split(h, 3) == 2 and L.mpa_plan_set_split(h, 12) == 2
+        L.mpa_plan_destroy(h)
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 710, 3, schedule=2)  # wavefront keeps its split
+    assert L.mpa_plan_set_split(h, 7) == 0 and L.mpa_plan_set_split(h, 6) == 2
+    L.mpa_plan_destroy(h)

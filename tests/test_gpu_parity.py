@@ -270,3 +270,28 @@ def test_batch_graph_replay_and_oracle(M):
     c.propagate(use_graph=True)
     ref = oracle.mpa(s.field(), s.fiber, s.T_ps, 0.0, s.length_km, L, Mn, n_iter)
     assert oracle.rel_l2(host(f), ref) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_every_split_and_the_autotuned_one_match_the_oracle(M, prec):
+    """The four-step split only reorders FP32 rounding: every admissible
+    column length, and the one mpa_plan_autotune picks, give the oracle's
+    result within the tolerance."""
+    fib = small_map()
+    N, T = 1 << 14, 6400.0
+    A0 = wdm_field(N, T, 3, 50.0, 64, 30.0, 10.0, "qpsk", seed=11)
+    ref = oracle.mpa(A0, fib, T, 0.0, 20.0, 2.0, 24, 3)
+    plan = M.Plan(fib, N, T, 2.0, 24, 3, precision=prec)
+    chosen = plan.autotune()
+    got = host(plan.propagate(dev(A0, prec), 0.0, 20.0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+    tried = 0
+    for l in range(4, 12):
+        try:
+            plan.set_split(l)
+        except M.MPAError:
+            continue
+        tried += 1
+        got = host(plan.propagate(dev(A0, prec), 0.0, 20.0))
+        assert oracle.rel_l2(got, ref) < TOL[prec], l
+    assert tried >= 3 and 4 <= chosen <= 11
