@@ -414,6 +414,7 @@ def run_batch(args, world, rank, local):
     src = [torch.from_numpy(s.field().astype(np.complex64)).cuda() for s in specs]
     fields = [x.clone() for x in src]
     batch = mpa.Batch([(s.fiber, s.T_ps, s.length_km, f) for s, f in zip(specs, fields)], L, Mn, nit, "fp32")
+    batch.autotune(torch.cuda.current_stream())  # per-group four-step split, before the timed region
     units = float(sum(s.N * s.length_km for s in specs))
     stream = torch.cuda.current_stream()
 
@@ -443,6 +444,8 @@ def run_batch(args, world, rank, local):
     # sequential per-link loop on every 8th link (same plans as a user would make)
     sub = specs[::8]
     plans = [mpa.Plan(s.fiber, s.N, s.T_ps, L, Mn, nit, "fp32") for s in sub]
+    for p in plans:
+        p.autotune()
     xs = [torch.from_numpy(s.field().astype(np.complex64)).cuda() for s in sub]
     for p, x, sp in zip(plans, xs, sub):
         p.propagate(x.clone(), 0.0, sp.length_km, stream)

@@ -222,6 +222,11 @@ MPA_API int mpa_batch_workspace_size(const mpa_batch* batch, size_t* bytes);
 /* Attaches caller-owned device workspace and uploads the node tables
  * (synchronous); a previously captured graph is discarded. */
 MPA_API int mpa_batch_set_workspace(mpa_batch* batch, void* workspace, size_t bytes);
+/* mpa_plan_autotune for every N group of the batch: times the group's first
+ * interval for each admissible four-step split and keeps the fastest.
+ * Overwrites the batch's working buffers (call it before propagating; the
+ * fields are not touched), drops a captured graph, synchronises. */
+MPA_API int mpa_batch_autotune(mpa_batch* batch, mpa_stream stream);
 /* Propagates every link.  use_graph != 0: the first such call runs the
  * launches directly and captures them into a CUDA graph (one parallel
  * branch per N group, on library-owned streams joined to `stream`); later

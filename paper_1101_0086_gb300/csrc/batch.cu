@@ -331,6 +331,73 @@ int mpa_batch_propagate(mpa_batch* b, int32_t use_graph, mpa_stream stream) {
     return MPA_OK;
 }
 
+int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
+    if (!b) return MPA_ERR_INVALID_ARG;
+    if (!b->ws) return MPA_ERR_WORKSPACE;
+    release_graph(b);  // the captured launches use the old splits
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    MPA_TRY(cudaEventCreate(&e0));
+    MPA_TRY(cudaEventCreate(&e1));
+    int rc = MPA_OK;
+    for (auto& g : b->groups) {
+        const Split keep = g.sp;
+        const int n = (int)g.links.size();
+        const size_t N = (size_t)keep.N;
+        Split best = keep;
+        float best_ms = -1.f;
+        for (int l = keep.logN / 2 - 3; l <= keep.logN / 2 + 3 && rc == MPA_OK; ++l) {
+            Split s;
+            if (split_with(keep.N, b->prec, l, &s) != MPA_OK) continue;
+            g.sp = s;
+            // the group's first interval on a zero field (timing does not depend on values)
+            if (cudaMemsetAsync(b->ws + g.off_state, 0, (size_t)n * N * sizeof(double2), st) != cudaSuccess ||
+                (b->prec == MPA_FP32 &&
+                 cudaMemsetAsync(b->ws + g.off_psi0c, 0, (size_t)n * N * sizeof(float2), st) != cudaSuccess)) {
+                rc = cuda_fail(cudaGetLastError());
+                break;
+            }
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == MPA_OK; ++rep) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) {
+                    rc = MPA_ERR_CUDA;
+                    break;
+                }
+                rc = b->prec == MPA_FP32
+                         ? mpa_levels<float>(g.sp, b->M, b->n_iter, g.active[0],
+                                             reinterpret_cast<float2*>(b->ws + g.off_psi),
+                                             reinterpret_cast<float2*>(b->ws + g.off_psi0c),
+                                             reinterpret_cast<double2*>(b->ws + g.off_state),
+                                             reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
+                                             reinterpret_cast<const int*>(b->ws + g.off_loff),
+                                             reinterpret_cast<const double*>(b->ws + g.off_gain),
+                                             reinterpret_cast<unsigned int*>(b->ws + g.off_err), 1, nullptr, st)
+                         : mpa_levels<double>(g.sp, b->M, b->n_iter, g.active[0],
+                                              reinterpret_cast<double2*>(b->ws + g.off_psi),
+                                              reinterpret_cast<double2*>(b->ws + g.off_psi0c),
+                                              reinterpret_cast<double2*>(b->ws + g.off_state),
+                                              reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
+                                              reinterpret_cast<const int*>(b->ws + g.off_loff),
+                                              reinterpret_cast<const double*>(b->ws + g.off_gain),
+                                              reinterpret_cast<unsigned int*>(b->ws + g.off_err), 1, nullptr, st);
+                if (rc == MPA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    rc = cuda_fail(cudaGetLastError());
+            }
+            if (rc == MPA_OK && (best_ms < 0.f || ms < best_ms)) {
+                best_ms = ms;
+                best = s;
+            }
+        }
+        g.sp = rc == MPA_OK ? best : keep;
+        if (cudaMemsetAsync(b->ws + g.off_err, 0, sizeof(unsigned int), st) != cudaSuccess && rc == MPA_OK)
+            rc = cuda_fail(cudaGetLastError());
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 void mpa_batch_destroy(mpa_batch* b) {
     if (!b) return;
     release_graph(b);

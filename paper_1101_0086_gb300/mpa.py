@@ -54,7 +54,8 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "mpa_profile_read", "mpa_profile_kind_name", "mpa_fft_noalloc", "mpa_batch_create",
            "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate", "mpa_batch_destroy",
            "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
-           "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split")
+           "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split",
+           "mpa_batch_autotune")
 
 
 def library_path() -> str:
@@ -110,6 +111,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_size_t, dptr, dptr, vp]
         L.mpa_plan_autotune.argtypes = [vp, vp, ctypes.POINTER(i32)]
         L.mpa_plan_set_split.argtypes = [vp, i32]
+        L.mpa_batch_autotune.argtypes = [vp, vp]
+        L.mpa_batch_autotune.restype = ctypes.c_int
         L.mpa_profile_kind_name.restype = ctypes.c_char_p
         for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
                   "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft",
@@ -344,6 +347,10 @@ class Batch:
         self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=device)
         _check(L.mpa_batch_set_workspace(h, ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel()),
                "mpa_batch_set_workspace")
+
+    def autotune(self, stream=None) -> None:
+        """``mpa_batch_autotune``: per-group four-step split by timing."""
+        _check(lib().mpa_batch_autotune(self._h, _stream(stream)), "mpa_batch_autotune")
 
     def propagate(self, use_graph: bool = True, stream=None) -> None:
         _check(lib().mpa_batch_propagate(self._h, 1 if use_graph else 0, _stream(stream)), "mpa_batch_propagate")

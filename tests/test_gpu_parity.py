@@ -295,3 +295,20 @@ def test_every_split_and_the_autotuned_one_match_the_oracle(M, prec):
         got = host(plan.propagate(dev(A0, prec), 0.0, 20.0))
         assert oracle.rel_l2(got, ref) < TOL[prec], l
     assert tried >= 3 and 4 <= chosen <= 11
+
+
+def test_autotuned_batch_matches_the_oracle(M):
+    """Per-group split tuning changes only the rounding order: after
+    mpa_batch_autotune every link still matches the oracle, and the fields
+    were not touched by the tuning."""
+    specs = _batch_specs()
+    L, Mn, n_iter = 5.0, 20, 3
+    fields = [dev(s.field(), "fp32") for s in specs]
+    b = M.Batch([(s.fiber, s.T_ps, s.length_km, f) for s, f in zip(specs, fields)], L, Mn, n_iter)
+    b.autotune()
+    for s, f in zip(specs, fields):
+        assert oracle.rel_l2(host(f), s.field()) < 1e-7
+    b.propagate(use_graph=True)
+    for s, f in list(zip(specs, fields))[:3]:
+        ref = oracle.mpa(s.field(), s.fiber, s.T_ps, 0.0, s.length_km, L, Mn, n_iter)
+        assert oracle.rel_l2(host(f), ref) < TOL["fp32"]
