@@ -553,6 +553,17 @@ def run_grad(args, world, rank, local):
         e.record(stream)
         torch.cuda.synchronize()
         t = s.elapsed_time(e) / 1e3 / reps
+        kern = None
+        if meth == "mpa":
+            # per-kernel times of one more gradient (CUDA events around every launch)
+            mpa.profile(True)
+            step()
+            torch.cuda.synchronize()
+            prof = mpa.profile_read()
+            mpa.profile(False)
+            tot = sum(v[0] for v in prof.values())
+            kern = {k: {"ms": round(v[0], 2), "launches": v[1], "share": round(v[0] / tot, 4),
+                        "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1)} for k, v in prof.items() if v[1] > 0}
         # scaling identity of the cubic term (exact for both discrete methods):
         # sum sigma dl/dsigma - Re<g_A, A>/2 = -Re<g_out, out>/2, with the
         # direct dependence of l on A_in taken out of g_A
@@ -564,7 +575,7 @@ def run_grad(args, world, rank, local):
                                  "scaling_identity_residual": abs(lhs - rhs) / max(abs(rhs), 1e-300),
                                  "launches_per_gradient": (mpa.kernel_launches() - l0) / reps,
                                  "grad_sigma_first": [float(x) for x in gs[:2]],
-                                 "grad_beta2_first": [float(x) for x in gb[:2]]}
+                                 "grad_beta2_first": [float(x) for x in gb[:2]], "kernels": kern}
     line = {"metric": "gradient evaluations in mode*km/s (forward with checkpoints + loss + reverse pass)",
             "value": res["mpa_fp32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -250,10 +250,16 @@ template <typename T> __device__ __forceinline__ cx<T> expi_ratio(long long e, i
     const long long n = 1ll << log2n;
     e &= (n - 1);
     if (e >= (n >> 1)) e -= n;
-    const T x = (T)e * (T)2 / (T)n;  // exact: |e| <= 2^24 (FP32) or 2^52 (FP64)
     T s, c;
-    if constexpr (sizeof(T) == 4) sincospif(x, &s, &c);
-    else sincospi(x, &s, &c);
+    if constexpr (sizeof(T) == 4) {
+        // |e| <= 2^24 here: a 32-bit conversion (a 64-bit one runs on the
+        // FP64 pipe) and an exact scaling by the power of two 2^(1 - log2n)
+        const float x = (float)(int)e * __int_as_float((128 - log2n) << 23);
+        sincospif(x, &s, &c);
+    } else {
+        const double x = (double)e * 2.0 / (double)n;  // exact: |e| <= 2^52
+        sincospi(x, &s, &c);
+    }
     return mkc(c, s);
 }
 
