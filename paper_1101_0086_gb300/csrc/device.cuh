@@ -287,18 +287,28 @@ template <int L> struct TwDims {
     static constexpr int NHI = L >> SH;
 };
 
+// Slot of entry e of the low twiddle table.  A row-pass warp looks up
+// e = s j for 32 consecutive j and a power of two s; 8-byte entries sit in 16
+// bank pairs, so in natural order the stride s = 4, 8, 16 lookups would
+// collide 4- to 8-fold.  XOR-ing the entry's 16-block index into its low
+// four bits spreads every such stride over distinct bank pairs.
+template <int NLO> __device__ __forceinline__ int tw_lo_slot(int e) {
+    if constexpr (NLO >= 32) return e ^ ((e >> 4) & 15);
+    else return e;
+}
+
 template <typename T, int L> __device__ __forceinline__ void tw_init(cx<T>* hi, cx<T>* lo, int tid, int nt) {
     typedef TwDims<L> D;
     for (int i = tid; i < D::NLO + D::NHI; i += nt) {
-        if (i < D::NLO) lo[i] = expi_ratio<T>(i, D::logL);
+        if (i < D::NLO) lo[tw_lo_slot<D::NLO>(i)] = expi_ratio<T>(i, D::logL);
         else hi[i - D::NLO] = expi_ratio<T>((long long)(i - D::NLO) << D::SH, D::logL);
     }
 }
 
 template <typename T, int L> __device__ __forceinline__ cx<T> tw_get(const cx<T>* hi, const cx<T>* lo, int e) {
     typedef TwDims<L> D;
-    if constexpr (D::NHI == 1) return lo[e];
-    else return cmul(hi[e >> D::SH], lo[e & (D::NLO - 1)]);
+    if constexpr (D::NHI == 1) return lo[tw_lo_slot<D::NLO>(e)];
+    else return cmul(hi[e >> D::SH], lo[tw_lo_slot<D::NLO>(e & (D::NLO - 1))]);
 }
 
 // v[r] *= W_L^{S r e1} for r = 1..R-1 (R <= 32): table lookups of

@@ -655,20 +655,37 @@ __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
     T rx = T(0.5) * v0.x, ry = T(0.5) * v0.y, cxx = T(0), cyy = T(0);
     const C p0 = p.psi0c[lo + k];
     C vl = v0;
-    for (int j = 1; j <= p.M; ++j) {
-        C* q = psi + (long long)j * p.N + k;
-        vl = *q;
-        if (p.mode == 0) {
-            // psi_0 + i (R + V_j/2), R = running sum (compensation removed)
-            const T sx = (rx - cxx) + T(0.5) * vl.x, sy = (ry - cyy) + T(0.5) * vl.y;
-            *q = mkc(p0.x - sy, p0.y + sx);
+    // V_j are loaded SCAN_U nodes ahead of their use (more loads in flight
+    // per thread; the loads never touch a node the loop has written)
+    constexpr int U = 8;
+    C nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) nxt[u] = (1 + u <= p.M) ? psi[(long long)(1 + u) * p.N + k] : mkc(T(0), T(0));
+    for (int jb = 1; jb <= p.M; jb += U) {
+        C cur[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cur[u] = nxt[u];
+            const int jn = jb + U + u;
+            nxt[u] = (jn <= p.M) ? psi[(long long)jn * p.N + k] : mkc(T(0), T(0));
         }
-        if constexpr (sizeof(T) == 4) {
-            kahan_add(rx, cxx, vl.x);
-            kahan_add(ry, cyy, vl.y);
-        } else {
-            rx += vl.x;
-            ry += vl.y;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = jb + u;
+            if (j > p.M) break;
+            vl = cur[u];
+            if (p.mode == 0) {
+                // psi_0 + i (R + V_j/2), R = running sum (compensation removed)
+                const T sx = (rx - cxx) + T(0.5) * vl.x, sy = (ry - cyy) + T(0.5) * vl.y;
+                psi[(long long)j * p.N + k] = mkc(p0.x - sy, p0.y + sx);
+            }
+            if constexpr (sizeof(T) == 4) {
+                kahan_add(rx, cxx, vl.x);
+                kahan_add(ry, cyy, vl.y);
+            } else {
+                rx += vl.x;
+                ry += vl.y;
+            }
         }
     }
     if (p.mode == 0) return;
