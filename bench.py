@@ -525,6 +525,7 @@ def run_grad(args, world, rank, local):
         a = torch.from_numpy(A0).to(dt).cuda()
         if meth == "mpa":
             plan = mpa.Plan(fib, N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision=prec)
+            plan.autotune(stream)
             ws = torch.empty(plan.adjoint_workspace_bytes(0.0, km), dtype=torch.uint8, device="cuda")
         else:
             ssw = torch.empty(mpa.ss_workspace_bytes(N, prec), dtype=torch.uint8, device="cuda")

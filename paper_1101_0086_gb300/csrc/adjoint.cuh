@@ -23,6 +23,16 @@
 
 #include "kernels.cuh"
 
+// CTAs per SM the reverse passes are compiled for (1: up to 255 registers,
+// no spills; 2: 128 registers): column passes 1 (2 spills and is slower),
+// row passes 2 (2357 -> 2810 GB/s in the MPA reverse row pass).
+#ifndef MPA_ADJ_MINB
+#define MPA_ADJ_MINB 1
+#endif
+#ifndef MPA_ADJ_MINB_R
+#define MPA_ADJ_MINB_R 2
+#endif
+
 namespace mpa {
 
 enum { KCA_G = 0, KCA_P = 1 };
@@ -92,8 +102,26 @@ template <int NT> __device__ __forceinline__ double block_sum(double v, double* 
 // Im(conj(a) b)
 template <typename C> __device__ __forceinline__ auto im_conj_mul(C a, C b) { return a.x * b.y - a.y * b.x; }
 
+// A thread's partial sum of a reduction: compensated in FP32 (FP64 adds
+// are scarce on this GPU), plain in FP64; the block sums it in FP64.
+template <typename T> struct PartSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T v) {
+        if constexpr (sizeof(T) == 4) kahan_add(s, c, v);
+        else s += v;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// k'^2 in the working precision (exact in FP32 up to |k'| = 2^12, then
+// rounded once)
+template <typename T> __device__ __forceinline__ T ksq(long long kk) {
+    const T x = (T)(int)kk;
+    return x * x;
+}
+
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) kca_kernel(const KCAParams<T> p) {
+__global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MPA_ADJ_MINB : 1) kca_kernel(const KCAParams<T> p) {
     typedef cx<T> C;
     typedef KCGeom<T, L> Gm;
     typedef Tiling<T> P;
@@ -130,7 +158,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) kca_kernel(const KCAParam
     }
     __syncthreads();
 
-    double acc = 0.0;
+    PartSum<T> acc;
     C vin[XA::Q0][XA::R0];
 #pragma unroll
     for (int q = 0; q < XA::Q0; ++q) {
@@ -145,7 +173,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) kca_kernel(const KCAParam
             C v = gn[idx];
             if constexpr (INV) {
                 const long long kk = signed_k(idx, p.N);
-                acc += (double)(kk * kk) * (double)im_conj_mul(v, aux[idx]);
+                acc.add(ksq<T>(kk) * im_conj_mul(v, aux[idx]));
                 C ph;
                 if constexpr (FAST) ph = expi_turns_poly(th[r]);
                 else ph = expi_turns<T>(phase_q64(kk, nc));
@@ -181,17 +209,17 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) kca_kernel(const KCAParam
                 if constexpr (FAST) ph = expi_turns_poly(th[r]);
                 else ph = expi_turns<T>(phase_q64(kk, nc));
                 v = cscale(cmul(v, cconj(ph)), post);
-                acc -= (double)(kk * kk) * (double)im_conj_mul(v, aux[idx]);
+                acc.add(-ksq<T>(kk) * im_conj_mul(v, aux[idx]));
             }
             gn[idx] = v;
         }
     }
-    const double tot = block_sum<NT>(acc, red);
+    const double tot = block_sum<NT>(acc.value(), red);
     if (tid == 0) p.part[blockIdx.x] = tot * p.wscale;
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) kra_kernel(const KRAParams<T> p) {
+__global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MPA_ADJ_MINB_R : 1) kra_kernel(const KRAParams<T> p) {
     typedef cx<T> C;
     typedef KRGeom<T, L> Gm;
     typedef Tiling<T, 1> P;
@@ -245,7 +273,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) kra_kernel(const KRAParam
         }
         XI::run(vin, vg, s, thi, tlo);
     }
-    double acc = 0.0;
+    PartSum<T> acc;
 #pragma unroll
     for (int q = 0; q < XI::QL; ++q) {
 #pragma unroll
@@ -253,7 +281,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) kra_kernel(const KRAParam
             const C a = cscale(va[q][r], p.inv_n);
             const C gu = vg[q][r];
             const T pw = a.x * a.x + a.y * a.y;
-            acc += (double)(pw * (gu.x * a.x + gu.y * a.y));  // Re(conj(g_U') U)
+            acc.add(pw * (gu.x * a.x + gu.y * a.y));  // Re(conj(g_U') U)
             const C a2 = mkc(a.x * a.x - a.y * a.y, T(2) * a.x * a.y);
             const C t = cmul(a2, cconj(gu));
             vg[q][r] = mkc(sig * (T(2) * pw * gu.x + t.x), sig * (T(2) * pw * gu.y + t.y));
@@ -274,7 +302,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) kra_kernel(const KRAParam
             dst[l] = cmul(vout[q][r], w);
         }
     }
-    const double tot = block_sum<NT>(acc, red);
+    const double tot = block_sum<NT>(acc.value(), red);
     if (tid == 0) p.part[blockIdx.x] = tot;
 }
 
@@ -305,37 +333,71 @@ __global__ void __launch_bounds__(256) rscan_kernel(const RScanParams<T> p) {
             g[(long long)p.M * p.N + k] = half;
         } else if (p.mode == RSCAN_LEVEL) {
             T tx = T(0), ty = T(0), cx_ = T(0), cy_ = T(0);  // sum_{l>j} g_psi_l (compensated in FP32)
-            double sx = 0.0, sy = 0.0;
-            for (int j = p.M; j >= 0; --j) {
-                C* q = g + (long long)j * p.N + k;
-                const C gl = *q;
-                sx += (double)gl.x;
-                sy += (double)gl.y;
-                const T ux = tx - cx_, uy = ty - cy_;
-                const T ax = j == 0 ? T(0.5) * ux : ux + T(0.5) * gl.x;
-                const T ay = j == 0 ? T(0.5) * uy : uy + T(0.5) * gl.y;
-                *q = mkc(ay, -ax);
-                if (j > 0) {
+            // sum over all l for the gradient of psi_0: compensated in the
+            // working precision (FP64 adds are scarce on this GPU)
+            T sx = T(0), sy = T(0), csx = T(0), csy = T(0);
+            // nodes loaded U ahead of their use (downwards; never a node already written)
+            constexpr int U = 8;
+            C nxt[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) nxt[u] = (p.M - u >= 0) ? g[(long long)(p.M - u) * p.N + k] : mkc(T(0), T(0));
+            for (int jb = p.M; jb >= 0; jb -= U) {
+                C cur[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    cur[u] = nxt[u];
+                    const int jn = jb - U - u;
+                    nxt[u] = (jn >= 0) ? g[(long long)jn * p.N + k] : mkc(T(0), T(0));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = jb - u;
+                    if (j < 0) break;
+                    const C gl = cur[u];
                     if constexpr (sizeof(T) == 4) {
-                        kahan_add(tx, cx_, gl.x);
-                        kahan_add(ty, cy_, gl.y);
+                        kahan_add(sx, csx, gl.x);
+                        kahan_add(sy, csy, gl.y);
                     } else {
-                        tx += gl.x;
-                        ty += gl.y;
+                        sx += gl.x;
+                        sy += gl.y;
+                    }
+                    const T ux = tx - cx_, uy = ty - cy_;
+                    const T ax = j == 0 ? T(0.5) * ux : ux + T(0.5) * gl.x;
+                    const T ay = j == 0 ? T(0.5) * uy : uy + T(0.5) * gl.y;
+                    g[(long long)j * p.N + k] = mkc(ay, -ax);
+                    if (j > 0) {
+                        if constexpr (sizeof(T) == 4) {
+                            kahan_add(tx, cx_, gl.x);
+                            kahan_add(ty, cy_, gl.y);
+                        } else {
+                            tx += gl.x;
+                            ty += gl.y;
+                        }
                     }
                 }
             }
             double2 s0 = p.gs0[k];
-            p.gs0[k] = make_double2(s0.x + sx, s0.y + sy);
+            p.gs0[k] = make_double2(s0.x + ((double)sx - (double)csx), s0.y + ((double)sy - (double)csy));
         } else {
-            double sx = 0.0, sy = 0.0;
-            for (int j = 0; j <= p.M; ++j) {
-                const C gl = g[(long long)j * p.N + k];
-                sx += (double)gl.x;
-                sy += (double)gl.y;
+            T sx = T(0), sy = T(0), csx = T(0), csy = T(0);
+            constexpr int U = 8;
+            for (int jb = 0; jb <= p.M; jb += U) {
+                C cur[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) cur[u] = (jb + u <= p.M) ? g[(long long)(jb + u) * p.N + k] : mkc(T(0), T(0));
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if constexpr (sizeof(T) == 4) {
+                        kahan_add(sx, csx, cur[u].x);
+                        kahan_add(sy, csy, cur[u].y);
+                    } else {
+                        sx += cur[u].x;
+                        sy += cur[u].y;
+                    }
+                }
             }
             double2 s0 = p.gs0[k];
-            p.gs0[k] = make_double2(s0.x + sx, s0.y + sy);
+            p.gs0[k] = make_double2(s0.x + ((double)sx - (double)csx), s0.y + ((double)sy - (double)csy));
         }
     }
     if (p.mode == RSCAN_TOP) {
@@ -412,7 +474,7 @@ template <typename T> struct SSRParams {
 };
 
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) ssc_kernel(const SSCParams<T> p) {
+__global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MPA_ADJ_MINB : 1) ssc_kernel(const SSCParams<T> p) {
     typedef cx<T> C;
     typedef KCGeom<T, L> Gm;
     typedef Tiling<T> P;
@@ -452,7 +514,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) ssc_kernel(const SSCParam
     }
     C vm[XF::QL][XF::RL];
     XF::run(vin, vm, s, thi, tlo);
-    double acc = 0.0;
+    PartSum<T> acc;
 #pragma unroll
     for (int q = 0; q < XF::QL; ++q) {
         int j, g;
@@ -466,10 +528,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) ssc_kernel(const SSCParam
             C ph;
             if constexpr (FAST) ph = expi_turns_poly(th[r]);
             else ph = expi_turns<T>(phase_q64(signed_k(idx, p.N), p.flow));
-            if constexpr (MODE == SS_REV) {
-                const long long kk = signed_k(idx, p.N);
-                acc -= (double)(kk * kk) * (double)im_conj_mul(vm[q][r], p.xs[idx]);
-            }
+            if constexpr (MODE == SS_REV) acc.add(-ksq<T>(signed_k(idx, p.N)) * im_conj_mul(vm[q][r], p.xs[idx]));
             vm[q][r] = cscale(cmul(vm[q][r], ph), (T)p.pre);
             if constexpr (MODE == SS_STORE) p.xs[idx] = vm[q][r];
         }
@@ -490,13 +549,13 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, 1) ssc_kernel(const SSCParam
         }
     }
     if constexpr (MODE == SS_REV) {
-        const double tot = block_sum<NT>(acc, red);
+        const double tot = block_sum<NT>(acc.value(), red);
         if (tid == 0) p.part[blockIdx.x] = tot * p.wscale;
     }
 }
 
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) ssr_kernel(const SSRParams<T> p) {
+__global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MPA_ADJ_MINB_R : 1) ssr_kernel(const SSRParams<T> p) {
     typedef cx<T> C;
     typedef KRGeom<T, L> Gm;
     typedef Tiling<T, 1> P;
@@ -534,7 +593,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) ssr_kernel(const SSRParam
     }
     C vm[XI::QL][XI::RL];
     XI::run(vin, vm, s, thi, tlo);
-    double acc = 0.0;
+    PartSum<T> acc;
 #pragma unroll
     for (int q = 0; q < XI::QL; ++q) {
         int j, g;
@@ -561,7 +620,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) ssr_kernel(const SSRParam
                 const C e = mkc(cs, sn);
                 const C y = cmul(t, e);
                 const T c = -im_conj_mul(gy, y);
-                acc += (double)(c * pw);
+                acc.add(c * pw);
                 const C a = cmul(gy, cconj(e));
                 const T f = T(2) * c * p.rot;
                 vm[q][r] = mkc(a.x + f * t.x, a.y + f * t.y);
@@ -584,7 +643,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, 1) ssr_kernel(const SSRParam
         }
     }
     if constexpr (MODE == SS_REV) {
-        const double tot = block_sum<NT>(acc, red);
+        const double tot = block_sum<NT>(acc.value(), red);
         if (tid == 0) p.part[blockIdx.x] = tot * p.scale;
     }
 }
