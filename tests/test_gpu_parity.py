@@ -202,14 +202,16 @@ def test_small_workload_fp32(M):
 
 def test_bench_workload_sampled_interval_fp32(M):
     """The N = 2^20, 16-channel workload in the benchmark's launch
-    configuration (L = 5 km, M = 142, n = 3): one full interval against the
-    oracle, starting from the seeded field's spectrum at z = 45 km."""
+    configuration (L = 5 km, M = 142, the workload's n_tot): one full
+    interval against the oracle, starting from the seeded field's spectrum at
+    z = 45 km."""
     w = workload("1")
     A0 = w.field()
     psi0 = oracle.fft(A0, +1)
     z0 = 45.0
     ref = oracle.mpa_interval(psi0, w.fiber, w.T_ps, z0, w.mpa_L_km, w.mpa_M, w.mpa_n_iter)
     plan = M.Plan(w.fiber, w.N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32")
+    plan.autotune()  # the split the benchmark times
     got = host(plan.interval(dev(psi0, "fp64"), z0))
     assert oracle.rel_l2(got, ref) < TOL["fp32"]
 
@@ -223,12 +225,45 @@ def test_largest_workload_sampled_interval_and_split_step(M):
     psi0 = oracle.fft(A0, +1)
     ref = oracle.mpa_interval(psi0, w.fiber, w.T_ps, 0.0, 0.5, 4, 2)
     plan = M.Plan(w.fiber, w.N, w.T_ps, 0.5, 4, 2, precision="fp32")
+    plan.autotune()
     got = host(plan.interval(dev(psi0, "fp64"), 0.0))
     assert oracle.rel_l2(got, ref) < TOL["fp32"]
     del plan
     ref_ss = oracle.ss(A0, w.fiber, w.T_ps, 0.0, 0.1, 0.05)
     got_ss = host(M.ss_propagate(dev(A0, "fp64"), w.fiber, w.T_ps, 0.05, 0.0, 0.1))
     assert oracle.rel_l2(got_ss, ref_ss) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_empty_propagation_is_the_transform_round_trip(M, prec):
+    """z_to = z_from: no interval runs, the field goes through F and F^-1 only."""
+    fib = small_map()
+    N, T = 1 << 12, 3200.0
+    A0 = wdm_field(N, T, 3, 50.0, 32, 30.0, 10.0, "qpsk", seed=3)
+    ref = oracle.mpa(A0, fib, T, 10.0, 10.0, 2.0, 24, 3)
+    plan = M.Plan(fib, N, T, 2.0, 24, 3, precision=prec)
+    got = host(plan.propagate(dev(A0, prec), 10.0, 10.0))
+    assert oracle.rel_l2(got, ref) < (1e-14 if prec == "fp64" else 1e-6)
+    assert oracle.rel_l2(ref, A0) < 1e-14
+
+
+def test_maximum_sizes(M):
+    """The largest transforms the passes support: N = 2^25 in FP32 (column
+    pass 2^11 x row pass 2^14) and N = 2^24 in FP64 (2^11 x 2^13), one short
+    interval each (M = 2) against the oracle."""
+    from paper_1101_0086_gb300.workloads import dm_map
+    fib = dm_map(1, beta3=0.08)
+    for prec, logn in (("fp32", 25), ("fp64", 24)):
+        N = 1 << logn
+        T = 100.0 * N / 8192
+        A0 = random_field(N, seed=logn, scale=0.03)  # about 2 mW per sample, every frequency occupied
+        psi0 = oracle.fft(A0, +1)
+        ref = oracle.mpa_interval(psi0, fib, T, 0.0, 0.5, 2, 2)
+        plan = M.Plan(fib, N, T, 0.5, 2, 2, precision=prec)
+        got = host(plan.interval(dev(psi0, "fp64"), 0.0))
+        assert oracle.rel_l2(got, ref) < TOL[prec], (prec, logn)
+        assert oracle.rel_l2(got - psi0, ref - psi0) < (1e-9 if prec == "fp64" else 3e-3)
+        del plan, got
 
 
 # ------------------------------------------------------ batched links
