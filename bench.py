@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, split-step and CPU legs (profiling runs)")
     ap.add_argument("--schedule", default="auto", choices=["auto", "level", "wavefront"])
+    ap.add_argument("--grad-methods", default="mpa_fp32,ss_fp32,ss_fp64",
+                    help="workload 4: methods to time (ss_fp64 only for --km <= 100)")
     ap.add_argument("--log2-n2", type=int, default=0,
                     help="four-step column length 2^l (default: mpa_plan_autotune chooses, before the timed region)")
     return ap.parse_args()
@@ -521,7 +523,11 @@ def run_grad(args, world, rank, local):
         return loss, g_out, (2.0 / N) * r
 
     res = {}
-    methods = [("mpa", "fp32"), ("ss", "fp32")] + ([("ss", "fp64")] if km <= 100.0 else [])
+    want = set(args.grad_methods.split(","))
+    methods = [m for m in (("mpa", "fp32"), ("ss", "fp32"), ("ss", "fp64"))
+               if f"{m[0]}_{m[1]}" in want and (m != ("ss", "fp64") or km <= 100.0)]
+    if n_spans < 1 or abs(n_spans * fib.period_km - km) > 1e-9:
+        raise SystemExit("--workload 4: --km must be a whole number of spans")
     for meth, prec in methods:
         dt = torch.complex64 if prec == "fp32" else torch.complex128
         a = torch.from_numpy(A0).to(dt).cuda()
@@ -580,7 +586,7 @@ def run_grad(args, world, rank, local):
                                  "grad_sigma_first": [float(x) for x in gs[:2]],
                                  "grad_beta2_first": [float(x) for x in gb[:2]], "kernels": kern}
     line = {"metric": "gradient evaluations in mode*km/s (forward with checkpoints + loss + reverse pass)",
-            "value": res["mpa_fp32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "value": res[next(iter(res))]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w.name, "N": N, "km": km, "n_segments": 2 * n_spans,
