@@ -59,7 +59,7 @@ template <typename T> struct KCAParams {
 };
 
 template <typename T> struct KRAParams {
-    const cx<T>* a;  // rows after the inverse column pass of P (KC MPA_PRE)
+    cx<T>* a;        // rows after the inverse column pass of P (KC MPA_PRE); receives A(t)
     cx<T>* g;        // rows after KCA_G; overwritten with the forward row pass of g_A
     long long nrows;
     long long N;
@@ -248,9 +248,12 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
     __syncthreads();
 
     // A(t) and the unnormalised inverse of q, on the same element layout
-    C va[XI::QL][XI::RL], vg[XI::QL][XI::RL];
+    // A(t) goes back to its own rows of p.a (each thread rereads exactly the
+    // elements it wrote, right after the second transform, mostly from L2):
+    // holding both transforms' results in registers would spill
+    C vg[XI::QL][XI::RL];
     {
-        C vin[XI::Q0][XI::R0];
+        C vin[XI::Q0][XI::R0], va[XI::QL][XI::RL];
 #pragma unroll
         for (int q = 0; q < XI::Q0; ++q) {
             int j, g;
@@ -260,6 +263,14 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
             for (int r = 0; r < XI::R0; ++r) vin[q][r] = src[j + r * (L / XI::R0)];
         }
         XI::run(vin, va, s, thi, tlo);
+#pragma unroll
+        for (int q = 0; q < XI::QL; ++q) {
+            int j, g;
+            bmap<LAYOUT_ROW, L, G, XI::RL>(tid + q * NT, j, g);
+            C* dst = p.a + (row0 + g) * L;
+#pragma unroll
+            for (int r = 0; r < XI::RL; ++r) dst[j + r * (L / XI::RL)] = cscale(va[q][r], p.inv_n);
+        }
     }
     {
         C vin[XI::Q0][XI::R0];
@@ -276,9 +287,12 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
     PartSum<T> acc;
 #pragma unroll
     for (int q = 0; q < XI::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XI::RL>(tid + q * NT, j, g);
+        const C* at = p.a + (row0 + g) * L;
 #pragma unroll
         for (int r = 0; r < XI::RL; ++r) {
-            const C a = cscale(va[q][r], p.inv_n);
+            const C a = at[j + r * (L / XI::RL)];
             const C gu = vg[q][r];
             const T pw = a.x * a.x + a.y * a.y;
             acc.add(pw * (gu.x * a.x + gu.y * a.y));  // Re(conj(g_U') U)
