@@ -194,13 +194,16 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         const long long c = (col0 + g) & N1m;
         unsigned long long th[XA::RL];
         if constexpr (FAST && !INV) phase_run<XA::RL>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::RL), nc, th);
+        constexpr bool HOIST = (L / XA::RL) % Gm::OLO == 0;  // one low-table lookup per butterfly
+        C wlo = mkc(T(1), T(0));
+        if constexpr (INV && HOIST) wlo = olo[(j & (Gm::OLO - 1)) * G + g];
 #pragma unroll
         for (int r = 0; r < XA::RL; ++r) {
             const int row = j + r * (L / XA::RL);
             const long long idx = c + (long long)row * p.N1;
             C v = vout[q][r];
             if constexpr (INV) {
-                C w = olo[(row & (Gm::OLO - 1)) * G + g];
+                C w = HOIST ? wlo : olo[(row & (Gm::OLO - 1)) * G + g];
                 if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
                 v = cmul(v, w);
             } else {
@@ -308,10 +311,12 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
         int j, g;
         bmap<LAYOUT_ROW, L, G, XF::RL>(tid + q * NT, j, g);
         C* dst = p.g + (row0 + g) * L;
+        constexpr bool HOIST = (L / XF::RL) % Gm::OLO == 0;
+        const C wlo = HOIST ? olo[g * Gm::OLO + (j & (Gm::OLO - 1))] : mkc(T(1), T(0));
 #pragma unroll
         for (int r = 0; r < XF::RL; ++r) {
             const int l = j + r * (L / XF::RL);
-            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+            C w = HOIST ? wlo : olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
             if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
             dst[l] = cmul(vout[q][r], w);
         }
@@ -554,10 +559,12 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         int j, g;
         bmap<LAYOUT_COL, L, G, XI::RL>(tid + q * NT, j, g);
         const long long c = (col0 + g) & N1m;
+        constexpr bool HOIST = (L / XI::RL) % Gm::OLO == 0;
+        const C wlo = HOIST ? olo[(j & (Gm::OLO - 1)) * G + g] : mkc(T(1), T(0));
 #pragma unroll
         for (int r = 0; r < XI::RL; ++r) {
             const int row = j + r * (L / XI::RL);
-            C w = olo[(row & (Gm::OLO - 1)) * G + g];
+            C w = HOIST ? wlo : olo[(row & (Gm::OLO - 1)) * G + g];
             if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
             p.data[c + (long long)row * p.N1] = cmul(vout[q][r], w);
         }
@@ -648,10 +655,12 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
         int j, g;
         bmap<LAYOUT_ROW, L, G, XF::RL>(tid + q * NT, j, g);
         C* dst = p.data + (row0 + g) * L;
+        constexpr bool HOIST = (L / XF::RL) % Gm::OLO == 0;
+        const C wlo = HOIST ? olo[g * Gm::OLO + (j & (Gm::OLO - 1))] : mkc(T(1), T(0));
 #pragma unroll
         for (int r = 0; r < XF::RL; ++r) {
             const int l = j + r * (L / XF::RL);
-            C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+            C w = HOIST ? wlo : olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
             if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
             dst[l] = cmul(vout[q][r], w);
         }

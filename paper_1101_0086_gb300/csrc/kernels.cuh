@@ -264,13 +264,18 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         unsigned long long th[RO];
         if constexpr (FAST && MODE == KC_MPA_POST)
             phase_run<RO>(c + (long long)j * p.N1, (long long)p.N1 * (L / RO), nc, th);
+        // rows j + r L/RO share their low outer-factor index when L/RO is a
+        // multiple of the low table's length: one lookup per butterfly
+        constexpr bool HOIST = (L / RO) % Gm::OLO == 0;
+        C wlo = mkc(T(1), T(0));
+        if constexpr (INV && HOIST) wlo = olo[(j & (Gm::OLO - 1)) * G + g];
 #pragma unroll
         for (int r = 0; r < RO; ++r) {
             const int row = j + r * (L / RO);
             C v = vout[q][r];
             if constexpr (INV) {
                 // four-step factor W_N^{-n2 k1}, n2 = row
-                C w = olo[(row & (Gm::OLO - 1)) * G + g];
+                C w = HOIST ? wlo : olo[(row & (Gm::OLO - 1)) * G + g];
                 if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
                 v = cmul(v, w);
             }
@@ -380,12 +385,15 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
         bmap<LAYOUT_ROW, L, G, RO>(tid + q * NT, j, g);
         if (row0 + g >= p.nrows) continue;
         C* dst = p.data + (row0 + g) * L;
+        constexpr bool HOIST = (L / RO) % Gm::OLO == 0;  // one low-table lookup per butterfly
+        C wlo = mkc(T(1), T(0));
+        if constexpr (FWD && HOIST) wlo = olo[g * Gm::OLO + (j & (Gm::OLO - 1))];
 #pragma unroll
         for (int r = 0; r < RO; ++r) {
             const int l = j + r * (L / RO);  // k1
             C v = vout[q][r];
             if constexpr (FWD) {
-                C w = olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
+                C w = HOIST ? wlo : olo[g * Gm::OLO + (l & (Gm::OLO - 1))];
                 if constexpr (Gm::OHI > 1) w = cmul(ohi[g * Gm::OHI + (l >> Gm::OSH)], w);
                 v = cmul(v, w);
             } else {
