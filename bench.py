@@ -523,6 +523,7 @@ def run_grad(args, world, rank, local):
         return loss, g_out, (2.0 / N) * r
 
     res = {}
+    head = {}  # clocks, roofline and launches of the first (headline) method
     want = set(args.grad_methods.split(","))
     methods = [m for m in (("mpa", "fp32"), ("ss", "fp32"), ("ss", "fp64"))
                if f"{m[0]}_{m[1]}" in want and (m != ("ss", "fp64") or km <= 100.0)]
@@ -551,9 +552,12 @@ def run_grad(args, world, rank, local):
             return loss, gi - direct, gs, gb, out, g_out
 
         reps = args.steps if meth == "mpa" else 1
-        for _ in range(1 if meth == "mpa" else 0):
+        for _ in range(args.warmup if meth == "mpa" else 1):
             step()
         torch.cuda.synchronize()
+        clocks = Clocks(torch.cuda.current_device()) if meth == "mpa" else None
+        if clocks:
+            clocks.start()
         l0 = mpa.kernel_launches()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
@@ -561,6 +565,9 @@ def run_grad(args, world, rank, local):
             loss, gi, gs, gb, out, g_out = step()
         e.record(stream)
         torch.cuda.synchronize()
+        launches = mpa.kernel_launches() - l0
+        if clocks:
+            head["clocks"] = clocks.stop()
         t = s.elapsed_time(e) / 1e3 / reps
         kern = None
         if meth == "mpa":
@@ -573,6 +580,14 @@ def run_grad(args, world, rank, local):
             tot = sum(v[0] for v in prof.values())
             kern = {k: {"ms": round(v[0], 2), "launches": v[1], "share": round(v[0] / tot, 4),
                         "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1)} for k, v in prof.items() if v[1] > 0}
+            peak, peak_src = peaks()
+            dom_name, (dom_ms, dom_n, dom_bytes) = max(prof.items(), key=lambda kv: kv[1][0])
+            achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+            head["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom_name,
+                                "algorithmic_bytes_per_launch": dom_bytes / dom_n, "peak_source": peak_src}
+            head["ms_per_step"] = t * 1e3
+            head["gpu_launches"] = launches
         # scaling identity of the cubic term (exact for both discrete methods):
         # sum sigma dl/dsigma - Re<g_A, A>/2 = -Re<g_out, out>/2, with the
         # direct dependence of l on A_in taken out of g_A
@@ -582,16 +597,17 @@ def run_grad(args, world, rank, local):
         rhs = -0.5 * float(torch.real(torch.vdot(g_out.to(torch.complex128), out.to(torch.complex128))))
         res[f"{meth}_{prec}"] = {"value": N * km / t, "unit": UNIT, "s_per_gradient": t, "loss": float(loss),
                                  "scaling_identity_residual": abs(lhs - rhs) / max(abs(rhs), 1e-300),
-                                 "launches_per_gradient": (mpa.kernel_launches() - l0) / reps,
+                                 "launches_per_gradient": launches / reps,
                                  "grad_sigma_first": [float(x) for x in gs[:2]],
                                  "grad_beta2_first": [float(x) for x in gb[:2]], "kernels": kern}
     line = {"metric": "gradient evaluations in mode*km/s (forward with checkpoints + loss + reverse pass)",
             "value": res[next(iter(res))]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "N": N, "km": km, "n_segments": 2 * n_spans,
-                       "loss": "mean |D^-1 A_out - A_in|^2, D = exact linear flow"},
-            "methods": res}
+                       "loss": "mean |D^-1 A_out - A_in|^2, D = exact linear flow",
+                       "l2": "inputs larger than L2 (each gradient moves tens of GB)"},
+            **head, "methods": res}
     print(json.dumps(line), flush=True)
     return 0
 

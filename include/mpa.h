@@ -170,8 +170,9 @@ MPA_API void mpa_plan_destroy(mpa_plan* plan);
  * the phases beta(w, z_j) and sigma(z_j) of Eq. (6) and step 7).
  *
  * Memory: a checkpoint of A_hat (complex128) at every interval start, then,
- * for one interval at a time, the node spectra of every level (2 n_iter
- * buffers of (M+1) N samples) and two more node buffers.  Level-schedule
+ * for one interval at a time, psi^{(n)}, A^{(n)}(t) and V^{(n)} of every
+ * level and the running gradient (3 n_iter buffers of (M+1) N samples in
+ * all) and a few buffers of N samples.  Level-schedule
  * plans only (MPA_SCHEDULE_WAVEFRONT plans are rejected with
  * MPA_ERR_INVALID_ARG), and N >= 2^13 (MPA_ERR_UNSUPPORTED_N).
  * The workspace is caller-owned device memory, 256-byte aligned. */

@@ -59,6 +59,51 @@ cudaError_t kra_one(const KRAParams<T>& p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The forward row pass of the recompute, keeping A(t) (KR_MPA_KEEP).
+template <typename T, int L>
+cudaError_t krk_one(const KRParams<T>& p, cudaStream_t st) {
+    typedef KRGeom<T, L> Gm;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kr_kernel<T, L, KR_MPA_KEEP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::smem_bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kr_kernel<T, L, KR_MPA_KEEP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (!p.keep) return cudaErrorInvalidValue;
+    const long long nblk = (p.nrows + Gm::G - 1) / Gm::G;
+    if (nblk <= 0) return cudaSuccess;
+    const bool prof = g_prof_on.load(std::memory_order_relaxed);
+    if (prof) prof_begin(st);
+    kr_kernel<T, L, KR_MPA_KEEP><<<(unsigned)nblk, Gm::NT, Gm::smem_bytes, st>>>(p);
+    // rows read and written, A(t) written
+    if (prof) prof_end(PK_KR_MPA, st, 3.0 * (double)p.nrows * L * sizeof(cx<T>));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t krk_any(int logL, const KRParams<T>& p, cudaStream_t st) {
+    switch (logL) {
+        case 4: return krk_one<T, 16>(p, st);
+        case 5: return krk_one<T, 32>(p, st);
+        case 6: return krk_one<T, 64>(p, st);
+        case 7: return krk_one<T, 128>(p, st);
+        case 8: return krk_one<T, 256>(p, st);
+        case 9: return krk_one<T, 512>(p, st);
+        case 10: return krk_one<T, 1024>(p, st);
+        case 11: return krk_one<T, 2048>(p, st);
+        case 12: return krk_one<T, 4096>(p, st);
+        case 13: return krk_one<T, 8192>(p, st);
+        case 14:
+            if constexpr (sizeof(T) == 4) return krk_one<T, 16384>(p, st);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, int L, int MODE>
 cudaError_t ssc_one(const SSCParams<T>& p, cudaStream_t st) {
     typedef KCGeom<T, L> Gm;
@@ -253,6 +298,9 @@ cudaError_t scale_to_state_any(const cx<T>* in, double2* state, double scale, lo
     }                                                                                                          \
     template <> cudaError_t kra_launch<T>(int logL, const KRAParams<T>& p, cudaStream_t st) {                  \
         return adj::kra_any<T>(logL, p, st);                                                                   \
+    }                                                                                                          \
+    template <> cudaError_t kr_keep_launch<T>(int logL, const KRParams<T>& p, cudaStream_t st) {               \
+        return adj::krk_any<T>(logL, p, st);                                                                   \
     }                                                                                                          \
     template <> cudaError_t rscan_launch<T>(const RScanParams<T>& p, cudaStream_t st) {                        \
         return adj::rscan_any<T>(p, st);                                                                       \

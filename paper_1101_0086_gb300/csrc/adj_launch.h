@@ -8,6 +8,8 @@ namespace mpa {
 
 template <typename T> cudaError_t kca_launch(int mode, int logL, const KCAParams<T>& p, cudaStream_t st);
 template <typename T> cudaError_t kra_launch(int logL, const KRAParams<T>& p, cudaStream_t st);
+// The forward row pass (KR_MPA) that also writes A(t) to p.keep.
+template <typename T> cudaError_t kr_keep_launch(int logL, const KRParams<T>& p, cudaStream_t st);
 template <typename T> cudaError_t rscan_launch(const RScanParams<T>& p, cudaStream_t st);
 template <typename T>
 cudaError_t scan_store_launch(const cx<T>* v, cx<T>* psi, const cx<T>* psi0c, long long N, int M, cudaStream_t st);

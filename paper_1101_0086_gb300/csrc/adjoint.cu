@@ -4,11 +4,11 @@
 // Schedule: a forward pass stores A_hat at every interval start (FP64
 // checkpoints).  The intervals are then walked backwards.  For each one the
 // levels of MPA steps 2-5 are recomputed from its checkpoint with every
-// level kept (psi^{(n)} and V^{(n)} at all nodes), and the levels are
-// reversed one by one (adjoint.cuh): reverse scan, the two column passes and
-// the row pass of the node transforms, and the recomputed inverse column
-// pass of A_j.  Per-node partial sums of the parameter gradients go to a
-// small device table that the host folds into the segments at the end.
+// level kept (psi^{(n)}, A^{(n)}(t) and V^{(n)} at all nodes), and the
+// levels are reversed one by one (adjoint.cuh): reverse scan, then the two
+// column passes and the row pass of the node transforms.  Per-node partial
+// sums of the parameter gradients go to a small device table that the host
+// folds into the segments at the end.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -27,7 +27,7 @@ struct AdjLayout {
     double z_from = 0.0;
     int acc_stride = 0;   // per interval: M+1 beta2 sums, M+1 sigma sums, the step-7 beta2 sum
     long long tiles = 0;  // largest number of partial sums of one launch
-    size_t off_ck = 0, off_psi = 0, off_v = 0, off_g = 0, off_gx = 0, off_gs = 0, off_p0 = 0, off_part = 0,
+    size_t off_ck = 0, off_psi = 0, off_a = 0, off_v = 0, off_g = 0, off_gx = 0, off_gs = 0, off_p0 = 0, off_part = 0,
            off_acc = 0, off_adjc = 0, need = 0;
     std::vector<int> types;
     std::vector<long> amps;
@@ -69,7 +69,8 @@ int adj_layout(const mpa_plan* p, double z_from, double z_to, AdjLayout* a) {
     a->acc_stride = 2 * (int)nodes + 1;
     a->off_ck = 0;
     a->off_psi = align256(a->off_ck + (size_t)(a->n_int + 1) * N * sizeof(double2));
-    a->off_v = align256(a->off_psi + (S - 1) * nodes * N * cs);
+    a->off_a = align256(a->off_psi + (S - 1) * nodes * N * cs);
+    a->off_v = align256(a->off_a + S * nodes * N * cs);
     a->off_g = align256(a->off_v + S * nodes * N * cs);
     a->off_gx = align256(a->off_g + nodes * N * cs);
     a->off_gs = align256(a->off_gx + N * sizeof(double2));
@@ -175,6 +176,7 @@ int adjoint_t(mpa_plan* p, const void* field_in, const void* grad_out, void* gra
     const size_t NM = (size_t)nodes * (size_t)N;
     double2* ck = reinterpret_cast<double2*>(ws + a.off_ck);
     C* psi_lv = reinterpret_cast<C*>(ws + a.off_psi);  // psi^{(n)}, n = 1..S-1
+    C* a_lv = reinterpret_cast<C*>(ws + a.off_a);      // A^{(n)}(t), n = 0..S-1 (row pass layout)
     C* v_lv = reinterpret_cast<C*>(ws + a.off_v);      // V^{(n)}, n = 0..S-1
     C* G = reinterpret_cast<C*>(ws + a.off_g);
     double2* gx = reinterpret_cast<double2*>(ws + a.off_gx);
@@ -251,7 +253,8 @@ int adjoint_t(mpa_plan* p, const void* field_in, const void* grad_out, void* gra
         for (int n = 0; n < S; ++n) {
             MPA_TRY(kc_pre(n, t));
             KRParams<T> r{W, (long long)nodes * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
-            MPA_TRY(kr_launch<T>(KR_MPA, s.logN1, r, st));
+            r.keep = a_lv + (size_t)n * NM;
+            MPA_TRY(kr_keep_launch<T>(s.logN1, r, st));
             KCParams<T> c{};
             c.src = W;
             c.src_stride = N;
@@ -290,15 +293,13 @@ int adjoint_t(mpa_plan* p, const void* field_in, const void* grad_out, void* gra
                 MPA_TRY(rscan_launch<T>(rs, st));
             }
             MPA_TRY(kca(KCA_G, n, t, accq));
-            MPA_TRY(kc_pre(n, t));
             KRAParams<T> r{};
-            r.a = W;
+            r.a = a_lv + (size_t)n * NM;
             r.g = G;
             r.nrows = (long long)nodes * s.N2;
             r.N = N;
             r.logN = s.logN;
             r.N2 = (int)s.N2;
-            r.inv_n = (T)(1.0 / (double)N);
             r.adj = adjc + (size_t)t * nodes;
             r.part = part;
             MPA_TRY(kra_launch<T>(s.logN1, r, st));

@@ -6,9 +6,9 @@
 // A = F^-1[P], U = |A|^2 A, V_j = sigma_j dz F[U] e^{-i beta_j} / pre_j):
 //   KCA_G (column pass)  g_V_j  -> q = e^{+i beta_j} (dz / pre_j) g_V_j -> inverse column DFT
 //                        and the beta2 term sum_k (w_k^2/2) Im(conj(g_V) V)
-//   KC_MPA_PRE           psi_j  -> the inverse column DFT of P (as in the forward pass)
-//   KRA (row pass)       inverse row DFTs of both: A = (.)/N, g_U' = unnormalised (the
-//                        gradient of U over sigma_j, F^H = N F^-1);
+//   KRA (row pass)       A(t), kept by the forward recompute (KR_MPA_KEEP); the inverse
+//                        row DFT of g: g_U' = unnormalised (the gradient of U over
+//                        sigma_j, F^H = N F^-1);
 //                        g_A = sigma_j (2 |A|^2 g_U' + A^2 conj(g_U')) -> forward row DFT,
 //                        and the sigma term Re sum_n conj(g_U') U
 //   KCA_P (column pass)  forward column DFT -> g_psi_j = e^{-i beta_j} (pre_j / N) F[g_A]
@@ -59,13 +59,12 @@ template <typename T> struct KCAParams {
 };
 
 template <typename T> struct KRAParams {
-    cx<T>* a;        // rows after the inverse column pass of P (KC MPA_PRE); receives A(t)
+    const cx<T>* a;  // A(t) of the level's nodes, rows as the forward row pass kept them
     cx<T>* g;        // rows after KCA_G; overwritten with the forward row pass of g_A
     long long nrows;
     long long N;
     int logN;
     int N2;
-    T inv_n;
     const AdjC* adj;
     double* part;
 };
@@ -250,31 +249,9 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
     }
     __syncthreads();
 
-    // A(t) and the unnormalised inverse of q, on the same element layout
-    // A(t) goes back to its own rows of p.a (each thread rereads exactly the
-    // elements it wrote, right after the second transform, mostly from L2):
-    // holding both transforms' results in registers would spill
+    // the unnormalised inverse of q, on the element layout in which the
+    // forward row pass kept A(t)
     C vg[XI::QL][XI::RL];
-    {
-        C vin[XI::Q0][XI::R0], va[XI::QL][XI::RL];
-#pragma unroll
-        for (int q = 0; q < XI::Q0; ++q) {
-            int j, g;
-            bmap<LAYOUT_ROW, L, G, XI::R0>(tid + q * NT, j, g);
-            const C* src = p.a + (row0 + g) * L;
-#pragma unroll
-            for (int r = 0; r < XI::R0; ++r) vin[q][r] = src[j + r * (L / XI::R0)];
-        }
-        XI::run(vin, va, s, thi, tlo);
-#pragma unroll
-        for (int q = 0; q < XI::QL; ++q) {
-            int j, g;
-            bmap<LAYOUT_ROW, L, G, XI::RL>(tid + q * NT, j, g);
-            C* dst = p.a + (row0 + g) * L;
-#pragma unroll
-            for (int r = 0; r < XI::RL; ++r) dst[j + r * (L / XI::RL)] = cscale(va[q][r], p.inv_n);
-        }
-    }
     {
         C vin[XI::Q0][XI::R0];
 #pragma unroll

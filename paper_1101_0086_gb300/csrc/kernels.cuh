@@ -29,7 +29,9 @@
 namespace mpa {
 
 enum { KC_MPA_PRE = 0, KC_MPA_POST = 1, KC_SS_STEP = 2, KC_FWD = 3, KC_INV = 4 };
-enum { KR_MPA = 0, KR_SS = 1, KR_FWD = 2, KR_INV = 3 };
+// KR_MPA_KEEP: KR_MPA that also writes A(t) to keep (the reverse mode's
+// forward recompute keeps it for the adjoint of the Kerr term)
+enum { KR_MPA = 0, KR_SS = 1, KR_FWD = 2, KR_INV = 3, KR_MPA_KEEP = 4 };
 
 // A launch covers nl links x npl nodes each (node index within the launch
 // n = l npl + jn); a single link is nl = 1.
@@ -60,6 +62,7 @@ template <typename T> struct KRParams {
     int N2;
     T inv_n;  // 1/N
     T rot;    // SS: int sigma over the step
+    cx<T>* keep;  // KR_MPA_KEEP: receives A(t), rows laid out as data
 };
 
 // Column pass geometry for column length L: G columns per tile, NT threads.
@@ -357,11 +360,21 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
         XI::run(vin, vm, s, thi, tlo);
 #pragma unroll
         for (int q = 0; q < XI::QL; ++q) {
+            C* kp = nullptr;
+            int jk = 0;
+            if constexpr (MODE == KR_MPA_KEEP) {
+                int g;
+                bmap<LAYOUT_ROW, L, G, XI::RL>(tid + q * NT, jk, g);
+                if (row0 + g < p.nrows) kp = p.keep + (row0 + g) * L;
+            }
 #pragma unroll
             for (int r = 0; r < XI::RL; ++r) {
                 C a = cscale(vm[q][r], p.inv_n);  // A(t) (MPA step 3 / SS inverse)
+                if constexpr (MODE == KR_MPA_KEEP) {
+                    if (kp) kp[jk + r * (L / XI::RL)] = a;
+                }
                 const T pw = a.x * a.x + a.y * a.y;
-                if constexpr (MODE == KR_MPA) {
+                if constexpr (MODE == KR_MPA || MODE == KR_MPA_KEEP) {
                     a = cscale(a, pw);  // |A|^2 A (MPA step 4)
                 } else {
                     T sn, cs;  // A exp(i s |A|^2), the nonlinear step of Eq. (4)
