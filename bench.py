@@ -135,19 +135,36 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str, split: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel sources with the same four-step split."""
+def ncu_record(kernel: str, workload: str, split: str) -> dict:
+    """The committed ncu counters of `kernel` (profiles/traffic.json), if
+    they were taken on the current kernel sources with the same four-step
+    split; else {}."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
     except (OSError, ValueError):
-        return None
+        return {}
     e = d.get(kernel)
     if not e or e.get("source_hash") != source_hash() or e.get("workload") != workload or e.get("split") != split:
-        return None
-    return e.get("dram_bytes_per_launch")
+        return {}
+    return e
+
+
+def ncu_traffic(kernel: str, workload: str, split: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None."""
+    return ncu_record(kernel, workload, split).get("dram_bytes_per_launch")
+
+
+def issue_roofline(warp_inst: float, launch_s: float, sm_mhz: float, n_sm: int = 152) -> dict:
+    """Instruction-issue view of a kernel: its warp instructions per launch
+    (ncu) over its live launch time, against the issue limit of the GPU (each
+    SM's four schedulers issue one warp instruction per cycle) at the SM
+    clock sampled during the timed region."""
+    peak = n_sm * 4 * sm_mhz * 1e6 / 1e9
+    ach = warp_inst / launch_s / 1e9
+    return {"unit": "G warp-instructions/s", "warp_instructions_per_launch": warp_inst, "achieved": round(ach, 1),
+            "peak": round(peak, 1), "frac": round(ach / peak, 4), "sm_mhz": sm_mhz}
 
 
 def max_over_ranks(t: float, dist=None, device="cpu") -> float:
@@ -288,10 +305,12 @@ def run_mpa(args, world, rank, local):
     kern = {k: {"ms_total": round(v[0], 3), "launches": v[1], "share": round(v[0] / sum(x[0] for x in prof.values()), 4),
                 "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1)} for k, v in prof.items()}
     split = f"N1 x N2 = 2^{int(np.log2(N)) - log2_n2} x 2^{log2_n2}"
-    traffic = ncu_traffic(dom_name, w.name, split)
+    rec = ncu_record(dom_name, w.name, split)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom_name,
+                "frac": round(achieved / peak, 4), "traffic": rec.get("dram_bytes_per_launch"), "kernel": dom_name,
                 "algorithmic_bytes_per_launch": dom_bytes / dom_n, "peak_source": peak_src}
+    if rec.get("warp_instructions_per_launch") and ck.get("sm_mhz"):
+        roofline["issue"] = issue_roofline(rec["warp_instructions_per_launch"], dom_ms / 1e3 / dom_n, ck["sm_mhz"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,

@@ -53,3 +53,15 @@ def test_single_process_defaults():
     assert bench.dist_env() == (1, 0, 0)
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_value(1, 10.0, 2.0) == 5.0
+
+
+def test_roofline_helpers():
+    """The issue view: 152 SMs x 4 schedulers x 1 warp instruction per
+    cycle; the committed ncu record is used only on matching sources and
+    split."""
+    r = bench.issue_roofline(608e6, 1e-3, 2000.0)
+    assert r["peak"] == pytest.approx(152 * 4 * 2.0)
+    assert r["achieved"] == pytest.approx(608.0)
+    assert r["frac"] == pytest.approx(0.5)
+    assert bench.ncu_record("kr_mpa", "no such workload", "x") == {}
+    assert bench.ncu_traffic("no_such_kernel", "w", "s") is None
