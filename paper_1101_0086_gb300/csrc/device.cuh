@@ -339,6 +339,57 @@ template <int LAYOUT, int L, int G> __device__ __forceinline__ int eidx(int l, i
     return LAYOUT == LAYOUT_COL ? l * G + g : g * L + l;
 }
 
+// The padded slot phys(eidx(l, g)) for l = lb + c written as base(lb, g) +
+// off(c): with c a compile-time constant of an unrolled loop, off(c) folds
+// into the shared-memory instruction's immediate offset, so each element
+// costs no integer work.  The padding term i >> PSH is
+//   COL, G >= 2^PSH: l (G >> PSH) + (g >> PSH)        (no condition)
+//   COL, G <  2^PSH: l >> SH, SH = PSH - log2 G       (as g < G)
+//   ROW, L >= 2^PSH: g (L >> PSH) + (l >> PSH)        (SH = PSH)
+//   ROW, L <  2^PSH: g >> (PSH - log2 L)              (no condition)
+// and the split is exact when (lb + c) >> SH = (lb >> SH) + (c >> SH) for
+// every c the caller adds: `split` states that case (see SlotSplit).
+// Sites of the column layout that use the split form (bit 0: first-pass
+// scatter, 1: middle-pass reads, 2: middle-pass writes, 3: last-pass
+// gather); the row layout uses it wherever it is exact.  Measured on the
+// 2^20 link (split 2^12 x 2^8): the split row layout takes the row pass
+// from 3223 to 3316 GB/s; in the column layout it cuts instructions too,
+// but the forward column pass, whose last pass gathers 32 elements per
+// thread, fell from 3816 to 3417 GB/s, so the column layout keeps the
+// direct form (0).
+#ifndef MPA_SLOT_COL
+#define MPA_SLOT_COL 0
+#endif
+template <int LAYOUT, int SITE> __host__ __device__ constexpr bool slot_site_on() {
+    return LAYOUT != LAYOUT_COL || ((MPA_SLOT_COL >> SITE) & 1) != 0;
+}
+
+template <int LAYOUT, int L, int G, int PSH> struct Slot {
+    __host__ __device__ static constexpr int lg(int x) { return x <= 1 ? 0 : 1 + lg(x / 2); }
+    static constexpr int P2 = 1 << PSH;
+    static constexpr bool COL = LAYOUT == LAYOUT_COL;
+    // l enters through a shift by SH (else the split needs no condition)
+    static constexpr bool LDEP = COL ? (G < P2) : (L >= P2);
+    static constexpr int SH = COL ? (G < P2 ? PSH - lg(G) : 0) : (L >= P2 ? PSH : 0);
+    static __device__ __forceinline__ int base(int lb, int g) {
+        if constexpr (COL) {
+            if constexpr (G >= P2) return lb * (G + (G >> PSH)) + g + (g >> PSH);
+            else return lb * G + g + (lb >> SH);
+        } else {
+            if constexpr (L >= P2) return g * (L + (L >> PSH)) + lb + (lb >> PSH);
+            else return g * L + (g >> (PSH - lg(L))) + lb;
+        }
+    }
+    static __host__ __device__ constexpr int off(int c) {
+        return COL ? (G >= P2 ? c * (G + (G >> PSH)) : c * G + (c >> SH)) : (L >= P2 ? c + (c >> PSH) : c);
+    }
+    // lb + r STRIDE with 0 <= lb < STRIDE, r < R: the shift splits if STRIDE
+    // is a multiple of 2^SH or the whole range R STRIDE fits below 2^SH
+    template <int STRIDE, int R> __host__ __device__ static constexpr bool strided() {
+        return !LDEP || STRIDE % (1 << SH) == 0 || STRIDE * R <= (1 << SH);
+    }
+};
+
 // Two-level table of W_L^e = exp(2 pi i e/L): hi[e >> SH] * lo[e & (2^SH-1)].
 template <int L> struct TwDims {
     static constexpr int logL = (L >= 16384) ? 14 : (L >= 8192) ? 13 : (L >= 4096) ? 12 : (L >= 2048) ? 11
@@ -422,8 +473,15 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
         const int b = threadIdx.x + q * NT;
         const int j = LAYOUT == LAYOUT_COL ? b / G : b % (L / R);
         const int g = LAYOUT == LAYOUT_COL ? b % G : b / (L / R);
+        typedef Slot<LAYOUT, L, G, PSH> SL;
+        if constexpr (slot_site_on<LAYOUT, 1>() && SL::template strided<L / R, R>()) {
+            const C* sb = s + SL::base(j, g);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = s[phys<PSH>(eidx<LAYOUT, L, G>(j + r * (L / R), g))];
+            for (int r = 0; r < R; ++r) v[q][r] = sb[SL::off(r * (L / R))];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = s[phys<PSH>(eidx<LAYOUT, L, G>(j + r * (L / R), g))];
+        }
         if constexpr (NS > 1) twiddle_row<T, L, R, S>(v[q], (j & (NS - 1)) * (L / (NS * R)), hi, lo);
         Dft<R, S, C>::run(v[q]);
     }
@@ -435,8 +493,16 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
         const int g = LAYOUT == LAYOUT_COL ? b % G : b / (L / R);
         const int k = j & (NS - 1);
         const int dst = (j - k) * R + k;
+        typedef Slot<LAYOUT, L, G, PSH> SL;
+        // dst = m NS R + k (k < NS): the offsets r NS stay below NS R
+        if constexpr (slot_site_on<LAYOUT, 2>() && SL::template strided<NS, R>()) {
+            C* sb = s + SL::base(dst, g);
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(dst + r * NS, g))] = v[q][r];
+            for (int r = 0; r < R; ++r) sb[SL::off(r * NS)] = v[q][r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(dst + r * NS, g))] = v[q][r];
+        }
     }
     __syncthreads();
 }
@@ -510,8 +576,17 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
                 int j, g;
                 bmap<LAYOUT, L, G, R0>(threadIdx.x + q * NT, j, g);
                 Dft<R0, S, C>::run(vin[q]);
+                // j R0 + r, r < R0: the shift always splits (j R0 is a multiple
+                // of 2^SH, or R0 divides 2^SH and r < R0 adds no carry)
+                typedef Slot<LAYOUT, L, G, PSH> SL;
+                if constexpr (slot_site_on<LAYOUT, 0>()) {
+                    C* sb = s + SL::base(j * R0, g);
 #pragma unroll
-                for (int r = 0; r < R0; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(j * R0 + r, g))] = vin[q][r];
+                    for (int r = 0; r < R0; ++r) sb[SL::off(r)] = vin[q][r];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R0; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(j * R0 + r, g))] = vin[q][r];
+                }
             }
             __syncthreads();
             mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, 1, NP>(s, hi, lo);
@@ -520,8 +595,15 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
             for (int q = 0; q < QL; ++q) {
                 int j, g;
                 bmap<LAYOUT, L, G, RL>(threadIdx.x + q * NT, j, g);
+                typedef Slot<LAYOUT, L, G, PSH> SL;
+                if constexpr (slot_site_on<LAYOUT, 3>() && SL::template strided<L / RL, RL>()) {
+                    const C* sb = s + SL::base(j, g);
 #pragma unroll
-                for (int r = 0; r < RL; ++r) vout[q][r] = s[phys<PSH>(eidx<LAYOUT, L, G>(j + r * (L / RL), g))];
+                    for (int r = 0; r < RL; ++r) vout[q][r] = sb[SL::off(r * (L / RL))];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RL; ++r) vout[q][r] = s[phys<PSH>(eidx<LAYOUT, L, G>(j + r * (L / RL), g))];
+                }
                 twiddle_row<T, L, RL, S>(vout[q], j, hi, lo);
                 Dft<RL, S, C>::run(vout[q]);
             }
