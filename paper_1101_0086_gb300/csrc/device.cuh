@@ -328,14 +328,14 @@ template <typename T> __device__ __forceinline__ cx<T> expi_ratio(long long e, i
 // ------------------------------------------------- shared-memory Stockham
 // Padding of the shared-memory tile: one extra element per 2^PSH elements
 // keeps every pass free of bank conflicts (PSH = log2 of the largest radix).
-template <int PSH> __device__ __forceinline__ int phys(int i) { return i + (i >> PSH); }
+template <int PSH> __host__ __device__ __forceinline__ int phys(int i) { return i + (i >> PSH); }
 
 // Tile layouts of G independent transforms of length L:
 //   COL: element (l, g) at l*G + g  (a tile of G columns of an N2 x N1 matrix)
 //   ROW: element (l, g) at g*L + l  (G contiguous rows)
 enum { LAYOUT_COL = 0, LAYOUT_ROW = 1 };
 
-template <int LAYOUT, int L, int G> __device__ __forceinline__ int eidx(int l, int g) {
+template <int LAYOUT, int L, int G> __host__ __device__ __forceinline__ int eidx(int l, int g) {
     return LAYOUT == LAYOUT_COL ? l * G + g : g * L + l;
 }
 
@@ -371,7 +371,7 @@ template <int LAYOUT, int L, int G, int PSH> struct Slot {
     // l enters through a shift by SH (else the split needs no condition)
     static constexpr bool LDEP = COL ? (G < P2) : (L >= P2);
     static constexpr int SH = COL ? (G < P2 ? PSH - lg(G) : 0) : (L >= P2 ? PSH : 0);
-    static __device__ __forceinline__ int base(int lb, int g) {
+    static __host__ __device__ __forceinline__ int base(int lb, int g) {
         if constexpr (COL) {
             if constexpr (G >= P2) return lb * (G + (G >> PSH)) + g + (g >> PSH);
             else return lb * G + g + (lb >> SH);
