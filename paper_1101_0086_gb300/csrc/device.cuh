@@ -348,20 +348,21 @@ template <int LAYOUT, int L, int G> __host__ __device__ __forceinline__ int eidx
 //   ROW, L >= 2^PSH: g (L >> PSH) + (l >> PSH)        (SH = PSH)
 //   ROW, L <  2^PSH: g >> (PSH - log2 L)              (no condition)
 // and the split is exact when (lb + c) >> SH = (lb >> SH) + (c >> SH) for
-// every c the caller adds: `split` states that case (see SlotSplit).
-// Sites of the column layout that use the split form (bit 0: first-pass
-// scatter, 1: middle-pass reads, 2: middle-pass writes, 3: last-pass
-// gather); the row layout uses it wherever it is exact.  Measured on the
-// 2^20 link (split 2^12 x 2^8): the split row layout takes the row pass
-// from 3223 to 3316 GB/s; in the column layout it cuts instructions too,
-// but the forward column pass, whose last pass gathers 32 elements per
-// thread, fell from 3816 to 3417 GB/s, so the column layout keeps the
-// direct form (0).
+// every c the caller adds (strided() states the cases the passes use).
+// Sites of the column layout that use the split form: bits 0-3 for
+// transforms with the small radix last (SF false), bits 4-7 for those with
+// it first (bit 0: first-pass scatter, 1: middle-pass reads, 2: middle-pass
+// writes, 3: last-pass gather); the row layout uses it wherever it is
+// exact.  Measured on the 2^20 link (split 2^12 x 2^8): the split row
+// layout takes the row pass from 3223 to 3316 GB/s.  In the column layout
+// it cuts instructions in both directions, but the forward column pass
+// (radix 8 then 32, a 32-element gather per thread) fell from 3816 to
+// 3417 GB/s while the inverse one (32 then 8) rose from 2906 to 2992 GB/s.
 #ifndef MPA_SLOT_COL
-#define MPA_SLOT_COL 0
+#define MPA_SLOT_COL 0x0F
 #endif
-template <int LAYOUT, int SITE> __host__ __device__ constexpr bool slot_site_on() {
-    return LAYOUT != LAYOUT_COL || ((MPA_SLOT_COL >> SITE) & 1) != 0;
+template <int LAYOUT, bool SF, int SITE> __host__ __device__ constexpr bool slot_site_on() {
+    return LAYOUT != LAYOUT_COL || ((MPA_SLOT_COL >> (SITE + (SF ? 4 : 0))) & 1) != 0;
 }
 
 template <int LAYOUT, int L, int G, int PSH> struct Slot {
@@ -461,7 +462,7 @@ __device__ __forceinline__ void twiddle_row(cx<T>* v, int e1, const cx<T>* hi, c
 // read and write phases).  Butterfly j of transform g reads elements
 // j + r L/R, applies W_{NS R}^{S r (j mod NS)}, does the R-point DFT and
 // writes to (j - j mod NS) R + j mod NS + r NS.
-template <typename T, int L, int G, int NT, int R, int NS, int S, int LAYOUT, int PSH>
+template <typename T, int L, int G, int NT, int R, int NS, int S, int LAYOUT, int PSH, bool SF>
 __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
     typedef cx<T> C;
     constexpr int NB = (L / R) * G;
@@ -474,7 +475,7 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
         const int j = LAYOUT == LAYOUT_COL ? b / G : b % (L / R);
         const int g = LAYOUT == LAYOUT_COL ? b % G : b / (L / R);
         typedef Slot<LAYOUT, L, G, PSH> SL;
-        if constexpr (slot_site_on<LAYOUT, 1>() && SL::template strided<L / R, R>()) {
+        if constexpr (slot_site_on<LAYOUT, SF, 1>() && SL::template strided<L / R, R>()) {
             const C* sb = s + SL::base(j, g);
 #pragma unroll
             for (int r = 0; r < R; ++r) v[q][r] = sb[SL::off(r * (L / R))];
@@ -495,7 +496,7 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
         const int dst = (j - k) * R + k;
         typedef Slot<LAYOUT, L, G, PSH> SL;
         // dst = m NS R + k (k < NS): the offsets r NS stay below NS R
-        if constexpr (slot_site_on<LAYOUT, 2>() && SL::template strided<NS, R>()) {
+        if constexpr (slot_site_on<LAYOUT, SF, 2>() && SL::template strided<NS, R>()) {
             C* sb = s + SL::base(dst, g);
 #pragma unroll
             for (int r = 0; r < R; ++r) sb[SL::off(r * NS)] = v[q][r];
@@ -530,7 +531,7 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
 __device__ __forceinline__ void mid_passes(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
     if constexpr (P < NP - 1) {
         typedef Sched<L, RMAX> SC;
-        stockham_pass<T, L, G, NT, SC::template radix<SF>(P), SC::template ns<SF>(P), S, LAYOUT, PSH>(s, hi, lo);
+        stockham_pass<T, L, G, NT, SC::template radix<SF>(P), SC::template ns<SF>(P), S, LAYOUT, PSH, SF>(s, hi, lo);
         mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, P + 1, NP>(s, hi, lo);
     }
 }
@@ -579,7 +580,7 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
                 // j R0 + r, r < R0: the shift always splits (j R0 is a multiple
                 // of 2^SH, or R0 divides 2^SH and r < R0 adds no carry)
                 typedef Slot<LAYOUT, L, G, PSH> SL;
-                if constexpr (slot_site_on<LAYOUT, 0>()) {
+                if constexpr (slot_site_on<LAYOUT, SF, 0>()) {
                     C* sb = s + SL::base(j * R0, g);
 #pragma unroll
                     for (int r = 0; r < R0; ++r) sb[SL::off(r)] = vin[q][r];
@@ -596,7 +597,7 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
                 int j, g;
                 bmap<LAYOUT, L, G, RL>(threadIdx.x + q * NT, j, g);
                 typedef Slot<LAYOUT, L, G, PSH> SL;
-                if constexpr (slot_site_on<LAYOUT, 3>() && SL::template strided<L / RL, RL>()) {
+                if constexpr (slot_site_on<LAYOUT, SF, 3>() && SL::template strided<L / RL, RL>()) {
                     const C* sb = s + SL::base(j, g);
 #pragma unroll
                     for (int r = 0; r < RL; ++r) vout[q][r] = sb[SL::off(r * (L / RL))];
