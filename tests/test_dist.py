@@ -65,3 +65,17 @@ def test_roofline_helpers():
     assert r["frac"] == pytest.approx(0.5)
     assert bench.ncu_record("kr_mpa", "no such workload", "x") == {}
     assert bench.ncu_traffic("no_such_kernel", "w", "s") is None
+
+
+def test_clock_samples_are_parsed():
+    """The clocks record: median SM clock of the loaded samples, the maximum
+    clock, and every throttle reason that was active in any sample."""
+    idle = "0, 345, 2070, 120.5, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active"
+    busy = "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1965, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    hot = "0, 1800, 2070, 1400.0, 0x0000000000000020, Not Active, Not Active, Active, Not Active"
+    r = bench.parse_clock_samples("\n".join([idle, busy, busy, capped, "garbage line", ""]))
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 4
+    assert r["reasons"] == ["sw_power_cap"]
+    assert bench.parse_clock_samples(hot)["reasons"] == ["sw_thermal_slowdown"]
+    assert bench.parse_clock_samples("")["reasons"] == ["no samples"]
