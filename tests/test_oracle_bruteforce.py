@@ -1,0 +1,127 @@
+"""Tiny brute-force pin of the oracle's MPA (MPA steps 1-7, Eq. (6)).
+
+Eq. (6) is evaluated literally with dense DFT matrices (the forward
+transform with exp(+i omega t), text after Eq. (1)) on N = 8 or 16 modes
+and M = 2..4 nodes, and compared with the oracle's radix-2, node-parallel
+implementation.  The phases beta(w, z) = w^2/2 int beta2 + w^3/6 int beta3
+(text after Eq. (2)) and the gain factor exp(int G), G = g - gamma, are
+integrated segment by segment; sigma at a node on a segment boundary is the
+mean of the one-sided values inside the interval and the inner value at its
+ends (the composite trapezoid on each smooth piece); a lumped amplifier at
+the interval end multiplies the result by exp(z_a gamma) (G of Eq. (1))."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_0086_gb300.workloads import FiberMap, Segment
+
+
+def dft_matrices(N):
+    n = np.arange(N)
+    F = np.exp(2j * np.pi * np.outer(n, n) / N)  # F[x]_k = sum_n x_n e^{+2 pi i k n / N}
+    return F, np.conj(F) / N
+
+
+def omegas(N, T):
+    k = np.arange(N)
+    return 2 * np.pi * np.where(k < N // 2, k, k - N) / T
+
+
+def integral(fib, za, zb, f):
+    """int_za^zb f(segment) dz over the periodic map, piece by piece."""
+    out, a = 0.0, 0.0
+    for p in range(fib.n_periods):
+        for s in fib.segments:
+            b = a + s.length_km
+            lo, hi = max(a, za), min(b, zb)
+            if hi > lo:
+                out += f(s) * (hi - lo)
+            a = b
+    return out
+
+
+def sigma_at(fib, z, z0, z1):
+    """sigma(z_j): one-sided values at a boundary, averaged inside (z0, z1)."""
+    eps = 1e-9
+    left = [s for s in _pieces(fib) if s[0] < z - eps / 2 <= s[1]]
+    right = [s for s in _pieces(fib) if s[0] <= z + eps / 2 < s[1]]
+    sl, sr = left[0][2].sigma_per_W_km if left else None, right[0][2].sigma_per_W_km if right else None
+    if abs(z - z0) < eps:
+        return sr
+    if abs(z - z1) < eps:
+        return sl
+    return 0.5 * (sl + sr)
+
+
+def _pieces(fib):
+    a = 0.0
+    for p in range(fib.n_periods):
+        for s in fib.segments:
+            yield (a, a + s.length_km, s)
+            a += s.length_km
+
+
+def brute_mpa(A0, fib, T, z0, L, M, n_tot):
+    N = A0.size
+    F, Fi = dft_matrices(N)
+    w = omegas(N, T)
+    dz = L / M
+    z = z0 + dz * np.arange(M + 1)
+    z[M] = z0 + L
+
+    def beta(zz):
+        b2 = integral(fib, z0, zz, lambda s: s.beta2_ps2_per_km)
+        b3 = integral(fib, z0, zz, lambda s: s.beta3_ps3_per_km)
+        return w ** 2 / 2 * b2 + w ** 3 / 6 * b3
+
+    def intG(zz):
+        return integral(fib, z0, zz, lambda s: s.gain_per_km - fib.gamma_per_km)
+
+    psi0 = F @ A0                                  # step 1: A_hat(z0)
+    psi = np.tile(psi0, (M + 1, 1))                # psi^{(0)}_j = psi_0
+    for _ in range(n_tot):                         # step 6
+        V = np.empty_like(psi)
+        for j in range(M + 1):
+            Ahat = psi[j] * np.exp(1j * beta(z[j]) + intG(z[j]))      # step 2
+            A = Fi @ Ahat                                             # step 3
+            U = np.abs(A) ** 2 * A                                    # step 4
+            V[j] = sigma_at(fib, z[j], z0, z0 + L) * dz * (F @ U) * np.exp(-1j * beta(z[j]) - intG(z[j]))
+        new = np.empty_like(psi)                   # step 5: the trapezoid of Eq. (6)
+        new[0] = psi0
+        for l in range(1, M + 1):
+            new[l] = psi0 + 1j * (V[0] / 2 + V[1:l].sum(axis=0) + V[l] / 2)
+        psi = new
+    out = psi[M] * np.exp(1j * beta(z0 + L) + intG(z0 + L))        # step 7
+    k_end = (z0 + L) / fib.z_a_km
+    if abs(k_end - round(k_end)) < 1e-9 and round(k_end) >= 1:
+        out = out * np.exp(fib.z_a_km * fib.gamma_per_km)          # lumped gain at z_k
+    return Fi @ out
+
+
+CASES = {
+    # one segment, interval inside the span (no amplifier), distributed gain
+    "uniform": (FiberMap((Segment(4.0, -1.3, 0.12, 1.1, 0.02),), 0.05, 4.0, 1), 16, 8.0, 0.0, 2.0, 3, 2),
+    # two segments, the boundary on node 2 of 4, the interval ends at the amplifier
+    "boundary_on_node": (FiberMap((Segment(1.0, -1.0, 0.1, 1.2), Segment(1.0, 2.0, -0.05, 0.8, 0.03)), 0.07, 2.0, 2),
+                         16, 8.0, 0.0, 2.0, 4, 3),
+    # the same map, the boundary between nodes (M = 3), a later interval
+    "boundary_between_nodes": (FiberMap((Segment(1.0, -1.0, 0.1, 1.2), Segment(1.0, 2.0, -0.05, 1.2, 0.03)), 0.07,
+                                        2.0, 2), 8, 6.0, 2.0, 2.0, 3, 2),
+    # a single node step (M = 2) at n_tot = 1
+    "one_level": (FiberMap((Segment(3.0, 0.8, 0.0, 0.9),), 0.0, 3.0, 1), 8, 6.0, 0.0, 1.5, 2, 1),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_oracle_mpa_equals_literal_eq6(case):
+    fib, N, T, z0, L, M, n_tot = CASES[case]
+    rng = np.random.default_rng(7)
+    A0 = (rng.standard_normal(N) + 1j * rng.standard_normal(N)) * 0.6
+    ref = brute_mpa(A0, fib, T, z0, L, M, n_tot)
+    got = oracle.mpa(A0, fib, T, z0, z0 + L, L, M, n_tot)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    # the nonlinear part is not negligible: the linear flow alone is far off
+    lin = brute_mpa(A0, FiberMap(tuple(Segment(s.length_km, s.beta2_ps2_per_km, s.beta3_ps3_per_km, 0.0,
+                                               s.gain_per_km) for s in fib.segments),
+                                 fib.gamma_per_km, fib.z_a_km, fib.n_periods), T, z0, L, M, n_tot)
+    assert np.linalg.norm(got - lin) / np.linalg.norm(ref) > 1e-3
