@@ -125,3 +125,54 @@ def test_oracle_mpa_equals_literal_eq6(case):
                                                s.gain_per_km) for s in fib.segments),
                                  fib.gamma_per_km, fib.z_a_km, fib.n_periods), T, z0, L, M, n_tot)
     assert np.linalg.norm(got - lin) / np.linalg.norm(ref) > 1e-3
+
+
+def brute_ss(A0, fib, T, z_from, z_to, dz):
+    """Eq. (4) as Strang splitting, literally: a half linear step, then per
+    step a Kerr rotation exp(i |A|^2 int sigma) and a full linear step (the
+    last one a half step); each linear step is the exact multiplier
+    exp(i beta + int G) times exp(z_a gamma) for every amplifier z_k in its
+    range (a, b]."""
+    N = A0.size
+    F, Fi = dft_matrices(N)
+    w = omegas(N, T)
+    K = int(round((z_to - z_from) / dz))
+
+    def lin(X, a, b):
+        b2 = integral(fib, a, b, lambda s: s.beta2_ps2_per_km)
+        b3 = integral(fib, a, b, lambda s: s.beta3_ps3_per_km)
+        G = integral(fib, a, b, lambda s: s.gain_per_km - fib.gamma_per_km)
+        n_amp = sum(1 for k in range(1, 10 * fib.n_periods + 2) if a < k * fib.z_a_km <= b + 1e-12)
+        return X * np.exp(1j * (w ** 2 / 2 * b2 + w ** 3 / 6 * b3) + G + n_amp * fib.z_a_km * fib.gamma_per_km)
+
+    X = F @ A0
+    a, b = z_from, z_from + dz / 2
+    X = lin(X, a, b)
+    for k in range(K):
+        A = Fi @ X
+        S = integral(fib, z_from + k * dz, z_from + (k + 1) * dz, lambda s: s.sigma_per_W_km)
+        A = A * np.exp(1j * S * np.abs(A) ** 2)
+        X = F @ A
+        a, b = b, (z_to if k == K - 1 else b + dz)
+        X = lin(X, a, b)
+    return Fi @ X
+
+
+SS_CASES = {
+    # a segment boundary inside a step (sigma differs), distributed gain, an
+    # amplifier inside a linear step (z = 2) and one at the end (z = 4)
+    "two_spans": (FiberMap((Segment(1.3, -1.0, 0.1, 1.2), Segment(0.7, 2.0, -0.05, 0.8, 0.03)), 0.07, 2.0, 2),
+                  16, 8.0, 0.0, 4.0, 0.5),
+    # a later stretch that ends between amplifiers, one segment type
+    "inside_a_span": (FiberMap((Segment(3.0, 0.8, 0.0, 0.9),), 0.05, 3.0, 2), 8, 6.0, 1.5, 4.5, 0.25),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SS_CASES))
+def test_oracle_ss_equals_literal_eq4(case):
+    fib, N, T, z0, z1, dz = SS_CASES[case]
+    rng = np.random.default_rng(11)
+    A0 = (rng.standard_normal(N) + 1j * rng.standard_normal(N)) * 0.6
+    ref = brute_ss(A0, fib, T, z0, z1, dz)
+    got = oracle.ss(A0, fib, T, z0, z1, dz)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
