@@ -61,7 +61,9 @@ def _pieces(fib):
             a += s.length_km
 
 
-def brute_mpa(A0, fib, T, z0, L, M, n_tot):
+def brute_mpa(A0, fib, T, z0, L, M, n_tot, psi_last=False):
+    """Steps 1-7 with dense matrices; psi_last=True returns psi^{(n_tot)} at
+    node M (natural frequency order) instead, before step 7."""
     N = A0.size
     F, Fi = dft_matrices(N)
     w = omegas(N, T)
@@ -91,6 +93,8 @@ def brute_mpa(A0, fib, T, z0, L, M, n_tot):
         for l in range(1, M + 1):
             new[l] = psi0 + 1j * (V[0] / 2 + V[1:l].sum(axis=0) + V[l] / 2)
         psi = new
+    if psi_last:
+        return psi[M]
     out = psi[M] * np.exp(1j * beta(z0 + L) + intG(z0 + L))        # step 7
     k_end = (z0 + L) / fib.z_a_km
     if abs(k_end - round(k_end)) < 1e-9 and round(k_end) >= 1:
@@ -125,6 +129,55 @@ def test_oracle_mpa_equals_literal_eq6(case):
                                                s.gain_per_km) for s in fib.segments),
                                  fib.gamma_per_km, fib.z_a_km, fib.n_periods), T, z0, L, M, n_tot)
     assert np.linalg.norm(got - lin) / np.linalg.norm(ref) > 1e-3
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_oracle_mpa_interval_equals_literal_eq6(case):
+    """The exported single-interval entry (steps 2-6 from a given spectrum,
+    no step 7), which the full-size GPU parity tests compare against, equals
+    the dense evaluation of Eq. (6) at node M."""
+    fib, N, T, z0, L, M, n_tot = CASES[case]
+    rng = np.random.default_rng(7)
+    A0 = (rng.standard_normal(N) + 1j * rng.standard_normal(N)) * 0.6
+    F, _ = dft_matrices(N)
+    ref = brute_mpa(A0, fib, T, z0, L, M, n_tot, psi_last=True)
+    got = oracle.mpa_interval(F @ A0, fib, T, z0, L, M, n_tot)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def step7(psiM, fib, T, z0, L):
+    """Step 7 written out with numpy: A(z0+L) = F^-1[psi_M exp(i beta(w, L)
+    + int G)], times exp(z_a gamma) when z0+L is an amplifier location."""
+    N = psiM.size
+    w = omegas(N, T)
+    b2 = integral(fib, z0, z0 + L, lambda s: s.beta2_ps2_per_km)
+    b3 = integral(fib, z0, z0 + L, lambda s: s.beta3_ps3_per_km)
+    G = integral(fib, z0, z0 + L, lambda s: s.gain_per_km - fib.gamma_per_km)
+    out = psiM * np.exp(1j * (w ** 2 / 2 * b2 + w ** 3 / 6 * b3) + G)
+    k_end = (z0 + L) / fib.z_a_km
+    if abs(k_end - round(k_end)) < 1e-9 and round(k_end) >= 1:
+        out = out * np.exp(fib.z_a_km * fib.gamma_per_km)
+    return np.fft.fft(out) / N  # F^-1 with the exp(+i w t) forward sign: (1/N) sum_k X_k e^{-2 pi i kn/N}
+
+
+@pytest.mark.parametrize("N,M,n_tot,z0", [(1 << 10, 8, 2, 0.0), (1 << 12, 12, 3, 5.0), (1 << 9, 5, 1, 45.0)])
+def test_oracle_mpa_interval_then_step7_equals_oracle_mpa(N, M, n_tot, z0):
+    """oracle.mpa_interval followed by step 7 in numpy reproduces oracle.mpa
+    over that interval on the benchmark DM map (natural frequency order in,
+    interval start z0 anywhere in the span, including the interval that ends
+    at the amplifier)."""
+    from paper_1101_0086_gb300.workloads import dm_map, wdm_field
+    fib = dm_map(2)
+    T = 100.0 * N / 256
+    L = 5.0
+    A0 = wdm_field(N, T, 2, 50.0, N // 256, 30.0, 2.0, "qpsk", seed=N + M)
+    ref = oracle.mpa(A0, fib, T, z0, z0 + L, L, M, n_tot)
+    psi0 = N * np.fft.ifft(A0)  # F[A]_k = sum_n A_n e^{+2 pi i kn/N}
+    got = step7(oracle.mpa_interval(psi0, fib, T, z0, L, M, n_tot), fib, T, z0, L)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-13
+    # the nonlinear correction itself (beyond the linear flow) is what matches
+    lin = step7(psi0, fib, T, z0, L)
+    assert np.linalg.norm(ref - lin) / np.linalg.norm(ref) > 1e-5
 
 
 def brute_ss(A0, fib, T, z_from, z_to, dz):
