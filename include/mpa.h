@@ -49,7 +49,9 @@ enum {
     MPA_ERR_WORKSPACE = 3,     /* workspace missing or smaller than required */
     MPA_ERR_CUDA = 4,          /* a CUDA call failed (see mpa_last_cuda_error) */
     MPA_ERR_GRID = 5,          /* z-grid inconsistent with the fiber map (see each call) */
-    MPA_ERR_NONFINITE = 6      /* a NaN/Inf was produced (mpa_plan_status) */
+    MPA_ERR_NONFINITE = 6,     /* a NaN/Inf was produced (mpa_plan_status, mpa_batch_status) */
+    MPA_ERR_DIVERGED = 7,      /* the Picard iteration did not contract (mpa_plan_status, mpa_batch_status) */
+    MPA_ERR_SCALES = 8         /* scales outside the weakly nonlinear regime (mpa_plan_check_scales) */
 };
 
 enum { MPA_FP32 = 0, MPA_FP64 = 1 };
@@ -150,12 +152,50 @@ MPA_API int mpa_plan_autotune(mpa_plan* plan, mpa_stream stream, int32_t* log2_n
 /* Sets the split to column length 2^log2_n2 without timing (e.g. a value an
  * earlier mpa_plan_autotune chose).  MPA_ERR_UNSUPPORTED_N if the passes or
  * the reverse-mode tiling do not support it; a WAVEFRONT plan accepts only
- * its current split.  Host-only. */
+ * its current split.  log2_n2 = 0 selects the on-chip node transform where N
+ * allows it (N <= 2^14 FP32, 2^13 FP64): MPA steps 2-4 and the weight of
+ * Eq. (6) for a node in one kernel, the spectrum held in shared memory
+ * (mpa_plan_autotune reports this choice as 0 and tries it first).
+ * Host-only. */
 MPA_API int mpa_plan_set_split(mpa_plan* plan, int32_t log2_n2);
 
-/* Returns MPA_ERR_NONFINITE if any propagate since the last call produced a
- * NaN/Inf (synchronises the stream), else MPA_OK; clears the flag. */
+/* Run-time checks of the propagations since the last call (synchronises the
+ * stream; clears the flags):
+ *   MPA_ERR_NONFINITE  an interval result (step 7) held a NaN/Inf;
+ *   MPA_ERR_DIVERGED   the Picard iteration of the text before MPA step 1
+ *                      did not contract in some interval: the relative
+ *                      increment at node M, ||psi^{(n+1)}_M - psi^{(n)}_M|| /
+ *                      ||psi^{(n+1)}_M|| (all frequencies), failed to shrink
+ *                      from one iteration to the next while above 1e-5 (the
+ *                      rounding floor of the node-M sums).  The iteration
+ *                      converges when L << z_nl (the paragraph after Eq. (2));
+ *                      this is what a too long interval or too strong
+ *                      nonlinearity produces.  Needs n_iter >= 2 and the
+ *                      level schedule (the wavefront schedule reports only
+ *                      MPA_ERR_NONFINITE).
+ * MPA_ERR_NONFINITE takes precedence; else MPA_OK. */
 MPA_API int mpa_plan_status(mpa_plan* plan, mpa_stream stream);
+
+/* The largest contraction factor rel_n / rel_{n-1} of the Picard increments
+ * (as defined at mpa_plan_status) over all intervals and iterations
+ * n >= 1 since the last call, into *worst (0 if none was measured);
+ * synchronises the stream and resets the value.  Well below 1 in the
+ * weakly nonlinear regime (about L / z_nl); >= 1 means no contraction. */
+MPA_API int mpa_plan_contraction(mpa_plan* plan, mpa_stream stream, double* worst);
+
+/* Scale check of the assumptions after Eq. (2): weak nonlinearity
+ * z_nl >> z_disp, and an interval L well below z_nl (the Picard iteration
+ * contracts by about L / z_nl) and L <~ z_disp.  With the typical peak power
+ * P (W) and pulse width tau (ps) of the field:
+ *   z_nl = 1 / (sigma_max P)          sigma_max: largest sigma of the map
+ *   z_disp = tau^2 / <|beta2|>        <|beta2|>: length-weighted mean over a period
+ * (km; written when the pointers are not NULL).  *flags (may be NULL)
+ * receives MPA_SCALE_* bits.  Returns MPA_ERR_SCALES when z_nl <= z_disp or
+ * L >= z_nl; MPA_SCALE_L_ABOVE_ZDISP alone (a soft condition of the paper)
+ * still returns MPA_OK.  Host only. */
+enum { MPA_SCALE_STRONG_NONLINEARITY = 1, MPA_SCALE_L_ABOVE_ZNL = 2, MPA_SCALE_L_ABOVE_ZDISP = 4 };
+MPA_API int mpa_plan_check_scales(const mpa_plan* plan, double peak_power_W, double pulse_width_ps,
+                                  double* z_nl_km, double* z_disp_km, int32_t* flags);
 
 MPA_API void mpa_plan_destroy(mpa_plan* plan);
 
@@ -234,6 +274,10 @@ MPA_API int mpa_batch_autotune(mpa_batch* batch, mpa_stream stream);
  * calls replay the graph on `stream`.  Do not call it while `stream` is
  * being captured by the caller. */
 MPA_API int mpa_batch_propagate(mpa_batch* batch, int32_t use_graph, mpa_stream stream);
+/* mpa_plan_status for all links of the batch: MPA_ERR_NONFINITE or
+ * MPA_ERR_DIVERGED if any link produced it since the last call (synchronises
+ * the stream, clears the flags), else MPA_OK. */
+MPA_API int mpa_batch_status(mpa_batch* batch, mpa_stream stream);
 MPA_API void mpa_batch_destroy(mpa_batch* batch);
 
 /* Symmetric split-step of Eq. (4) on the GPU: half linear step, then
@@ -284,8 +328,11 @@ MPA_API int mpa_fft(int64_t N, int32_t precision, int32_t sign, void* data, void
  * and uses a scratch array compiled into the library, which every GPU that
  * loads the library holds (MPA_FFT_NOALLOC_MAX_BYTES) until the process
  * exits.  It calls no cudaMalloc, cudaFree or allocating routine.
- * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * Each call made outside stream capture looks up the array's device address
+ * with the current device (so a device reset that recreates the context is
+ * picked up); a call under stream capture reuses the address of the last
+ * uncaptured call on that device, so make one call on each device before any
+ * stream capture (without one: MPA_ERR_CUDA).
  * All calls share the one array, so calls that overlap on the GPU race:
  * order them on one stream or synchronise between them.  Nothing in the
  * array needs to start at zero (each call overwrites what it reads).
@@ -299,6 +346,22 @@ MPA_API const char* mpa_last_cuda_error(void);
 
 /* Number of this library's kernels launched since load (all threads). */
 MPA_API int64_t mpa_kernel_launches(void);
+
+/* Fault injection for tests of the error paths (tooling; the paper has no
+ * counterpart).  after_launches >= 0 arms it: the kernel launch that many
+ * launches from now (0: the next one) is not made, and the entry point that
+ * attempted it returns MPA_ERR_CUDA with cuda_error (a cudaError_t value,
+ * nonzero) as mpa_last_cuda_error.  It fires once, then disarms;
+ * after_launches < 0 disarms.  Process-wide, shared by all threads.  No
+ * GPU is touched: the launch is skipped on the host. */
+MPA_API int mpa_debug_fail_launch(int64_t after_launches, int32_t cuda_error);
+
+/* Measured fused multiply-add throughput of the current device in FP64
+ * (MPA_FP64) or FP32 (MPA_FP32), in flop/s (2 per FMA), into *flops_per_s:
+ * the ALU roofline of the FP64 split-step comparator (tooling; the paper has
+ * no counterpart).  Runs a short kernel of independent FMA chains on
+ * `stream` (tens of ms) and synchronises; allocates nothing. */
+MPA_API int mpa_alu_peak(int32_t precision, double* flops_per_s, mpa_stream stream);
 
 /* Launch timing (tooling): with enable != 0 every subsequent launch of a
  * column pass, row pass or scan is bracketed by CUDA events on its stream

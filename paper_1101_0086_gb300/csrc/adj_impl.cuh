@@ -9,14 +9,16 @@ namespace adj {
 
 template <typename T, int L, int MODE>
 cudaError_t kca_one(const KCAParams<T>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     typedef KCGeom<T, L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(kca_kernel<T, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     if (p.ncols % Gm::G != 0) return cudaErrorInvalidValue;
     const long long nblk = p.ncols / Gm::G;
     if (nblk <= 0) return cudaSuccess;
@@ -40,14 +42,16 @@ cudaError_t kca_mode(int mode, const KCAParams<T>& p, cudaStream_t st) {
 
 template <typename T, int L>
 cudaError_t kra_one(const KRAParams<T>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     typedef KRGeom<T, L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(kra_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     if (p.nrows % Gm::G != 0) return cudaErrorInvalidValue;
     const long long nblk = p.nrows / Gm::G;
     if (nblk <= 0) return cudaSuccess;
@@ -62,16 +66,18 @@ cudaError_t kra_one(const KRAParams<T>& p, cudaStream_t st) {
 // The forward row pass of the recompute, keeping A(t) (KR_MPA_KEEP).
 template <typename T, int L>
 cudaError_t krk_one(const KRParams<T>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     typedef KRGeom<T, L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(kr_kernel<T, L, KR_MPA_KEEP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kr_kernel<T, L, KR_MPA_KEEP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     if (!p.keep) return cudaErrorInvalidValue;
     const long long nblk = (p.nrows + Gm::G - 1) / Gm::G;
     if (nblk <= 0) return cudaSuccess;
@@ -106,14 +112,16 @@ cudaError_t krk_any(int logL, const KRParams<T>& p, cudaStream_t st) {
 
 template <typename T, int L, int MODE>
 cudaError_t ssc_one(const SSCParams<T>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     typedef KCGeom<T, L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(ssc_kernel<T, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     if (p.N1 % Gm::G != 0) return cudaErrorInvalidValue;
     const bool prof = g_prof_on.load(std::memory_order_relaxed);
     if (prof) prof_begin(st);
@@ -125,14 +133,16 @@ cudaError_t ssc_one(const SSCParams<T>& p, cudaStream_t st) {
 
 template <typename T, int L, int MODE>
 cudaError_t ssr_one(const SSRParams<T>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     typedef KRGeom<T, L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(ssr_kernel<T, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     if (p.nrows % Gm::G != 0) return cudaErrorInvalidValue;
     const bool prof = g_prof_on.load(std::memory_order_relaxed);
     if (prof) prof_begin(st);
@@ -256,6 +266,7 @@ int kra_rows(int logL) {
 
 template <typename T>
 cudaError_t rscan_any(const RScanParams<T>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     const unsigned nb = (unsigned)((p.N + 255) / 256);
     const bool prof = g_prof_on.load(std::memory_order_relaxed);
     if (prof) prof_begin(st);
@@ -273,6 +284,7 @@ cudaError_t rscan_any(const RScanParams<T>& p, cudaStream_t st) {
 
 template <typename T>
 cudaError_t scan_store_any(const cx<T>* v, cx<T>* psi, const cx<T>* psi0c, long long N, int M, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     const bool prof = g_prof_on.load(std::memory_order_relaxed);
     if (prof) prof_begin(st);
     scan_store_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(v, psi, psi0c, N, M);
@@ -283,6 +295,7 @@ cudaError_t scan_store_any(const cx<T>* v, cx<T>* psi, const cx<T>* psi0c, long 
 
 template <typename T>
 cudaError_t scale_to_state_any(const cx<T>* in, double2* state, double scale, long long N, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     scale_to_state_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(in, state, scale, N);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();

@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(128) reduce_parts_kernel(const double* __restr
 }
 
 cudaError_t reduce_parts_launch(const double* part, int per, int n, double* acc, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     reduce_parts_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(part, per, n, acc);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();

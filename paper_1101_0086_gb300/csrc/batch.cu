@@ -37,7 +37,16 @@ struct Group {
     std::vector<int> active;       // links running at interval q
     long n_int = 0;
     size_t off_psi = 0, off_state = 0, off_psi0c = 0, off_nodes = 0, off_loff = 0, off_gain = 0, off_err = 0;
+    size_t off_conv = 0, off_dprev = 0;  // Picard increment check: ConvState and D at node M per link
 };
+
+Monitor group_monitor(unsigned char* ws, const Group& g) {
+    Monitor m{};
+    m.err = reinterpret_cast<unsigned int*>(ws + g.off_err);
+    m.conv = reinterpret_cast<ConvState*>(ws + g.off_conv);
+    m.dprev = reinterpret_cast<float2*>(ws + g.off_dprev);
+    return m;
+}
 
 }  // namespace
 
@@ -83,7 +92,7 @@ int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
     const NodeC* nodes = reinterpret_cast<const NodeC*>(b->ws + g.off_nodes);
     const int* loff = reinterpret_cast<const int*>(b->ws + g.off_loff);
     const double* gain = reinterpret_cast<const double*>(b->ws + g.off_gain);
-    unsigned int* err = reinterpret_cast<unsigned int*>(b->ws + g.off_err);
+    const Monitor mon = group_monitor(b->ws, g);
     // A_hat(0) = F[A] for every link (its node-0 buffer is the scratch)
     for (int i = 0; i < n; ++i) {
         cx<T>* scratch = psi + (long long)i * (M + 1) * N;
@@ -94,7 +103,7 @@ int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
     }
     for (long q = 0; q < g.n_int; ++q) {
         int rc = mpa_levels<T>(s, M, b->n_iter, g.active[(size_t)q], psi, psi0c, state, nodes, loff + (size_t)q * n,
-                               gain + (size_t)q * n, err, 1, nullptr, st);
+                               gain + (size_t)q * n, mon, 1, nullptr, st);
         if (rc) return rc;
     }
     for (int i = 0; i < n; ++i) {
@@ -257,6 +266,10 @@ int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_
         off = align256(off + g.gain.size() * sizeof(double));
         g.off_err = off;
         off = align256(off + sizeof(unsigned int));
+        g.off_conv = off;
+        off = align256(off + (size_t)n * sizeof(ConvState));
+        g.off_dprev = off;
+        if (n_iter > 1) off = align256(off + (size_t)n * N * sizeof(float2));
     }
     b->ws_need = off;
     *out = b;
@@ -279,8 +292,25 @@ int mpa_batch_set_workspace(mpa_batch* b, void* ws, size_t bytes) {
         MPA_TRY(cudaMemcpy(b->ws + g.off_loff, g.loff.data(), g.loff.size() * sizeof(int), cudaMemcpyHostToDevice));
         MPA_TRY(cudaMemcpy(b->ws + g.off_gain, g.gain.data(), g.gain.size() * sizeof(double), cudaMemcpyHostToDevice));
         MPA_TRY(cudaMemset(b->ws + g.off_err, 0, sizeof(unsigned int)));
+        MPA_TRY(cudaMemset(b->ws + g.off_conv, 0, g.links.size() * sizeof(ConvState)));
     }
     return MPA_OK;
+}
+
+int mpa_batch_status(mpa_batch* b, mpa_stream stream) {
+    if (!b) return MPA_ERR_INVALID_ARG;
+    if (!b->ws) return MPA_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<unsigned int> h(b->groups.size(), 0u);
+    for (size_t i = 0; i < b->groups.size(); ++i)
+        MPA_TRY(cudaMemcpyAsync(&h[i], b->ws + b->groups[i].off_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    MPA_TRY(cudaStreamSynchronize(st));
+    unsigned int all = 0u;
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+        all |= h[i];
+        MPA_TRY(cudaMemsetAsync(b->ws + b->groups[i].off_err, 0, sizeof(unsigned int), st));
+    }
+    return (all & ERR_NONFINITE) ? MPA_ERR_NONFINITE : (all & ERR_DIVERGED) ? MPA_ERR_DIVERGED : MPA_OK;
 }
 
 int mpa_batch_propagate(mpa_batch* b, int32_t use_graph, mpa_stream stream) {
@@ -346,9 +376,15 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
         const size_t N = (size_t)keep.N;
         Split best = keep;
         float best_ms = -1.f;
-        for (int l = keep.logN / 2 - 3; l <= keep.logN / 2 + 3 && rc == MPA_OK; ++l) {
+        // the on-chip node transform where N fits (first), then the four-step splits
+        for (int l = keep.logN / 2 - 4; l <= keep.logN / 2 + 3 && rc == MPA_OK; ++l) {
             Split s;
-            if (split_with(keep.N, b->prec, l, &s) != MPA_OK) continue;
+            if (l == keep.logN / 2 - 4) {
+                if (!onchip_ok(keep.N, b->prec) || split_n(keep.N, b->prec, &s) != MPA_OK) continue;
+                s.onchip = true;
+            } else if (split_with(keep.N, b->prec, l, &s) != MPA_OK) {
+                continue;
+            }
             g.sp = s;
             // the group's first interval on a zero field (timing does not depend on values)
             if (cudaMemsetAsync(b->ws + g.off_state, 0, (size_t)n * N * sizeof(double2), st) != cudaSuccess ||
@@ -371,7 +407,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                                              reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
                                              reinterpret_cast<const int*>(b->ws + g.off_loff),
                                              reinterpret_cast<const double*>(b->ws + g.off_gain),
-                                             reinterpret_cast<unsigned int*>(b->ws + g.off_err), 1, nullptr, st)
+                                             group_monitor(b->ws, g), 1, nullptr, st)
                          : mpa_levels<double>(g.sp, b->M, b->n_iter, g.active[0],
                                               reinterpret_cast<double2*>(b->ws + g.off_psi),
                                               reinterpret_cast<double2*>(b->ws + g.off_psi0c),
@@ -379,7 +415,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                                               reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
                                               reinterpret_cast<const int*>(b->ws + g.off_loff),
                                               reinterpret_cast<const double*>(b->ws + g.off_gain),
-                                              reinterpret_cast<unsigned int*>(b->ws + g.off_err), 1, nullptr, st);
+                                              group_monitor(b->ws, g), 1, nullptr, st);
                 if (rc == MPA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
                     rc = cuda_fail(cudaGetLastError());
@@ -390,7 +426,9 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
             }
         }
         g.sp = rc == MPA_OK ? best : keep;
-        if (cudaMemsetAsync(b->ws + g.off_err, 0, sizeof(unsigned int), st) != cudaSuccess && rc == MPA_OK)
+        if ((cudaMemsetAsync(b->ws + g.off_err, 0, sizeof(unsigned int), st) != cudaSuccess ||
+             cudaMemsetAsync(b->ws + g.off_conv, 0, (size_t)n * sizeof(ConvState), st) != cudaSuccess) &&
+            rc == MPA_OK)
             rc = cuda_fail(cudaGetLastError());
     }
     cudaEventDestroy(e0);

@@ -10,10 +10,10 @@
 // the process exits.  The entry point itself allocates nothing.
 #include <mutex>
 
-#include "launch.h"
-#include "mpa.h"
+#include "host.h"
 
 using namespace mpa;
+using namespace mpa::host;
 
 // Scratch of the no-allocation transform: one N-sample buffer that receives
 // the transposed field.  Every call (any stream, any thread) uses the same
@@ -29,55 +29,31 @@ std::mutex g_mu;
 void* g_scratch[kMaxDevices] = {};
 
 // Device address of the scratch on the current device.  The array's name is
-// only a host-side stand-in, so the address is looked up once per device
-// (with that device current) and cached.
-cudaError_t scratch_on_current_device(void** out) {
+// only a host-side stand-in, so the address is looked up with the device
+// current.  Outside stream capture it is looked up on every call (cheap, and
+// it allocates nothing), so a context that was reset and recreated is
+// picked up; while `st` is being captured the address cached by the last
+// uncaptured call on this device is used (the lookup is not a stream
+// operation, but a first call under capture has nothing to fall back on).
+cudaError_t scratch_on_current_device(cudaStream_t st, void** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, mpa_fft_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch[dev] = p;
+    } else if (!g_scratch[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch[dev];
     return cudaSuccess;
-}
-
-int log2_exact(long long n) {
-    int l = 0;
-    while ((1ll << l) < n) ++l;
-    return (1ll << l) == n ? l : -1;
-}
-
-template <typename T>
-cudaError_t transform(long long N, int logN, int logN1, int logN2, int sign, cx<T>* data, cx<T>* scratch,
-                      cudaStream_t st) {
-    const long long N1 = 1ll << logN1, N2 = 1ll << logN2;
-    cudaError_t e;
-    KCParams<T> c{};
-    c.dst = sign > 0 ? scratch : data;
-    c.src = c.dst;
-    c.N = N;
-    c.logN = logN;
-    c.N1 = (int)N1;
-    c.logN1 = logN1;
-    c.ncols = N1;
-    KRParams<T> r{sign > 0 ? scratch : data, N2, N, logN, (int)N2, (T)(1.0 / (double)N), T(0)};
-    if (sign > 0) {
-        // natural A(t) (N1 x N2) -> rows of the work layout -> natural spectrum
-        if ((e = transpose_launch<T>(data, scratch, N1, N2, st)) != cudaSuccess) return e;
-        if ((e = kr_launch<T>(KR_FWD, logN1, r, st)) != cudaSuccess) return e;
-        if ((e = kc_launch<T>(KC_FWD, logN2, c, st)) != cudaSuccess) return e;
-    } else {
-        if ((e = kc_launch<T>(KC_INV, logN2, c, st)) != cudaSuccess) return e;
-        if ((e = kr_launch<T>(KR_INV, logN1, r, st)) != cudaSuccess) return e;
-        if ((e = transpose_launch<T>(data, scratch, N2, N1, st)) != cudaSuccess) return e;
-    }
-    return cudaMemcpyAsync(data, scratch, (size_t)N * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace
@@ -85,20 +61,26 @@ cudaError_t transform(long long N, int logN, int logN1, int logN2, int sign, cx<
 extern "C" int mpa_fft_noalloc(int64_t N, int32_t precision, int32_t sign, void* data, mpa_stream stream) {
     if (!data || (sign != 1 && sign != -1)) return MPA_ERR_INVALID_ARG;
     if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
-    const int logN = log2_exact((long long)N);
-    if (logN < 8 || logN > (precision == MPA_FP32 ? 25 : 24)) return MPA_ERR_UNSUPPORTED_N;
-    const size_t csize = precision == MPA_FP32 ? sizeof(float2) : sizeof(double2);
-    if ((size_t)N * csize > (size_t)MPA_FFT_NOALLOC_MAX_BYTES) return MPA_ERR_WORKSPACE;
-    const int logN2 = logN / 2 < KC_LOG_MAX ? logN / 2 : KC_LOG_MAX;
-    const int logN1 = logN - logN2;
-    void* scratch = nullptr;
-    if (scratch_on_current_device(&scratch) != cudaSuccess) return MPA_ERR_CUDA;
+    // the same split as mpa_fft (split_n), checked before the size limit
+    Split s;
+    int rc = split_n(N, precision, &s);
+    if (rc) return rc;
+    const size_t bytes = (size_t)N * (precision == MPA_FP32 ? sizeof(float2) : sizeof(double2));
+    if (bytes > (size_t)MPA_FFT_NOALLOC_MAX_BYTES) return MPA_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const cudaError_t e =
-        precision == MPA_FP32
-            ? transform<float>(N, logN, logN1, logN2, sign, reinterpret_cast<float2*>(data),
-                               reinterpret_cast<float2*>(scratch), st)
-            : transform<double>(N, logN, logN1, logN2, sign, reinterpret_cast<double2*>(data),
-                                reinterpret_cast<double2*>(scratch), st);
-    return e == cudaSuccess ? MPA_OK : MPA_ERR_CUDA;
+    void* scratch = nullptr;
+    MPA_TRY(scratch_on_current_device(st, &scratch));
+    // the launch sequence of mpa_fft, with the static scratch as its workspace
+    if (precision == MPA_FP32) {
+        float2* d = reinterpret_cast<float2*>(data);
+        float2* w = reinterpret_cast<float2*>(scratch);
+        rc = sign > 0 ? fft_forward<float>(s, d, w, st) : fft_inverse<float>(s, d, w, st);
+    } else {
+        double2* d = reinterpret_cast<double2*>(data);
+        double2* w = reinterpret_cast<double2*>(scratch);
+        rc = sign > 0 ? fft_forward<double>(s, d, w, st) : fft_inverse<double>(s, d, w, st);
+    }
+    if (rc) return rc;
+    MPA_TRY(cudaMemcpyAsync(data, scratch, bytes, cudaMemcpyDeviceToDevice, st));
+    return MPA_OK;
 }

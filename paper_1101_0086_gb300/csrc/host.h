@@ -143,7 +143,17 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Split {
     int logN, logN1, logN2;
     long long N, N1, N2;
+    // node transforms of the MPA levels on chip (kn_kernel, one node per
+    // tile row) instead of the column, row and column passes; N1 x N2 stays
+    // the split of the entry/exit transforms and of the reverse mode
+    bool onchip = false;
 };
+
+// Whether N fits the on-chip node transform in this precision.
+inline bool onchip_ok(long long N, int prec) {
+    const int l = ilog2(N);
+    return (1ll << l) == N && l >= KN_LOG_MIN && l <= (prec == MPA_FP32 ? kn_log_max<float>() : kn_log_max<double>());
+}
 
 // The split with column length 2^logN2 (0 if the passes do not support it).
 inline int split_with(long long N, int prec, int logN2, Split* s) {
@@ -221,8 +231,12 @@ inline int fft_inverse(const Split& s, cx<T>* spec, cx<T>* out, cudaStream_t st)
 // link-major; defined in plan.cu for float and double.
 template <typename T>
 int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi0c, double2* state,
-               const NodeC* nodes, const int* loff, const double* gain, unsigned int* err, int scan_mode,
+               const NodeC* nodes, const int* loff, const double* gain, const Monitor& mon, int scan_mode,
                double2* out, cudaStream_t st);
+
+// Relative Picard increment below which a non-shrinking increment is
+// rounding noise of the node-M sums rather than divergence.
+inline constexpr double kDivergenceFloor = 1e-5;
 
 }  // namespace host
 }  // namespace mpa

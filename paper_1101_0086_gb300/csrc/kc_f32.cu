@@ -5,19 +5,21 @@ namespace mpa {
 
 template <int L, int MODE>
 static cudaError_t kc_one(const KCParams<float>& pin, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     // callers that leave the link fields unset launch one run of nodes
     KCParams<float> p = pin;
     if (p.npl <= 0) p.npl = (int)(p.ncols >> p.logN1) > 0 ? (int)(p.ncols >> p.logN1) : 1;
     typedef KCGeom<float, L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(kc_kernel<float, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kc_kernel<float, L, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     const long long nblk = (p.ncols + Gm::G - 1) / Gm::G;
     if (nblk <= 0) return cudaSuccess;
     const bool prof = g_prof_on.load(std::memory_order_relaxed);

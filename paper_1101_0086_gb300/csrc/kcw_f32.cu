@@ -26,16 +26,18 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(double2* state, float2
 
 template <int L>
 static cudaError_t kcw_one(const KCWParams& p, int n_tiles, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     typedef KCWGeom<L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(kcw_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kcw_kernel<L>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     const bool prof = g_prof_on.load(std::memory_order_relaxed);
     if (prof) prof_begin(st);
     kcw_kernel<L><<<dim3((unsigned)n_tiles, (unsigned)p.n_jobs), Gm::NT, Gm::smem_bytes, st>>>(p);
@@ -81,6 +83,7 @@ int kcw_tile_cols(int logL) {
 
 cudaError_t reconstruct_launch(double2* state, float2* psi0c, const double2* D, const NodeC& nodeM, double gain,
                                long long N, unsigned int* err, double2* out, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     reconstruct_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(state, psi0c, D, nodeM, gain, N, err, out);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();

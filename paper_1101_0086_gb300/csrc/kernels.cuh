@@ -418,6 +418,123 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
 }
 
 // ------------------------------------------------------------------
+// Whole node transform on chip (MPA steps 2-4 and the weight of Eq. (6)) for
+// N small enough that one spectrum fits in a CTA's shared memory (N <= 2^14
+// FP32, 2^13 FP64): G = TE/N nodes per CTA, each a row of the row-pass tile
+// layout holding its spectrum in natural order:
+//   A_hat = psi_j exp(i beta_j + int G)        (phase at the load, step 2)
+//   A = F^-1[A_hat]; U = |A|^2 A; F[U]          (steps 3-4, in shared memory)
+//   V_j = F[U] sigma_j dz exp(-i beta_j - int G)   (at the store, Eq. (6))
+// One HBM (or L2) round trip per node instead of the three of the column,
+// row and column passes, no four-step outer factors.  Node addressing as in
+// KCParams (nl links x npl nodes, psi_0 shared by node 0).
+template <typename T> struct KNParams {
+    const cx<T>* src;
+    long long src_stride, src_lstride;
+    const cx<T>* src0;  // if non-null: the source of node jn == 0 of link l is src0 + l src0_lstride
+    long long src0_lstride;
+    cx<T>* dst;
+    long long dst_stride, dst_lstride;
+    long long nrows;    // nl * npl nodes in this launch
+    int npl;
+    const NodeC* nodes;  // link l, node jn at nodes[loff[l] + jn]
+    const int* loff;
+    T inv_n;
+};
+
+template <typename T, int L> struct KNGeom {
+    typedef KRGeom<T, L> R;
+    static constexpr int G = R::G, TE = R::TE, NT = R::NT;
+    typedef Tiling<T, 1> P;
+    static constexpr size_t smem_bytes =
+        ((size_t)TE + (TE >> P::PSH) + 1 + TwDims<L>::NLO + TwDims<L>::NHI) * sizeof(cx<T>);
+};
+
+template <typename T, int L>
+__global__ void __launch_bounds__(KNGeom<T, L>::NT, KNGeom<T, L>::NT <= 256 ? MPA_KR_MINB : 1)
+    kn_kernel(const KNParams<T> p) {
+    typedef cx<T> C;
+    typedef KNGeom<T, L> Gm;
+    typedef Tiling<T, 1> P;
+    constexpr int G = Gm::G, NT = Gm::NT, TE = Gm::TE;
+    typedef Xform<T, L, G, NT, P::RMAX, -1, LAYOUT_ROW, P::PSH, false> XI;
+    typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_ROW, P::PSH, true> XF;
+    static_assert(XI::RL == XF::R0, "inverse/forward junction radix");
+    constexpr bool FAST = sizeof(T) == 4;  // FP32: finite-difference phases + polynomial exp
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* thi = s + TE + (TE >> P::PSH) + 1;
+    C* tlo = thi + TwDims<L>::NHI;
+    const int tid = threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * G;
+
+    tw_init<T, L>(thi, tlo, tid, NT);
+    __syncthreads();
+
+    // ---- load node spectra (natural order, k = element index) and step 2
+    C vin[XI::Q0][XI::R0];
+#pragma unroll
+    for (int q = 0; q < XI::Q0; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XI::R0>(tid + q * NT, j, g);
+        const long long row = row0 + g;
+        const bool ok = row < p.nrows;
+        const int node = ok ? (int)row : 0;
+        const int l = node / p.npl, jn = node - l * p.npl;
+        const C* src = (p.src0 && jn == 0) ? p.src0 + l * p.src0_lstride : p.src + l * p.src_lstride + jn * p.src_stride;
+        const NodeC nc = p.nodes[p.loff[l] + jn];
+        unsigned long long th[XI::R0];
+        if constexpr (FAST) phase_run<XI::R0>(j, L / XI::R0, nc, th);
+#pragma unroll
+        for (int r = 0; r < XI::R0; ++r) {
+            const int k = j + r * (L / XI::R0);
+            C v = ok ? src[k] : mkc(T(0), T(0));
+            C ph;
+            if constexpr (FAST) ph = expi_turns_poly(th[r]);
+            else ph = expi_turns<T>(phase_q64(signed_k(k, L), nc));
+            vin[q][r] = cscale(cmul(v, ph), (T)nc.pre);
+        }
+    }
+
+    // ---- steps 3-4: inverse transform, 1/N, |A|^2 A, forward transform
+    C vm[XI::QL][XI::RL];
+    XI::run(vin, vm, s, thi, tlo);
+#pragma unroll
+    for (int q = 0; q < XI::QL; ++q) {
+#pragma unroll
+        for (int r = 0; r < XI::RL; ++r) {
+            const C a = cscale(vm[q][r], p.inv_n);
+            vm[q][r] = cscale(a, a.x * a.x + a.y * a.y);
+        }
+    }
+    C vout[XF::QL][XF::RL];
+    XF::run(vm, vout, s, thi, tlo);
+
+    // ---- V_j (Eq. (6)) and the store, natural order
+#pragma unroll
+    for (int q = 0; q < XF::QL; ++q) {
+        int j, g;
+        bmap<LAYOUT_ROW, L, G, XF::RL>(tid + q * NT, j, g);
+        const long long row = row0 + g;
+        if (row >= p.nrows) continue;
+        const int node = (int)row;
+        const int l = node / p.npl, jn = node - l * p.npl;
+        C* dst = p.dst + l * p.dst_lstride + jn * p.dst_stride;
+        const NodeC nc = p.nodes[p.loff[l] + jn];
+        unsigned long long th[XF::RL];
+        if constexpr (FAST) phase_run<XF::RL>(j, L / XF::RL, nc, th);
+#pragma unroll
+        for (int r = 0; r < XF::RL; ++r) {
+            const int k = j + r * (L / XF::RL);
+            C ph;
+            if constexpr (FAST) ph = expi_turns_poly(th[r]);
+            else ph = expi_turns<T>(phase_q64(signed_k(k, L), nc));
+            dst[k] = cscale(cmul(vout[q][r], cconj(ph)), (T)nc.post);
+        }
+    }
+}
+
+// ------------------------------------------------------------------
 // Wavefront column pass (FP32): one CTA owns one column tile of one block
 // of B consecutive nodes at one Picard level and walks the nodes in order:
 //   forward column DFTs (finishing F[|A_j|^2 A_j])
@@ -649,6 +766,33 @@ __global__ void __launch_bounds__(KCWGeom<L>::NT, 1) kcw_kernel(const KCWParams 
 //   mode 0: write psi^{(n+1)}_j into psi[j] (next iteration)
 //   mode 1: step 7: state <- psi_M exp(i beta(w, z0+L) + int G) * gain, psi0c <- state
 //   mode 2: out <- psi_M (FP64, no step 7)
+//
+// Run-time checks (text before the MPA steps: psi^{(n)} are Picard iterates
+// that converge when L << z_nl).  Every level also measures its Picard
+// increment at node M, Delta^{(n+1)} = psi^{(n+1)}_M - psi^{(n)}_M =
+// i (D^{(n+1)} - D^{(n)}) with D the trapezoid sum of Eq. (6) at node M
+// (D^{(0)} = 0), relative to |psi^{(n+1)}_M|:
+//   rel_n = ||Delta^{(n+1)}|| / ||psi^{(n+1)}_M||   (sums over all frequencies).
+// The last block of a link to finish (atomic ticket, no waiting) compares
+// rel_n with rel_{n-1}: an increment that does not shrink, while above the
+// rounding floor of the working precision, sets bit 1 of the error word
+// (MPA_ERR_DIVERGED); a non-finite interval result sets bit 0.
+enum { ERR_NONFINITE = 1u, ERR_DIVERGED = 2u };
+struct ConvState {
+    double acc_d, acc_p;  // this level: sum |Delta|^2, sum |psi_M|^2
+    double prev_rel;      // rel of the previous level of this interval
+    double worst;         // largest rel_n / rel_{n-1} seen (contraction factor)
+    unsigned int count;   // blocks of this level finished
+    unsigned int pad;
+};
+// Device words of one group of links: the error word (bits above), one
+// ConvState per link and D at node M per link (N complex64 each).
+struct Monitor {
+    unsigned int* err;
+    ConvState* conv;
+    float2* dprev;
+};
+
 template <typename T> struct ScanParams {
     cx<T>* psi;          // link l's node j at psi + (l (M+1) + j) N
     long long N;
@@ -662,13 +806,66 @@ template <typename T> struct ScanParams {
     const int* loff;
     const double* gain;  // amplifier gain at the interval end, per link
     unsigned int* err;
+    // Picard increment check (skipped when conv is null): level n of n_iter
+    ConvState* conv;     // per link
+    float2* dprev;       // D^{(n)} at node M, link l at + l N (written unless last level)
+    int level, n_iter;
+    double floor_rel;    // increments below this relative size are rounding, not divergence
 };
+
+// Adds this block's sums to link l's accumulators; the last block of the
+// level closes the level (comparison with the previous one, reset).
+__device__ __forceinline__ void conv_close(ConvState* cs, unsigned int* err, double d2, double p2, int level,
+                                           int last_level, double floor_rel) {
+    __shared__ double red[2][8];
+    __shared__ bool last_block;
+    // warp sums, then the block's 8 warp sums by thread 0
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = d2;
+        red[1][w] = p2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sd = 0.0, sp = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            sd += red[0][i];
+            sp += red[1][i];
+        }
+        atomicAdd(&cs->acc_d, sd);
+        atomicAdd(&cs->acc_p, sp);
+        __threadfence();
+        last_block = atomicAdd(&cs->count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && last_block) {
+        __threadfence();
+        volatile ConvState* v = cs;
+        const double sd = v->acc_d, sp = v->acc_p;
+        const double rel = sp > 0.0 ? sqrt(sd / sp) : 0.0;
+        if (level > 0) {
+            const double q = v->prev_rel > 0.0 ? rel / v->prev_rel : (rel > 0.0 ? 1e300 : 0.0);
+            if (q > v->worst) v->worst = q;
+            if (!(rel < v->prev_rel) && rel > floor_rel) atomicOr(err, ERR_DIVERGED);
+        }
+        v->prev_rel = level == last_level ? 0.0 : rel;
+        v->acc_d = 0.0;
+        v->acc_p = 0.0;
+        v->count = 0u;
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
     typedef cx<T> C;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= p.N) return;
+    // N is a multiple of the block size (a power of two >= 256), so every
+    // thread has a frequency and takes part in the block reduction below
     const int l = blockIdx.y;
     const long long lo = (long long)l * p.N;
     cx<T>* psi = p.psi + lo * (p.M + 1);
@@ -709,10 +906,22 @@ __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
             }
         }
     }
-    if (p.mode == 0) return;
-    // psi_M = psi_0 + i (R_M - V_M/2) in FP64
+    // D = R_M - V_M/2 at node M in FP64 (psi_M = psi_0 + i D)
     const double sx = ((double)rx - (double)cxx) - 0.5 * (double)vl.x;
     const double sy = ((double)ry - (double)cyy) - 0.5 * (double)vl.y;
+    if (p.conv) {
+        // Picard increment at node M against the previous level's D
+        double dx = sx, dy = sy;
+        if (p.level > 0) {
+            const float2 d0 = p.dprev[lo + k];
+            dx -= (double)d0.x;
+            dy -= (double)d0.y;
+        }
+        if (p.level < p.n_iter - 1) p.dprev[lo + k] = make_float2((float)sx, (float)sy);
+        const double px = (double)p0.x - sy, py = (double)p0.y + sx;
+        conv_close(p.conv + l, p.err, dx * dx + dy * dy, px * px + py * py, p.level, p.n_iter - 1, p.floor_rel);
+    }
+    if (p.mode == 0) return;
     const double2 s0 = p.state[lo + k];
     const double2 psiM = make_double2(s0.x - sy, s0.y + sx);
     if (p.mode == 2) {
@@ -726,7 +935,7 @@ __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
     const double2 a = make_double2(g * (psiM.x * ph.x - psiM.y * ph.y), g * (psiM.x * ph.y + psiM.y * ph.x));
     p.state[lo + k] = a;
     p.psi0c_out[lo + k] = mkc((T)a.x, (T)a.y);
-    if (!(isfinite(a.x) && isfinite(a.y))) atomicOr(p.err, 1u);
+    if (!(isfinite(a.x) && isfinite(a.y))) atomicOr(p.err, ERR_NONFINITE);
 }
 
 // out[c][r] = in[r][c] for an R x Cc matrix (32 x 32 tiles).

@@ -5,16 +5,18 @@ namespace mpa {
 
 template <int L, int MODE>
 static cudaError_t kr_one(const KRParams<double>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     typedef KRGeom<double, L> Gm;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
         cudaError_t e = cudaFuncSetAttribute(kr_kernel<double, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Gm::smem_bytes);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kr_kernel<double, L, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     const long long nblk = (p.nrows + Gm::G - 1) / Gm::G;
     if (nblk <= 0) return cudaSuccess;
     const bool prof = g_prof_on.load(std::memory_order_relaxed);

@@ -11,11 +11,44 @@ namespace mpa {
 // Kernels launched by this library since load.
 extern std::atomic<long long> g_launches;
 
+// Host-side fault injection (mpa_debug_fail_launch): when armed, the launch
+// gate of the n-th kernel launch from now returns the chosen error instead
+// of launching, so the error paths of every entry point can be exercised
+// without making a GPU fault.  Every launcher calls it before its launch.
+extern std::atomic<long long> g_fail_countdown;  // < 0: disarmed
+extern std::atomic<int> g_fail_code;
+inline cudaError_t launch_gate() {
+    if (g_fail_countdown.load(std::memory_order_relaxed) < 0) return cudaSuccess;
+    const long long left = g_fail_countdown.fetch_sub(1, std::memory_order_acq_rel);
+    if (left == 0) return static_cast<cudaError_t>(g_fail_code.load(std::memory_order_relaxed));
+    if (left < 0) g_fail_countdown.store(-1, std::memory_order_relaxed);
+    return cudaSuccess;
+}
+
+// One-time kernel attribute setup per device: cudaFuncSetAttribute applies
+// to the current device only, so each launcher keeps one bit per device
+// (devices 0..63; any higher device sets the attributes on every launch).
+// Setting an attribute twice is harmless, so two threads racing on the first
+// launch of a device need no lock.
+struct AttrOnce {
+    std::atomic<unsigned long long> mask{0};
+};
+template <class F> inline cudaError_t attrs_once(AttrOnce& once, F&& set) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (once.mask.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess && bit) once.mask.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 // Optional CUDA-event timing of every launch, by kernel kind (off by
 // default; enabled through mpa_profile).
 enum {
     PK_KC_MPA_PRE = 0, PK_KC_MPA_POST, PK_KC_SS, PK_KC_FFT, PK_KR_MPA, PK_KR_SS, PK_KR_FFT, PK_SCAN, PK_AUX,
-    PK_KCW, PK_KC_ADJ, PK_KR_ADJ, PK_ADJ_AUX, PK_COUNT
+    PK_KCW, PK_KC_ADJ, PK_KR_ADJ, PK_ADJ_AUX, PK_KN, PK_COUNT
 };
 extern std::atomic<bool> g_prof_on;
 void prof_begin(cudaStream_t st);
@@ -33,6 +66,10 @@ template <typename T> constexpr int kr_log_max() { return sizeof(T) == 4 ? 14 : 
 
 template <typename T> cudaError_t kc_launch(int mode, int logL, const KCParams<T>& p, cudaStream_t st);
 template <typename T> cudaError_t kr_launch(int mode, int logL, const KRParams<T>& p, cudaStream_t st);
+// On-chip whole node transform for N = 2^logL, 2^8 <= N <= 2^kn_log_max.
+constexpr int KN_LOG_MIN = 8;
+template <typename T> constexpr int kn_log_max() { return sizeof(T) == 4 ? 14 : 13; }
+template <typename T> cudaError_t kn_launch(int logL, const KNParams<T>& p, cudaStream_t st);
 template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int links, cudaStream_t st);
 template <typename T> cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long C, cudaStream_t st);
 template <typename T> cudaError_t to_state_launch(const cx<T>* in, double2* state, cx<T>* copy, long long N, cudaStream_t st);

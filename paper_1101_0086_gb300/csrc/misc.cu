@@ -4,11 +4,14 @@
 #include <vector>
 
 #include "launch.h"
+#include "mpa.h"
 
 namespace mpa {
 
 std::atomic<long long> g_launches{0};
 std::atomic<bool> g_prof_on{false};
+std::atomic<long long> g_fail_countdown{-1};
+std::atomic<int> g_fail_code{0};
 
 namespace {
 struct Prof {
@@ -103,12 +106,14 @@ void prof_reset() {
     for (int k = 0; k < PK_COUNT; ++k) {
         P.ms[k] = 0.0;
         P.n[k] = 0;
+        P.bytes[k] = 0.0;
     }
 }
 
 static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int p_links, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     const bool pr = g_prof_on.load(std::memory_order_relaxed);
     if (pr) prof_begin(st);
     scan_kernel<T><<<dim3(blocks_for(p.N, 256), (unsigned)p_links), 256, 0, st>>>(p);
@@ -116,6 +121,7 @@ template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int p_link
         const double cs = (double)sizeof(cx<T>), n = (double)p.N;
         double b = ((p.M + 1) * n * cs + n * cs) * p_links;  // V_0..V_M and psi_0
         if (p.mode == 0) b += p.M * n * cs * p_links;  // psi^{(n+1)}_1..M
+        if (p.conv) b += ((p.level > 0 ? 8.0 : 0.0) + (p.level < p.n_iter - 1 ? 8.0 : 0.0)) * n * p_links;  // D at node M
         else b += (n * 16.0 + (p.mode == 1 ? n * (16.0 + cs) : n * 16.0)) * p_links;  // FP64 state in, result out
         prof_end(PK_SCAN, st, b);
     }
@@ -125,6 +131,7 @@ template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int p_link
 
 template <typename T>
 cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long C, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     dim3 grid((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32));
     transpose_kernel<T><<<grid, dim3(32, 8), 0, st>>>(in, out, R, C);
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -133,12 +140,14 @@ cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long
 
 template <typename T>
 cudaError_t to_state_launch(const cx<T>* in, double2* state, cx<T>* copy, long long N, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     to_state_kernel<T><<<blocks_for(N, 256), 256, 0, st>>>(in, state, copy, N);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
 template <typename T> cudaError_t from_state_launch(const double2* state, cx<T>* out, long long N, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
     from_state_kernel<T><<<blocks_for(N, 256), 256, 0, st>>>(state, out, N);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
@@ -154,3 +163,10 @@ template cudaError_t from_state_launch<float>(const double2*, float2*, long long
 template cudaError_t from_state_launch<double>(const double2*, double2*, long long, cudaStream_t);
 
 }  // namespace mpa
+
+extern "C" int mpa_debug_fail_launch(int64_t after_launches, int32_t cuda_error) {
+    if (after_launches >= 0 && cuda_error == 0) return MPA_ERR_INVALID_ARG;
+    mpa::g_fail_code.store(cuda_error, std::memory_order_relaxed);
+    mpa::g_fail_countdown.store(after_launches < 0 ? -1 : (long long)after_launches, std::memory_order_release);
+    return MPA_OK;
+}

@@ -2,6 +2,7 @@
 // per-node constants of Eq. (6)), workspace layout, and the launch schedule
 // of the MPA steps 1-7 and of the split-step of Eq. (4).
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -36,11 +37,29 @@ namespace host {
 // psi_0, so V_0 (identical at every iteration) is simply recomputed.
 template <typename T>
 int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi0c, double2* state,
-               const NodeC* nodes, const int* loff, const double* gain, unsigned int* err, int scan_mode,
+               const NodeC* nodes, const int* loff, const double* gain, const Monitor& mon, int scan_mode,
                double2* out, cudaStream_t st) {
     const long long N = s.N;
     const int npl = M + 1;
     for (int n = 0; n < n_iter; ++n) {
+        if (s.onchip) {
+            // steps 2-4 and the weight of Eq. (6), one launch for every node of every link
+            KNParams<T> k{};
+            k.src = n == 0 ? psi0c : psi;
+            k.src_stride = n == 0 ? 0 : N;
+            k.src_lstride = n == 0 ? N : (long long)npl * N;
+            k.src0 = psi0c;
+            k.src0_lstride = N;
+            k.dst = psi;
+            k.dst_stride = N;
+            k.dst_lstride = (long long)npl * N;
+            k.nrows = (long long)nl * npl;
+            k.npl = npl;
+            k.nodes = nodes;
+            k.loff = loff;
+            k.inv_n = (T)(1.0 / (double)N);
+            MPA_TRY(kn_launch<T>(s.logN, k, st));
+        } else {
         // steps 2-4 at every node (one launch per pass for all links)
         KCParams<T> c{};
         c.src = n == 0 ? psi0c : psi;
@@ -67,6 +86,7 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi
         c.src_lstride = (long long)npl * N;
         c.src0 = nullptr;
         MPA_TRY(kc_launch<T>(KC_MPA_POST, s.logN2, c, st));
+        }
         // step 5 (Eq. (6)); on the last iteration fused with step 7
         ScanParams<T> q{};
         q.psi = psi;
@@ -80,22 +100,35 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi
         q.nodes = nodes;
         q.loff = loff;
         q.gain = gain;
-        q.err = err;
+        q.err = mon.err;
+        q.conv = mon.conv;
+        q.dprev = mon.dprev;
+        q.level = n;
+        q.n_iter = n_iter;
+        q.floor_rel = kDivergenceFloor;
         MPA_TRY(scan_launch<T>(q, nl, st));
     }
     return MPA_OK;
 }
 
 template int mpa_levels<float>(const Split&, int, int, int, float2*, float2*, double2*, const NodeC*, const int*,
-                               const double*, unsigned int*, int, double2*, cudaStream_t);
+                               const double*, const Monitor&, int, double2*, cudaStream_t);
 template int mpa_levels<double>(const Split&, int, int, int, double2*, double2*, double2*, const NodeC*, const int*,
-                                const double*, unsigned int*, int, double2*, cudaStream_t);
+                                const double*, const Monitor&, int, double2*, cudaStream_t);
 
 }  // namespace host
 }  // namespace mpa
 
 namespace mpa {
 namespace host {
+
+Monitor monitor(const mpa_plan* p) {
+    Monitor m{};
+    m.err = reinterpret_cast<unsigned int*>(p->ws + p->off_err);
+    m.conv = reinterpret_cast<ConvState*>(p->ws + p->off_conv);
+    m.dprev = reinterpret_cast<float2*>(p->ws + p->off_dprev);
+    return m;
+}
 
 int interval_type(const mpa_plan* p, double z0, int* t) {
     if (p->n_types == 1) {
@@ -120,7 +153,7 @@ int run_interval(mpa_plan* p, int type, long n_amp, int scan_mode, double2* out,
                          reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c),
                          reinterpret_cast<double2*>(p->ws + p->off_state),
                          reinterpret_cast<const NodeC*>(p->ws + p->off_nodes), toff + type, gains + n_amp,
-                         reinterpret_cast<unsigned int*>(p->ws + p->off_err), scan_mode, out, st);
+                         monitor(p), scan_mode, out, st);
 }
 template int run_interval<float>(mpa_plan*, int, long, int, double2*, cudaStream_t);
 template int run_interval<double>(mpa_plan*, int, long, int, double2*, cudaStream_t);
@@ -395,7 +428,9 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
         p->off_toff = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
         p->off_gains = align256(p->off_toff + (size_t)p->n_types * sizeof(int));
         p->off_err = align256(p->off_gains + kMaxAmpsPerInterval * sizeof(double));
-        p->ws_need = align256(p->off_err + sizeof(unsigned int));
+        p->off_conv = align256(p->off_err + sizeof(unsigned int));
+        p->off_dprev = align256(p->off_conv + sizeof(ConvState));
+        p->ws_need = align256(p->off_dprev);  // the wavefront schedule has no increment check
         *out = p;
         return MPA_OK;
     }
@@ -409,7 +444,9 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
     p->off_toff = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
     p->off_gains = align256(p->off_toff + (size_t)p->n_types * sizeof(int));
     p->off_err = align256(p->off_gains + kMaxAmpsPerInterval * sizeof(double));
-    p->ws_need = align256(p->off_err + sizeof(unsigned int));
+    p->off_conv = align256(p->off_err + sizeof(unsigned int));
+    p->off_dprev = align256(p->off_conv + sizeof(ConvState));
+    p->ws_need = align256(p->off_dprev + (p->n_iter > 1 ? N * sizeof(float2) : 0));
     *out = p;
     return MPA_OK;
 }
@@ -434,6 +471,7 @@ int mpa_plan_set_workspace(mpa_plan* p, void* ws, size_t bytes) {
     for (int a = 0; a < kMaxAmpsPerInterval; ++a) gains[a] = std::exp((double)a * p->map.z_a * p->map.gamma);
     MPA_TRY(cudaMemcpy(p->ws + p->off_gains, gains, sizeof(gains), cudaMemcpyHostToDevice));
     MPA_TRY(cudaMemset(p->ws + p->off_err, 0, sizeof(unsigned int)));
+    MPA_TRY(cudaMemset(p->ws + p->off_conv, 0, sizeof(ConvState)));
     return MPA_OK;
 }
 
@@ -461,6 +499,16 @@ extern "C" {
 int mpa_plan_set_split(mpa_plan* p, int32_t log2_n2) {
     if (!p) return MPA_ERR_INVALID_ARG;
     if (p->wf) return log2_n2 == p->sp.logN2 ? MPA_OK : MPA_ERR_UNSUPPORTED_N;
+    if (log2_n2 == 0) {
+        // on-chip node transforms; the entry/exit transforms keep a four-step split
+        if (!onchip_ok(p->sp.N, p->prec)) return MPA_ERR_UNSUPPORTED_N;
+        if (p->sp.onchip) return MPA_OK;
+        Split s;
+        if (split_n(p->sp.N, p->prec, &s) != MPA_OK) return MPA_ERR_UNSUPPORTED_N;
+        s.onchip = true;
+        p->sp = s;
+        return MPA_OK;
+    }
     Split s;
     if (!admissible_split(p, log2_n2, &s)) return MPA_ERR_UNSUPPORTED_N;
     p->sp = s;
@@ -470,7 +518,7 @@ int mpa_plan_set_split(mpa_plan* p, int32_t log2_n2) {
 int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
     if (!p) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
-    if (log2_n2) *log2_n2 = p->sp.logN2;
+    if (log2_n2) *log2_n2 = p->sp.onchip ? 0 : p->sp.logN2;
     if (p->wf) return MPA_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const Split keep = p->sp;
@@ -482,9 +530,16 @@ int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
     Split best = keep;
     float best_ms = -1.f;
     int rc = MPA_OK;
-    for (int l = keep.logN / 2 - 3; l <= keep.logN / 2 + 3 && rc == MPA_OK; ++l) {
+    // candidates: the on-chip node transform (reported as column length 2^0)
+    // where N fits, then every admissible four-step split
+    for (int l = keep.logN / 2 - 4; l <= keep.logN / 2 + 3 && rc == MPA_OK; ++l) {
         Split s;
-        if (!admissible_split(p, l, &s)) continue;
+        if (l == keep.logN / 2 - 4) {
+            if (!onchip_ok(keep.N, p->prec) || split_n(keep.N, p->prec, &s) != MPA_OK) continue;
+            s.onchip = true;
+        } else if (!admissible_split(p, l, &s)) {
+            continue;
+        }
         p->sp = s;
         // a zero field: the timing does not depend on the values
         if (cudaMemsetAsync(p->ws + p->off_state, 0, N * sizeof(double2), st) != cudaSuccess ||
@@ -509,8 +564,9 @@ int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
     cudaEventDestroy(e1);
     p->sp = best;
     if (rc != MPA_OK) p->sp = keep;
-    if (log2_n2) *log2_n2 = p->sp.logN2;
+    if (log2_n2) *log2_n2 = p->sp.onchip ? 0 : p->sp.logN2;
     MPA_TRY(cudaMemsetAsync(p->ws + p->off_err, 0, sizeof(unsigned int), st));
+    MPA_TRY(cudaMemsetAsync(p->ws + p->off_conv, 0, sizeof(ConvState), st));
     return rc;
 }
 
@@ -538,7 +594,47 @@ int mpa_plan_status(mpa_plan* p, mpa_stream stream) {
     MPA_TRY(cudaMemcpyAsync(&h, p->ws + p->off_err, sizeof(h), cudaMemcpyDeviceToHost, st));
     MPA_TRY(cudaStreamSynchronize(st));
     MPA_TRY(cudaMemsetAsync(p->ws + p->off_err, 0, sizeof(unsigned int), st));
-    return h ? MPA_ERR_NONFINITE : MPA_OK;
+    return status_of_error_word(h);
+}
+
+int mpa_plan_contraction(mpa_plan* p, mpa_stream stream, double* worst) {
+    if (!p || !worst) return MPA_ERR_INVALID_ARG;
+    if (!p->ws) return MPA_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ConvState c{};
+    MPA_TRY(cudaMemcpyAsync(&c, p->ws + p->off_conv, sizeof(c), cudaMemcpyDeviceToHost, st));
+    MPA_TRY(cudaStreamSynchronize(st));
+    *worst = c.worst;
+    const double zero = 0.0;
+    MPA_TRY(cudaMemcpyAsync(p->ws + p->off_conv + offsetof(ConvState, worst), &zero, sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+    MPA_TRY(cudaStreamSynchronize(st));
+    return MPA_OK;
+}
+
+int mpa_plan_check_scales(const mpa_plan* p, double peak_power_W, double pulse_width_ps, double* z_nl_km,
+                          double* z_disp_km, int32_t* flags) {
+    if (!p || !(peak_power_W > 0.0) || !(pulse_width_ps > 0.0) || !std::isfinite(peak_power_W) ||
+        !std::isfinite(pulse_width_ps))
+        return MPA_ERR_INVALID_ARG;
+    // typical sigma and |beta2| of the map: the largest sigma (the strongest
+    // nonlinearity) and the length-weighted mean |beta2| over a period
+    double smax = 0.0, b2 = 0.0;
+    for (const auto& s : p->map.seg) {
+        smax = std::fmax(smax, std::fabs(s.sigma_per_W_km));
+        b2 += std::fabs(s.beta2_ps2_per_km) * s.length_km;
+    }
+    b2 /= p->map.period;
+    const double znl = smax > 0.0 ? 1.0 / (smax * peak_power_W) : HUGE_VAL;
+    const double zd = b2 > 0.0 ? pulse_width_ps * pulse_width_ps / b2 : HUGE_VAL;
+    int32_t f = 0;
+    if (!(znl > zd)) f |= MPA_SCALE_STRONG_NONLINEARITY;
+    if (!(p->L < znl)) f |= MPA_SCALE_L_ABOVE_ZNL;
+    if (p->L > zd) f |= MPA_SCALE_L_ABOVE_ZDISP;
+    if (z_nl_km) *z_nl_km = znl;
+    if (z_disp_km) *z_disp_km = zd;
+    if (flags) *flags = f;
+    return (f & (MPA_SCALE_STRONG_NONLINEARITY | MPA_SCALE_L_ABOVE_ZNL)) ? MPA_ERR_SCALES : MPA_OK;
 }
 
 void mpa_plan_destroy(mpa_plan* p) { delete p; }
@@ -605,6 +701,8 @@ const char* mpa_status_string(int status) {
         case MPA_ERR_CUDA: return "CUDA error";
         case MPA_ERR_GRID: return "z-grid inconsistent with the fiber map";
         case MPA_ERR_NONFINITE: return "non-finite value produced";
+        case MPA_ERR_DIVERGED: return "Picard iteration diverged (the increment grew between iterations)";
+        case MPA_ERR_SCALES: return "scales outside the weak-nonlinearity regime of the method";
     }
     return "unknown status";
 }
@@ -630,7 +728,7 @@ int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* byte
 const char* mpa_profile_kind_name(int kind) {
     static const char* names[PK_COUNT] = {"kc_mpa_pre", "kc_mpa_post", "kc_ss_step", "kc_fft", "kr_mpa",
                                           "kr_ss", "kr_fft", "scan", "aux", "kc_wavefront",
-                                          "kc_adjoint", "kr_adjoint", "adjoint_aux"};
+                                          "kc_adjoint", "kr_adjoint", "adjoint_aux", "kn_mpa"};
     return (kind >= 0 && kind < PK_COUNT) ? names[kind] : nullptr;
 }
 

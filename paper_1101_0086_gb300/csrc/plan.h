@@ -16,6 +16,7 @@ struct mpa_plan {
     std::vector<mpa::NodeC> nodes;  // n_types x (M+1)
     size_t csize;               // bytes per complex sample
     size_t off_psi, off_state, off_psi0c, off_nodes, off_err, off_toff, off_gains, ws_need;
+    size_t off_conv = 0, off_dprev = 0;  // Picard increment check (ConvState, D at node M)
     // wavefront schedule (FP32): S = n_iter slots of B node buffers
     bool wf = false;
     int B = 0;
@@ -26,6 +27,14 @@ struct mpa_plan {
 
 namespace mpa {
 namespace host {
+
+// The plan's run-time check words (error word, increment check).
+Monitor monitor(const mpa_plan* p);
+
+// MPA_ERR_NONFINITE or MPA_ERR_DIVERGED for the bits of an error word.
+inline int status_of_error_word(unsigned int h) {
+    return (h & ERR_NONFINITE) ? MPA_ERR_NONFINITE : (h & ERR_DIVERGED) ? MPA_ERR_DIVERGED : MPA_OK;
+}
 
 // Index of the interval start z0 within the DM period (its node table).
 int interval_type(const mpa_plan* p, double z0, int* t);

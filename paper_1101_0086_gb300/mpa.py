@@ -20,6 +20,9 @@ _lib: Optional[ctypes.CDLL] = None
 FP32, FP64 = 0, 1
 SCHEDULES = {"auto": 0, "level": 1, "wavefront": 2}
 _STATUS_NONFINITE = 6
+STATUS_DIVERGED = 7
+STATUS_SCALES = 8
+SCALE_FLAGS = {1: "strong nonlinearity (z_nl <= z_disp)", 2: "L >= z_nl", 4: "L > z_disp"}
 
 
 class MPAError(RuntimeError):
@@ -55,7 +58,8 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "mpa_batch_workspace_size", "mpa_batch_set_workspace", "mpa_batch_propagate", "mpa_batch_destroy",
            "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
            "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split",
-           "mpa_batch_autotune")
+           "mpa_batch_autotune", "mpa_plan_contraction", "mpa_plan_check_scales", "mpa_batch_status",
+           "mpa_debug_fail_launch", "mpa_alu_peak")
 
 
 def library_path() -> str:
@@ -114,6 +118,15 @@ def lib() -> ctypes.CDLL:
         L.mpa_batch_autotune.argtypes = [vp, vp]
         L.mpa_batch_autotune.restype = ctypes.c_int
         L.mpa_profile_kind_name.restype = ctypes.c_char_p
+        L.mpa_plan_contraction.argtypes = [vp, vp, ctypes.POINTER(dbl)]
+        L.mpa_plan_check_scales.argtypes = [vp, dbl, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                            ctypes.POINTER(i32)]
+        L.mpa_batch_status.argtypes = [vp, vp]
+        L.mpa_debug_fail_launch.argtypes = [i64, i32]
+        L.mpa_alu_peak.argtypes = [i32, ctypes.POINTER(dbl), vp]
+        for f in ("mpa_plan_contraction", "mpa_plan_check_scales", "mpa_batch_status", "mpa_debug_fail_launch",
+                  "mpa_alu_peak"):
+            getattr(L, f).restype = ctypes.c_int
         for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
                   "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft",
                   "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
@@ -173,6 +186,8 @@ class Plan:
         self.prec = _prec(precision)
         self.N = int(N)
         self.dtype = _cdtype(self.prec)
+        self.fiber = fiber
+        self._args = (float(T_ps), float(L_km), int(M), int(n_iter), schedule)
         self._fm, self._segs = _fiber_struct(fiber)
         prm = _PlanParams(self.N, float(T_ps), float(L_km), int(M), int(n_iter), self.prec, SCHEDULES[schedule])
         h = ctypes.c_void_p()
@@ -186,6 +201,7 @@ class Plan:
         self.workspace = workspace
         _check(L.mpa_plan_set_workspace(h, ctypes.c_void_p(workspace.data_ptr()), workspace.numel()),
                "mpa_plan_set_workspace")
+        self._split = min(max((self.N.bit_length() - 1) // 2, 4), 11)  # split_n's default column length
 
     def propagate(self, field: torch.Tensor, z_from_km: float, z_to_km: float, stream=None) -> torch.Tensor:
         """In-place MPA propagation of the time-domain field (``mpa_propagate``)."""
@@ -206,11 +222,13 @@ class Plan:
         GPU and keep the fastest; returns log2 of the chosen column length."""
         l2 = ctypes.c_int32()
         _check(lib().mpa_plan_autotune(self._h, _stream(stream), ctypes.byref(l2)), "mpa_plan_autotune")
+        self._split = int(l2.value)
         return int(l2.value)
 
     def set_split(self, log2_n2: int) -> None:
         """``mpa_plan_set_split``: use column length 2^log2_n2 (no timing)."""
         _check(lib().mpa_plan_set_split(self._h, int(log2_n2)), "mpa_plan_set_split")
+        self._split = int(log2_n2)
 
     @property
     def n_segments(self) -> int:
@@ -270,12 +288,78 @@ class Plan:
         return gi, gs, gb
 
     def status(self, stream=None) -> bool:
-        """False if a NaN/Inf was produced since the last call (synchronises)."""
+        """False if a NaN/Inf was produced since the last call (synchronises);
+        raises MPAError if the Picard iteration diverged (``mpa_plan_status``)."""
         rc = lib().mpa_plan_status(self._h, _stream(stream))
         if rc == _STATUS_NONFINITE:
             return False
         _check(rc, "mpa_plan_status")
         return True
+
+    def status_code(self, stream=None) -> int:
+        """The raw status of ``mpa_plan_status`` (0, 6 non-finite, 7 diverged)."""
+        return int(lib().mpa_plan_status(self._h, _stream(stream)))
+
+    def contraction(self, stream=None) -> float:
+        """Largest Picard contraction factor since the last call (``mpa_plan_contraction``)."""
+        q = ctypes.c_double()
+        _check(lib().mpa_plan_contraction(self._h, _stream(stream), ctypes.byref(q)), "mpa_plan_contraction")
+        return float(q.value)
+
+    def check_scales(self, peak_power_W: float, pulse_width_ps: float):
+        """``mpa_plan_check_scales``: (status, z_nl_km, z_disp_km, flags) for
+        the field's typical peak power and pulse width."""
+        znl, zd, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        rc = lib().mpa_plan_check_scales(self._h, float(peak_power_W), float(pulse_width_ps), ctypes.byref(znl),
+                                         ctypes.byref(zd), ctypes.byref(fl))
+        if rc not in (0, STATUS_SCALES):
+            _check(rc, "mpa_plan_check_scales")
+        return int(rc), float(znl.value), float(zd.value), int(fl.value)
+
+    def segment_coefficients(self):
+        """(sigma, beta2) per physical segment (period-major, float64 numpy)
+        as the plan was created with."""
+        import numpy as np
+        sig = np.array([sg.sigma_per_W_km for sg in self.fiber.segments] * self.fiber.n_periods, dtype=np.float64)
+        b2 = np.array([sg.beta2_ps2_per_km for sg in self.fiber.segments] * self.fiber.n_periods, dtype=np.float64)
+        return sig, b2
+
+    def with_segment_coefficients(self, sigma, beta2) -> "Plan":
+        """A new plan (same N, window, discretisation, precision and four-step
+        split) whose physical segments carry the given sigma and beta2
+        (float64, ``n_segments`` values each, period-major).  When the values
+        repeat every period the map stays periodic; otherwise it is unrolled
+        into one period that spans the link.  For optimisation loops that
+        update the per-segment coefficients between gradient steps."""
+        import dataclasses
+
+        import numpy as np
+        sig = np.asarray(sigma.detach().cpu() if isinstance(sigma, torch.Tensor) else sigma, dtype=np.float64)
+        b2 = np.asarray(beta2.detach().cpu() if isinstance(beta2, torch.Tensor) else beta2, dtype=np.float64)
+        segs, P = self.fiber.segments, self.fiber.n_periods
+        ns = len(segs)
+        if sig.shape != (ns * P,) or b2.shape != (ns * P,):
+            raise ValueError(f"expected {ns * P} values of sigma and beta2")
+        periodic = np.all(sig.reshape(P, ns) == sig[:ns]) and np.all(b2.reshape(P, ns) == b2[:ns])
+        if periodic:
+            new_segs = tuple(dataclasses.replace(sg, sigma_per_W_km=float(sig[i]), beta2_ps2_per_km=float(b2[i]))
+                             for i, sg in enumerate(segs))
+            fib = dataclasses.replace(self.fiber, segments=new_segs)
+        else:
+            new_segs = tuple(dataclasses.replace(segs[i % ns], sigma_per_W_km=float(sig[i]),
+                                                 beta2_ps2_per_km=float(b2[i])) for i in range(ns * P))
+            fib = dataclasses.replace(self.fiber, segments=new_segs, n_periods=1)
+        T_ps, L_km, M, n_iter, schedule = self._args
+        q = Plan(fib, self.N, T_ps, L_km, M, n_iter, precision=self.prec, device=self.workspace.device,
+                 schedule=schedule)
+        q.set_split(self.log2_n2)
+        return q
+
+    @property
+    def log2_n2(self) -> int:
+        """log2 of the current four-step column length (the library's default
+        split until :meth:`autotune` or :meth:`set_split` changes it)."""
+        return self._split
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -295,13 +379,23 @@ class MPAFunction(torch.autograd.Function):
     ``MPAFunction.apply(field, sigma, beta2, plan, z_from_km, z_to_km)``
     returns ``plan.propagate`` of a copy of ``field``.  ``sigma`` and
     ``beta2`` are float64 tensors of the plan's per-physical-segment
-    coefficients (``plan.n_segments`` values, period-major); they must hold
-    the values the plan was created with, and they receive dl/dsigma and
-    dl/dbeta2 when they require gradients.  The forward pass stores the
-    interval checkpoints; the backward pass is ``mpa_adjoint``."""
+    coefficients (``plan.n_segments`` values, period-major); they receive
+    dl/dsigma and dl/dbeta2 when they require gradients.  The plan carries
+    the coefficients the propagation uses, so the forward pass checks that
+    the tensors hold exactly those values and raises ValueError otherwise:
+    after an optimiser changes them, make the matching plan with
+    ``plan.with_segment_coefficients(sigma, beta2)``.  The forward pass
+    stores the interval checkpoints; the backward pass is ``mpa_adjoint``."""
 
     @staticmethod
     def forward(ctx, field, sigma, beta2, plan, z_from_km, z_to_km):
+        import numpy as np
+        ps, pb = plan.segment_coefficients()
+        gs = sigma.detach().to("cpu", torch.float64).reshape(-1).numpy()
+        gb = beta2.detach().to("cpu", torch.float64).reshape(-1).numpy()
+        if gs.shape != ps.shape or gb.shape != pb.shape or not (np.array_equal(gs, ps) and np.array_equal(gb, pb)):
+            raise ValueError("MPAFunction: sigma/beta2 differ from the coefficients the plan propagates with; "
+                             "use plan.with_segment_coefficients(sigma, beta2) to make the matching plan")
         out = field.detach().clone()
         ws = plan.propagate_checkpointed(out, z_from_km, z_to_km)
         ctx.plan, ctx.ws, ctx.z = plan, ws, (z_from_km, z_to_km)
@@ -354,6 +448,11 @@ class Batch:
 
     def propagate(self, use_graph: bool = True, stream=None) -> None:
         _check(lib().mpa_batch_propagate(self._h, 1 if use_graph else 0, _stream(stream)), "mpa_batch_propagate")
+
+    def status_code(self, stream=None) -> int:
+        """``mpa_batch_status``: 0, 6 (a link produced NaN/Inf) or 7 (a link's
+        Picard iteration diverged) since the last call; clears the flags."""
+        return int(lib().mpa_batch_status(self._h, _stream(stream)))
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -469,3 +568,17 @@ def profile_read() -> dict:
             out[name.decode()] = (float(ms.value), int(n.value), float(b.value))
         k += 1
     return out
+
+
+def debug_fail_launch(after_launches: int, cuda_error: int = 2) -> None:
+    """``mpa_debug_fail_launch``: make the library's launch ``after_launches``
+    from now fail on the host with ``cuda_error`` (default 2, out of memory);
+    a negative count disarms.  For tests of the error paths."""
+    _check(lib().mpa_debug_fail_launch(int(after_launches), int(cuda_error)), "mpa_debug_fail_launch")
+
+
+def alu_peak(precision="fp64", stream=None) -> float:
+    """``mpa_alu_peak``: measured FMA throughput of the current GPU in flop/s."""
+    v = ctypes.c_double()
+    _check(lib().mpa_alu_peak(_prec(precision), ctypes.byref(v), _stream(stream)), "mpa_alu_peak")
+    return float(v.value)

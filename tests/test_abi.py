@@ -1,6 +1,7 @@
 """The C-ABI library builds, loads without a GPU and exports every entry point
 declared in include/mpa.h; host-only argument and grid validation."""
 import ctypes
+import math
 import os
 import re
 
@@ -43,9 +44,58 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_status_strings(L):
-    for s in range(0, 7):
-        assert L.mpa_status_string(s)
+    for s in range(0, 9):
+        assert L.mpa_status_string(s) and L.mpa_status_string(s) != b"unknown status"
     assert L.mpa_status_string(99) == b"unknown status"
+
+
+def test_injected_launch_failure_reaches_the_caller_without_a_gpu(L):
+    """mpa_debug_fail_launch: the next kernel launch is refused on the host,
+    and the entry point that attempted it returns MPA_ERR_CUDA with the
+    injected error as its message; the injection fires once."""
+    fib = dm_map(1)
+    fm, segs = mpa._fiber_struct(fib)
+    N = 1 << 12
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: the first launch is refused
+    assert L.mpa_debug_fail_launch(0, 0) == 1  # an error code is required
+    assert L.mpa_debug_fail_launch(0, 2) == 0  # cudaErrorMemoryAllocation
+    rc = L.ss_propagate(ctypes.byref(fm), N, 1600.0, 0.05, 0, fake, 0.0, 0.05, fake, 1 << 20, None)
+    assert rc == 4
+    assert b"memory" in L.mpa_last_cuda_error()
+    assert L.mpa_debug_fail_launch(0, 719) == 0  # cudaErrorLaunchFailure
+    rc = L.mpa_fft(N, 1, -1, fake, fake, 1 << 20, None)
+    assert rc == 4 and b"launch" in L.mpa_last_cuda_error().lower()
+    assert L.mpa_debug_fail_launch(-1, 0) == 0  # disarm
+
+
+def test_scale_check_follows_the_weak_nonlinearity_assumptions(L):
+    """mpa_plan_check_scales: z_nl = 1/(sigma_max P), z_disp = tau^2/<|beta2|>
+    (length-weighted mean over the period), flags for z_nl <= z_disp and
+    L >= z_nl (errors) and L > z_disp (soft); values recomputed here from
+    the map."""
+    fib = dm_map(4)
+    rc, h = _plan(L, fib, 1 << 20, 102400.0, 5.0, 142, 2)
+    assert rc == 0
+    b2 = sum(abs(s.beta2_ps2_per_km) * s.length_km for s in fib.segments) / fib.period_km
+    smax = max(s.sigma_per_W_km for s in fib.segments)
+
+    def check(P, tau):
+        znl, zd, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        L.mpa_plan_check_scales.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_int32)]
+        r = L.mpa_plan_check_scales(h, P, tau, ctypes.byref(znl), ctypes.byref(zd), ctypes.byref(fl))
+        assert znl.value == pytest.approx(1.0 / (smax * P), rel=1e-12)
+        assert zd.value == pytest.approx(tau * tau / b2, rel=1e-12)
+        return r, fl.value
+
+    t0 = 30.0 / (2.0 * math.sqrt(math.log(2.0)))  # 30 ps intensity FWHM
+    assert check(2e-3, t0) == (0, 0)                # the benchmark link: z_nl 385 km, z_disp 8.4 km
+    assert check(1.0, t0) == (8, 1 | 2)             # 1 W: z_nl 0.77 km < z_disp and < L
+    assert check(2e-3, 3.0) == (0, 4)               # short pulses: L > z_disp only (soft)
+    assert check(0.5, 3.0)[0] == 8
+    assert L.mpa_plan_check_scales(h, -1.0, t0, None, None, None) == 1
+    L.mpa_plan_destroy(h)
 
 
 def _plan(L, fiber, N, T, Lkm, M, n, prec=0, schedule=0):

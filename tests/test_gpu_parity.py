@@ -321,7 +321,7 @@ def test_every_split_and_the_autotuned_one_match_the_oracle(M, prec):
     got = host(plan.propagate(dev(A0, prec), 0.0, 20.0))
     assert oracle.rel_l2(got, ref) < TOL[prec]
     tried = 0
-    for l in range(4, 12):
+    for l in range(0, 12):  # 0: the on-chip node transform (N = 2^14 fits in FP32)
         try:
             plan.set_split(l)
         except M.MPAError:
@@ -329,7 +329,7 @@ def test_every_split_and_the_autotuned_one_match_the_oracle(M, prec):
         tried += 1
         got = host(plan.propagate(dev(A0, prec), 0.0, 20.0))
         assert oracle.rel_l2(got, ref) < TOL[prec], l
-    assert tried >= 3 and 4 <= chosen <= 11
+    assert tried >= 3 and (chosen == 0 or 4 <= chosen <= 11)
 
 
 def test_autotuned_batch_matches_the_oracle(M):
@@ -347,3 +347,63 @@ def test_autotuned_batch_matches_the_oracle(M):
     for s, f in list(zip(specs, fields))[:3]:
         ref = oracle.mpa(s.field(), s.fiber, s.T_ps, 0.0, s.length_km, L, Mn, n_iter)
         assert oracle.rel_l2(host(f), ref) < TOL["fp32"]
+
+
+# --------------------------------- on-chip node transform (N <= 2^14 FP32)
+@pytest.mark.parametrize("prec,N,Lk,Mn,n_iter,z0", [
+    ("fp32", 1 << 8, 2.0, 5, 2, 8.0),     # smallest N: 32 node rows per tile, one ragged tile
+    ("fp32", 1 << 12, 10.0, 20, 3, 0.0),  # node on the 8-km dispersion jump
+    ("fp32", 1 << 14, 2.0, 37, 3, 4.0),   # largest FP32 size, one node per CTA
+    ("fp64", 1 << 10, 10.0, 20, 3, 0.0),
+    ("fp64", 1 << 13, 2.0, 11, 2, 8.0),   # largest FP64 size
+])
+def test_onchip_interval_matches_oracle(M, prec, N, Lk, Mn, n_iter, z0):
+    """mpa_plan_set_split(0): MPA steps 2-4 and the weight of Eq. (6) of a
+    node in one kernel (spectrum in shared memory), against the oracle."""
+    fib = small_map()
+    T = 800.0 * N / 1024
+    A0 = wdm_field(N, T, 2, 50.0, max(1, 8 * N // 1024), 30.0, 20.0, "qpsk", seed=N + Mn)
+    psi0 = oracle.fft(A0, +1)
+    ref = oracle.mpa_interval(psi0, fib, T, z0, Lk, Mn, n_iter)
+    plan = M.Plan(fib, N, T, Lk, Mn, n_iter, precision=prec)
+    plan.set_split(0)
+    got = host(plan.interval(dev(psi0, "fp64"), z0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+    assert oracle.rel_l2(got - psi0, ref - psi0) < (1e-9 if prec == "fp64" else 3e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_onchip_propagate_matches_oracle_across_amplifiers(M, prec):
+    fib = small_map()
+    N, T = 1 << 12, 3200.0
+    A0 = wdm_field(N, T, 3, 50.0, 32, 30.0, 10.0, "qpsk", seed=5)
+    ref = oracle.mpa(A0, fib, T, 0.0, 30.0, 2.0, 24, 3)
+    plan = M.Plan(fib, N, T, 2.0, 24, 3, precision=prec)
+    plan.set_split(0)
+    got = host(plan.propagate(dev(A0, prec), 0.0, 30.0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+    assert plan.status_code() == 0
+
+
+def test_onchip_small_workload_fp32(M):
+    """The 2^14-mode 4-channel link over two spans with the on-chip node
+    transform, and the autotuner's choice for it, against the oracle."""
+    w = workload("0")
+    A0 = w.field()
+    ref = oracle.mpa(A0, w.fiber, w.T_ps, 0.0, 100.0, w.mpa_L_km, w.mpa_M, w.mpa_n_iter)
+    for mode in ("onchip", "tuned"):
+        plan = M.Plan(w.fiber, w.N, w.T_ps, w.mpa_L_km, w.mpa_M, w.mpa_n_iter, precision="fp32")
+        if mode == "onchip":
+            plan.set_split(0)
+        else:
+            plan.autotune()
+        got = host(plan.propagate(dev(A0, "fp32"), 0.0, 100.0))
+        assert oracle.rel_l2(got, ref) < TOL["fp32"], mode
+
+
+def test_onchip_split_is_rejected_where_n_does_not_fit(M):
+    fib = small_map()
+    with pytest.raises(M.MPAError):
+        M.Plan(fib, 1 << 15, 800.0 * 32, 2.0, 4, 2, precision="fp32").set_split(0)
+    with pytest.raises(M.MPAError):
+        M.Plan(fib, 1 << 14, 800.0 * 16, 2.0, 4, 2, precision="fp64").set_split(0)

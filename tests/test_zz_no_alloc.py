@@ -3,12 +3,14 @@ memory (no workspace argument; the library's own static scratch is used).
 
 Called through the C ABI and compared with mpa_fft (caller-provided
 workspace) on two calls in a row, within the FFT parity tolerance used by the
-other GPU tests.  This file is collected last on purpose."""
+other GPU tests, and with the FP64 oracle's transform of the same input.
+This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1101_0086_gb300.workloads import random_field
 
 pytestmark = pytest.mark.gpu
@@ -40,7 +42,8 @@ def test_noalloc_matches_workspace_transform_twice(env, prec, logn, sign):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     ws = torch.empty(mpa.ss_workspace_bytes(N, prec), dtype=torch.uint8, device="cuda")
     for call in range(2):  # two calls in a row share (and reuse) the static scratch
-        x = torch.from_numpy(random_field(N, seed=100 * logn + call)).to(dt).cuda()
+        xh = random_field(N, seed=100 * logn + call)
+        x = torch.from_numpy(xh).to(dt).cuda()
         a = x.clone()
         b = x.clone()
         rc = L.mpa_fft_noalloc(N, code, sign, ctypes.c_void_p(a.data_ptr()), stream)
@@ -51,6 +54,9 @@ def test_noalloc_matches_workspace_transform_twice(env, prec, logn, sign):
         torch.cuda.synchronize()
         got, ref = a.cpu().numpy(), b.cpu().numpy()
         assert rel_l2(got, ref) < TOL[prec], (call, rel_l2(got, ref))
+        # the input as the GPU saw it (rounded to complex64 for FP32)
+        exact = oracle.fft(x.cpu().numpy().astype(np.complex128), sign)
+        assert rel_l2(got.astype(np.complex128), exact) < TOL[prec], (call, rel_l2(got, exact))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
