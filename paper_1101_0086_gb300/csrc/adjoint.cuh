@@ -605,16 +605,14 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
                 tr[l] = a;
                 const T pw = a.x * a.x + a.y * a.y;
                 T sn, cs;
-                if constexpr (sizeof(T) == 4) sincosf(p.rot * pw, &sn, &cs);
-                else sincos(p.rot * pw, &sn, &cs);
+                sincos_kerr(p.rot * pw, &sn, &cs);
                 vm[q][r] = cmul(a, mkc(cs, sn));
             } else {
                 const C gy = cscale(vm[q][r], p.inv_n);
                 const C t = tr[l];
                 const T pw = t.x * t.x + t.y * t.y;
                 T sn, cs;
-                if constexpr (sizeof(T) == 4) sincosf(p.rot * pw, &sn, &cs);
-                else sincos(p.rot * pw, &sn, &cs);
+                sincos_kerr(p.rot * pw, &sn, &cs);
                 const C e = mkc(cs, sn);
                 const C y = cmul(t, e);
                 const T c = -im_conj_mul(gy, y);

@@ -111,6 +111,12 @@ template <typename T> __device__ __forceinline__ void kahan_add(T& s, T& c, T v)
 #ifndef MPA_L2PF_KC
 #define MPA_L2PF_KC 0
 #endif
+// the forward column pass (V_j, MPA_POST) reads what the row pass just
+// wrote; one wave ahead it gains 3.7 % (3815 -> 3957 GB/s on the 2^20 link,
+// split 2^12 x 2^8) while the inverse pass loses 6.6 % with it
+#ifndef MPA_L2PF_KC_POST
+#define MPA_L2PF_KC_POST 304
+#endif
 #ifndef MPA_L2PF_KR
 #define MPA_L2PF_KR 304
 #endif
@@ -196,8 +202,9 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         }
     }
 
-    if constexpr (FAST && MPA_L2PF_KC > 0) {
-        const long long tb = (long long)blockIdx.x + MPA_L2PF_KC;
+    constexpr int L2PF = MODE == KC_MPA_POST ? MPA_L2PF_KC_POST : MPA_L2PF_KC;
+    if constexpr (FAST && L2PF > 0) {
+        const long long tb = (long long)blockIdx.x + L2PF;
         if (tb < (long long)gridDim.x) {
             // the first node's columns of that tile (all of it when G <= N1)
             const long long col = tb * G;
@@ -378,8 +385,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
                     a = cscale(a, pw);  // |A|^2 A (MPA step 4)
                 } else {
                     T sn, cs;  // A exp(i s |A|^2), the nonlinear step of Eq. (4)
-                    if constexpr (sizeof(T) == 4) sincosf(p.rot * pw, &sn, &cs);
-                    else sincos(p.rot * pw, &sn, &cs);
+                    sincos_kerr(p.rot * pw, &sn, &cs);
                     a = cmul(a, mkc(cs, sn));
                 }
                 vm[q][r] = a;
@@ -568,11 +574,19 @@ struct KCWParams {
     KCWJob job[8];  // one per Picard level (n_iter <= 8)
 };
 
+// Tile of the wavefront column pass: MPA_KCW_TE elements (at least 4
+// columns); the running sums and compensations take 16 bytes per element of
+// shared memory, so 4096-element tiles (about 102 KB with the transform
+// tile) let two CTAs share an SM and 8192-element ones (about 200 KB) one.
+#ifndef MPA_KCW_TE
+#define MPA_KCW_TE 4096
+#endif
+#ifndef MPA_KCW_MINB
+#define MPA_KCW_MINB 2
+#endif
 template <int L> struct KCWGeom {
     typedef Tiling<float, 2> P;
-    // tiles of at most 8192 elements (32- or 64-byte row segments): the
-    // running sums and compensations take 16 bytes per element of shared memory
-    static constexpr int G = (8192 / L) > 4 ? (8192 / L) : 4, TE = G * L, NT = TE / P::E;
+    static constexpr int G = (MPA_KCW_TE / L) > 4 ? (MPA_KCW_TE / L) : 4, TE = G * L, NT = TE / P::E;
     static constexpr int OSH = 5, OLO = L < 32 ? L : 32, OHI = L > 32 ? L / 32 : 1;
     // float2 offset of the running sums (float4 per element): rounded up to
     // an even count so the array starts on a 16-byte boundary
@@ -731,7 +745,8 @@ __device__ __forceinline__ void kcw_job(const KCWParams& p, const KCWJob& job, f
 }
 
 template <int L>
-__global__ void __launch_bounds__(KCWGeom<L>::NT, 1) kcw_kernel(const KCWParams p) {
+__global__ void __launch_bounds__(KCWGeom<L>::NT, KCWGeom<L>::NT <= 256 ? MPA_KCW_MINB : 1)
+    kcw_kernel(const KCWParams p) {
     typedef float2 C;
     typedef KCWGeom<L> Gm;
     typedef Tiling<float, 2> P;

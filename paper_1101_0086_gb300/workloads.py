@@ -194,16 +194,25 @@ def _wl0() -> Workload:
 
 def _wl1() -> Workload:
     # 16 ch @ 50 GHz, 1024 QPSK symbols, 30 ps FWHM, 2 mW, N=2^20, 40 spans (2000 km);
-    # MPA: L = 5 km, M = 142 (dz = 0.05/sqrt(2) km), n_tot = 2, the fewest
-    # iterations whose error over a span stays below the split-step's at dz = 0.05 km
+    # MPA: L = 5 km, n_tot = 2, M = 125 (dz = 0.04 km): the equal-accuracy
+    # choice over the first two spans against a FP64 split-step at dz/4, dz/8
+    # with Richardson (SS at dz = 0.05 km: 1.00e-2; MPA n_tot = 2 at M = 100,
+    # 110, 120, 130, 142: 1.06e-2, 1.03e-2, 9.8e-3, 8.5e-3, 7.2e-3; reference
+    # uncertainty 2.5e-4), so the coarsest M that stays below the split-step's
+    # error with a margin of several reference uncertainties
     return Workload("wdm16_qpsk_n2p20_2000km", 1 << 20, 102400.0, 16, 50.0, 1024, 30.0, 2.0, "qpsk", 1,
-                    dm_map(40), 0.05, 5.0, 142, 2)
+                    dm_map(40), 0.05, 5.0, 125, 2)
 
 
 def _wl2() -> Workload:
-    # 64 ch @ 25 GHz, 2048 QPSK symbols at 10 GBd, N=2^24, beta3=0.08, 100 spans (5000 km)
+    # 64 ch @ 25 GHz, 2048 QPSK symbols at 10 GBd, N=2^24, beta3=0.08, 100 spans (5000 km);
+    # MPA: L = 5 km, M = 142, n_tot = 4.  Over the first two spans against FP64
+    # split-steps at dz/4, dz/8 (Richardson) the split-step at dz = 0.05 km
+    # errs 6.7e-2 and the MPA at n_tot = 3 1.04e-1 whatever M (142, 213, 284:
+    # 1.04e-1, 9.9e-2, 9.6e-2: the Picard iteration, contraction about 0.43 on
+    # this 64-channel link, dominates), at n_tot = 4 5.5e-2
     return Workload("wdm64_qpsk_n2p24_5000km", 1 << 24, 204800.0, 64, 25.0, 2048, 30.0, 2.0, "qpsk", 2,
-                    dm_map(100, beta3=0.08), 0.05, 5.0, 142, 3)
+                    dm_map(100, beta3=0.08), 0.05, 5.0, 142, 4)
 
 
 def _wl4() -> Workload:

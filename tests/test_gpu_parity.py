@@ -202,7 +202,7 @@ def test_small_workload_fp32(M):
 
 def test_bench_workload_sampled_interval_fp32(M):
     """The N = 2^20, 16-channel workload in the benchmark's launch
-    configuration (L = 5 km, M = 142, the workload's n_tot): one full
+    configuration (L = 5 km, the workload's M and n_tot): one full
     interval against the oracle, starting from the seeded field's spectrum at
     z = 45 km."""
     w = workload("1")
