@@ -153,9 +153,12 @@ MPA_API int mpa_plan_autotune(mpa_plan* plan, mpa_stream stream, int32_t* log2_n
  * earlier mpa_plan_autotune chose).  MPA_ERR_UNSUPPORTED_N if the passes or
  * the reverse-mode tiling do not support it; a WAVEFRONT plan accepts only
  * its current split.  log2_n2 = 0 selects the on-chip node transform where N
- * allows it (N <= 2^14 FP32, 2^13 FP64): MPA steps 2-4 and the weight of
- * Eq. (6) for a node in one kernel, the spectrum held in shared memory
- * (mpa_plan_autotune reports this choice as 0 and tries it first).
+ * allows it (N <= 2^16 FP32, 2^13 FP64): MPA steps 2-4 and the weight of
+ * Eq. (6) for a node in one kernel, the spectrum held in shared memory (one
+ * CTA up to 2^14 FP32 / 2^13 FP64; for FP32 2^15 and 2^16 a cluster of 2 or
+ * 4 CTAs exchanging through distributed shared memory).  It is the default
+ * of FP32 plans up to 2^14; mpa_plan_autotune tries it first and reports it
+ * as 0.
  * Host-only. */
 MPA_API int mpa_plan_set_split(mpa_plan* plan, int32_t log2_n2);
 

@@ -208,7 +208,7 @@ int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_
             b->groups.emplace_back();
             split_n(k.N, precision, &b->groups.back().sp);
             // on-chip node transforms by default where an FP32 spectrum fits a CTA
-            b->groups.back().sp.onchip = precision == MPA_FP32 && onchip_ok(k.N, MPA_FP32);
+            b->groups.back().sp.onchip = precision == MPA_FP32 && onchip_ok(k.N, MPA_FP32) && k.N <= (1ll << 14);
         }
         b->groups.back().links.push_back(i);
     }

@@ -40,6 +40,8 @@ cudaError_t kn_launch<float>(int logL, const KNParams<float>& p, cudaStream_t st
         case 12: return kn_one<4096>(p, st);
         case 13: return kn_one<8192>(p, st);
         case 14: return kn_one<16384>(p, st);
+        case 15:
+        case 16: return knc_launch(logL, p, st);
     }
     return cudaErrorInvalidValue;
 }

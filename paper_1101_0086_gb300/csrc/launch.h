@@ -66,10 +66,13 @@ template <typename T> constexpr int kr_log_max() { return sizeof(T) == 4 ? 14 : 
 
 template <typename T> cudaError_t kc_launch(int mode, int logL, const KCParams<T>& p, cudaStream_t st);
 template <typename T> cudaError_t kr_launch(int mode, int logL, const KRParams<T>& p, cudaStream_t st);
-// On-chip whole node transform for N = 2^logL, 2^8 <= N <= 2^kn_log_max.
+// On-chip whole node transform for N = 2^logL, 2^8 <= N <= 2^kn_log_max:
+// one CTA per node up to 2^14 (FP32) / 2^13 (FP64), a cluster of 2 or 4 CTAs
+// over distributed shared memory for FP32 2^15 and 2^16 (knc_launch).
 constexpr int KN_LOG_MIN = 8;
-template <typename T> constexpr int kn_log_max() { return sizeof(T) == 4 ? 14 : 13; }
+template <typename T> constexpr int kn_log_max() { return sizeof(T) == 4 ? 16 : 13; }
 template <typename T> cudaError_t kn_launch(int logL, const KNParams<T>& p, cudaStream_t st);
+cudaError_t knc_launch(int logL, const KNParams<float>& p, cudaStream_t st);
 template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int links, cudaStream_t st);
 template <typename T> cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long C, cudaStream_t st);
 template <typename T> cudaError_t to_state_launch(const cx<T>* in, double2* state, cx<T>* copy, long long N, cudaStream_t st);

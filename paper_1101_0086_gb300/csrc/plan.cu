@@ -369,10 +369,11 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
         delete p;
         return rc;
     }
-    // FP32 plans whose spectra fit a CTA use the on-chip node transform by
-    // default (1.75x the three passes on the 2^14-mode link); FP64 plans keep
-    // the four-step passes unless set or tuned
-    p->sp.onchip = prm->precision == MPA_FP32 && prm->schedule != MPA_SCHEDULE_WAVEFRONT && onchip_ok(prm->N, MPA_FP32);
+    // FP32 plans whose spectra fit one CTA use the on-chip node transform by
+    // default (1.75x the three passes on the 2^14-mode link); the cluster
+    // form (2^15, 2^16) and FP64 plans are chosen by set_split(0) or tuning
+    p->sp.onchip = prm->precision == MPA_FP32 && prm->schedule != MPA_SCHEDULE_WAVEFRONT && onchip_ok(prm->N, MPA_FP32) &&
+                   prm->N <= (1ll << 14);
     p->T = prm->T_ps;
     p->L = prm->L_km;
     p->M = prm->M;

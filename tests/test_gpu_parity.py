@@ -404,6 +404,34 @@ def test_onchip_small_workload_fp32(M):
 def test_onchip_split_is_rejected_where_n_does_not_fit(M):
     fib = small_map()
     with pytest.raises(M.MPAError):
-        M.Plan(fib, 1 << 15, 800.0 * 32, 2.0, 4, 2, precision="fp32").set_split(0)
+        M.Plan(fib, 1 << 17, 800.0 * 128, 2.0, 4, 2, precision="fp32").set_split(0)
     with pytest.raises(M.MPAError):
         M.Plan(fib, 1 << 14, 800.0 * 16, 2.0, 4, 2, precision="fp64").set_split(0)
+
+
+@pytest.mark.parametrize("logn,Lk,Mn,n_iter,z0", [
+    (15, 2.0, 13, 3, 8.0),   # a cluster of 2 CTAs per node, interval in the +85 segment
+    (16, 10.0, 20, 2, 0.0),  # a cluster of 4 CTAs per node, node on the 8-km jump
+])
+def test_cluster_onchip_interval_matches_oracle(M, logn, Lk, Mn, n_iter, z0):
+    """FP32 N = 2^15 and 2^16 through the cluster form of the on-chip node
+    transform (slices exchanged through distributed shared memory)."""
+    fib = small_map()
+    N = 1 << logn
+    T = 800.0 * N / 1024
+    A0 = wdm_field(N, T, 3, 50.0, 8 * N // 1024, 30.0, 20.0, "qpsk", seed=N + Mn)
+    psi0 = oracle.fft(A0, +1)
+    ref = oracle.mpa_interval(psi0, fib, T, z0, Lk, Mn, n_iter)
+    plan = M.Plan(fib, N, T, Lk, Mn, n_iter, precision="fp32")
+    plan.set_split(0)
+    got = host(plan.interval(dev(psi0, "fp64"), z0))
+    assert oracle.rel_l2(got, ref) < TOL["fp32"]
+    assert oracle.rel_l2(got - psi0, ref - psi0) < 3e-3
+    # a whole propagation across an amplifier, against the four-step passes
+    a = dev(A0, "fp32")
+    plan.propagate(a, 0.0, 20.0)
+    four = M.Plan(fib, N, T, Lk, Mn, n_iter, precision="fp32")
+    four.set_split(logn // 2)
+    b = dev(A0, "fp32")
+    four.propagate(b, 0.0, 20.0)
+    assert oracle.rel_l2(host(a), host(b)) < 1e-5
