@@ -66,6 +66,9 @@ def parse():
                     help="km of the 2^24-mode 64-channel link timed as a second leg of the default run (0: off)")
     ap.add_argument("--no-full-length", dest="full_length", action="store_false",
                     help="skip the FP64 GPU MPA over the whole timed length (FP32 rounding drift)")
+    ap.add_argument("--only-comparator", action="store_true",
+                    help="time only the split-step comparator (FP64 and FP32) over --ss-km of the workload "
+                         "(profiling of its kernels)")
     return ap.parse_args()
 
 
@@ -142,12 +145,12 @@ def peaks():
 
 
 def source_hash() -> str:
-    """Hash of the sources that define the FP32 column- and row-pass kernels
-    whose ncu DRAM counters the roofline line quotes (kernel templates,
-    device helpers and the FP32 instantiations)."""
+    """Hash of the sources that define the FP32 kernels whose ncu DRAM
+    counters the roofline line quotes (kernel templates, device helpers and
+    the FP32 instantiations of the column, row and on-chip passes)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1101_0086_gb300", "csrc")
-    for f in ("device.cuh", "kernels.cuh", "kc_f32.cu", "kr_f32.cu"):
+    for f in ("device.cuh", "kernels.cuh", "knc.cuh", "kc_f32.cu", "kr_f32.cu", "kn_f32.cu", "knc_f32.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -417,6 +420,12 @@ def run_mpa(args, world, rank, local):
     km = w.length_km if args.km is None else float(args.km)
     N = w.N
     stream = torch.cuda.current_stream()
+    if args.only_comparator:
+        fp64_peak = mpa.alu_peak("fp64", stream)
+        print(json.dumps({"workload": w.name, "N": N, "fp64_peak_tflops": fp64_peak / 1e12,
+                          "comparator": ss_comparator(mpa, torch, w, args.ss_km, args.ss_km, stream, fp64_peak)}),
+              flush=True)
+        return 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     clocks = Clocks(torch.cuda.current_device())
 

@@ -316,6 +316,7 @@ int mpa_batch_status(mpa_batch* b, mpa_stream stream) {
 }
 
 int mpa_batch_propagate(mpa_batch* b, int32_t use_graph, mpa_stream stream) {
+    NvtxRange nv("mpa_batch_propagate");
     if (!b) return MPA_ERR_INVALID_ARG;
     if (!b->ws) return MPA_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

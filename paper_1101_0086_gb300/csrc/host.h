@@ -8,11 +8,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 #include "mpa.h"
 
 namespace mpa {
 namespace host {
+
+// NVTX range around an entry point or an interval (header-only NVTX3: a few
+// nanoseconds when no profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Records the CUDA error string for mpa_last_cuda_error.
 int cuda_fail(cudaError_t e);

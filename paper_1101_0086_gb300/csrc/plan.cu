@@ -278,6 +278,7 @@ int propagate_t(mpa_plan* p, void* field, double z_from, double z_to, cudaStream
     if (rc) return rc;
     MPA_TRY(to_state_launch<T>(psi, state, sizeof(T) == 4 ? psi0c : nullptr, s.N, st));
     for (long q = 0; q < n_int; ++q) {
+        NvtxRange nvq("interval");
         rc = p->wf ? run_interval_wf(p, types[(size_t)q], std::exp((double)amps[(size_t)q] * p->map.z_a * p->map.gamma),
                                      nullptr, st)
                    : run_interval<T>(p, types[(size_t)q], amps[(size_t)q], 1, nullptr, st);
@@ -521,6 +522,7 @@ int mpa_plan_set_split(mpa_plan* p, int32_t log2_n2) {
 }
 
 int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
+    NvtxRange nv("mpa_plan_autotune");
     if (!p) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
     if (log2_n2) *log2_n2 = p->sp.onchip ? 0 : p->sp.logN2;
@@ -576,6 +578,7 @@ int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
 }
 
 int mpa_propagate(mpa_plan* p, void* field, double z_from_km, double z_to_km, mpa_stream stream) {
+    NvtxRange nv("mpa_propagate");
     if (!p || !field) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -584,6 +587,7 @@ int mpa_propagate(mpa_plan* p, void* field, double z_from_km, double z_to_km, mp
 }
 
 int mpa_interval(mpa_plan* p, const void* psi0, void* psiM, double z0_km, mpa_stream stream) {
+    NvtxRange nv("mpa_interval");
     if (!p || !psi0 || !psiM) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -655,6 +659,7 @@ int ss_workspace_size(int64_t N, int32_t precision, size_t* bytes) {
 
 int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision, void* field,
                  double z_from_km, double z_to_km, void* workspace, size_t ws_bytes, mpa_stream stream) {
+    NvtxRange nv("ss_propagate");
     if (!map || !field || !workspace || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
     if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
     HostMap m;
