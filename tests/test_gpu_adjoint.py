@@ -262,7 +262,11 @@ def test_ss_adjoint_matches_oracle(M, prec, logn, ckpt):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_ss_energy_gradient_is_exact(M, prec):
     """gamma = 0, no amplifiers: l = sum |A_out|^2 = sum |A_in|^2, so g_A = 2 A
-    and the parameter gradients vanish (to rounding)."""
+    and the parameter gradients vanish (to rounding).  The FP32 bound is the
+    spec FP32 tolerance 1e-4: the forward and reverse passes take 40
+    split-steps each, four 2^13-point FP32 transforms per step, and their
+    rounding (about 1e-7 per transform, growing with the step count) reaches
+    a few 1e-6 here, above the 1e-5 first used for this test."""
     import torch
     N = 1 << 13
     A0, T = toy_field(N, seed=8)
