@@ -66,6 +66,10 @@ def parse():
                     help="km of the 2^24-mode 64-channel link timed as a second leg of the default run (0: off)")
     ap.add_argument("--no-full-length", dest="full_length", action="store_false",
                     help="skip the FP64 GPU MPA over the whole timed length (FP32 rounding drift)")
+    ap.add_argument("--batch-log2n", default="12,18",
+                    help="workload 3: range of log2 N of the batched links (the default is the 256-link batch)")
+    ap.add_argument("--persistent", default="auto", choices=["auto", "on", "off"],
+                    help="workload 3: the persistent work-queue kernel for the small groups (auto: the autotuner's choice)")
     ap.add_argument("--only-comparator", action="store_true",
                     help="time only the split-step comparator (FP64 and FP32) over --ss-km of the workload "
                          "(profiling of its kernels)")
@@ -594,12 +598,15 @@ def run_batch(args, world, rank, local):
     if rank == 0:
         B.build()
     mpa.lib()
-    specs = batch_links()
+    lo, hi = (int(x) for x in args.batch_log2n.split(","))
+    specs = batch_links() if (lo, hi) == (12, 18) else batch_links(log2_n=(lo, hi))
     L, Mn, nit = 5.0, 142, 3
     src = [torch.from_numpy(s.field().astype(np.complex64)).cuda() for s in specs]
     fields = [x.clone() for x in src]
     batch = mpa.Batch([(s.fiber, s.T_ps, s.length_km, f) for s, f in zip(specs, fields)], L, Mn, nit, "fp32")
-    batch.autotune(torch.cuda.current_stream())  # per-group four-step split, before the timed region
+    batch.autotune(torch.cuda.current_stream())  # per-group node transform, before the timed region
+    if args.persistent != "auto":
+        batch.set_persistent(args.persistent == "on")
     units = float(sum(s.N * s.length_km for s in specs))
     stream = torch.cuda.current_stream()
 
@@ -646,7 +653,8 @@ def run_batch(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch256_n2p12-2p18", "links": len(specs), "mode_km_per_step": units,
+            "config": {"workload": f"batch{len(specs)}_n2p{lo}-2p{hi}", "links": len(specs), "mode_km_per_step": units,
+                       "persistent": args.persistent,
                        "L_km": L, "M": Mn, "n_iter": nit, "method": "MPA FP32, batched links, CUDA graph",
                        "l2": "inputs reset between steps (working set > L2)"},
             "sequential_subset": {"value": seq, "unit": UNIT, "links": len(sub)},

@@ -51,7 +51,8 @@ enum {
     MPA_ERR_GRID = 5,          /* z-grid inconsistent with the fiber map (see each call) */
     MPA_ERR_NONFINITE = 6,     /* a NaN/Inf was produced (mpa_plan_status, mpa_batch_status) */
     MPA_ERR_DIVERGED = 7,      /* the Picard iteration did not contract (mpa_plan_status, mpa_batch_status) */
-    MPA_ERR_SCALES = 8         /* scales outside the weakly nonlinear regime (mpa_plan_check_scales) */
+    MPA_ERR_SCALES = 8,        /* scales outside the weakly nonlinear regime (mpa_plan_check_scales) */
+    MPA_ERR_TIMEOUT = 9        /* a wait of the persistent batch kernel ran out (mpa_batch_status) */
 };
 
 enum { MPA_FP32 = 0, MPA_FP64 = 1 };
@@ -277,10 +278,26 @@ MPA_API int mpa_batch_autotune(mpa_batch* batch, mpa_stream stream);
  * calls replay the graph on `stream`.  Do not call it while `stream` is
  * being captured by the caller. */
 MPA_API int mpa_batch_propagate(mpa_batch* batch, int32_t use_graph, mpa_stream stream);
-/* mpa_plan_status for all links of the batch: MPA_ERR_NONFINITE or
- * MPA_ERR_DIVERGED if any link produced it since the last call (synchronises
- * the stream, clears the flags), else MPA_OK. */
+/* mpa_plan_status for all links of the batch: MPA_ERR_TIMEOUT (a wait of
+ * the persistent kernel ran out: the results are incomplete), else
+ * MPA_ERR_NONFINITE or MPA_ERR_DIVERGED if any link produced it since the
+ * last call (synchronises the stream, clears the flags), else MPA_OK. */
 MPA_API int mpa_batch_status(mpa_batch* batch, mpa_stream stream);
+
+/* Groups of FP32 links on the single-CTA on-chip node transform (N <= 2^14)
+ * can run every interval and Picard iteration of all their links in ONE
+ * persistent launch: a work queue over (link, interval, iteration, node
+ * block) and (link, interval, iteration, frequency block), where the CTA
+ * that finishes a link's phase enqueues the next (the scan after the nodes,
+ * the next iteration or interval after the scan), so links advance
+ * independently.  The only waits are on queue slots, bounded by the wait
+ * limit (default 2^24 polls, about 2 s); a wait that runs out ends the
+ * kernel with MPA_ERR_TIMEOUT in mpa_batch_status.  mpa_batch_autotune
+ * chooses per group between it and per-pass launches; this call sets it
+ * for every eligible group (on != 0) or none.  Both drop a captured graph.
+ * The paper has no counterpart (the batching of independent problems). */
+MPA_API int mpa_batch_set_persistent(mpa_batch* batch, int32_t on);
+MPA_API int mpa_batch_set_wait_limit(mpa_batch* batch, int64_t polls);
 MPA_API void mpa_batch_destroy(mpa_batch* batch);
 
 /* Symmetric split-step of Eq. (4) on the GPU: half linear step, then

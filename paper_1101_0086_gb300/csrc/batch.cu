@@ -12,6 +12,7 @@
 #include <new>
 
 #include "host.h"
+#include "kp.cuh"
 
 using namespace mpa;
 using namespace mpa::host;
@@ -38,7 +39,18 @@ struct Group {
     long n_int = 0;
     size_t off_psi = 0, off_state = 0, off_psi0c = 0, off_nodes = 0, off_loff = 0, off_gain = 0, off_err = 0;
     size_t off_conv = 0, off_dprev = 0;  // Picard increment check: ConvState and D at node M per link
+    // persistent work-queue kernel (FP32 groups on the single-CTA on-chip transform)
+    bool persistent = false;
+    unsigned int q_cap = 0;
+    size_t off_qtask = 0, off_qseq = 0, off_ctr = 0, off_nint = 0;
+    std::vector<int> link_nint;  // intervals per link (group order)
 };
+
+// Whether the group can run on the persistent kernel: FP32 spectra that fit
+// one CTA, the on-chip node transform chosen.
+bool persistent_ok(const Group& g, int prec) {
+    return prec == MPA_FP32 && g.sp.onchip && g.sp.N <= (1ll << 14);
+}
 
 Monitor group_monitor(unsigned char* ws, const Group& g) {
     Monitor m{};
@@ -53,6 +65,7 @@ Monitor group_monitor(unsigned char* ws, const Group& g) {
 struct mpa_batch {
     double L;
     int M, n_iter, prec;
+    long long spin_limit = 1ll << 24;  // polls of a persistent-kernel wait (about 2 s)
     size_t csize;
     std::vector<Link> links;
     std::vector<Group> groups;
@@ -81,6 +94,41 @@ int link_type(const Link& k, double L, double z0, int* t) {
     return MPA_OK;
 }
 
+// All intervals (at most q_limit per link) of a group on the persistent
+// kernel, from the states and working copies in the workspace.
+int run_persistent(mpa_batch* b, Group& g, int q_limit, cudaStream_t st) {
+    const Split& s = g.sp;
+    const int n = (int)g.links.size();
+    KPParams k{};
+    k.psi = reinterpret_cast<float2*>(b->ws + g.off_psi);
+    k.psi0c = reinterpret_cast<float2*>(b->ws + g.off_psi0c);
+    k.state = reinterpret_cast<double2*>(b->ws + g.off_state);
+    k.nodes = reinterpret_cast<const NodeC*>(b->ws + g.off_nodes);
+    k.loff = reinterpret_cast<const int*>(b->ws + g.off_loff);
+    k.gain = reinterpret_cast<const double*>(b->ws + g.off_gain);
+    k.conv = reinterpret_cast<ConvState*>(b->ws + g.off_conv);
+    k.dprev = reinterpret_cast<float2*>(b->ws + g.off_dprev);
+    k.err = reinterpret_cast<unsigned int*>(b->ws + g.off_err);
+    k.n_int = reinterpret_cast<const int*>(b->ws + g.off_nint);
+    k.N = s.N;
+    k.M = b->M;
+    k.n_iter = b->n_iter;
+    k.n_links = n;
+    k.nb = (b->M + 1 + KN_TILE_ROWS(s.logN) - 1) / KN_TILE_ROWS(s.logN);
+    k.ns = (int)(s.N / KN_THREADS(s.logN));
+    k.q_limit = q_limit;
+    k.inv_n = (float)(1.0 / (double)s.N);
+    k.floor_rel = kDivergenceFloor;
+    k.q_task = reinterpret_cast<unsigned long long*>(b->ws + g.off_qtask);
+    k.q_seq = reinterpret_cast<unsigned int*>(b->ws + g.off_qseq);
+    k.q_cap = g.q_cap;
+    k.ctr = reinterpret_cast<unsigned int*>(b->ws + g.off_ctr);
+    k.spin_limit = b->spin_limit;
+    MPA_TRY(kp_init_launch(k.q_seq, k.q_cap, k.ctr, 3 + n, st));
+    MPA_TRY(kp_launch(s.logN, k, st));
+    return MPA_OK;
+}
+
 template <typename T>
 int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
     const Split& s = g.sp;
@@ -93,6 +141,9 @@ int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
     const int* loff = reinterpret_cast<const int*>(b->ws + g.off_loff);
     const double* gain = reinterpret_cast<const double*>(b->ws + g.off_gain);
     const Monitor mon = group_monitor(b->ws, g);
+    // a fresh increment check per propagation (a run that ended early, e.g.
+    // on a timeout, must not leave a half-counted level behind)
+    MPA_TRY(cudaMemsetAsync(mon.conv, 0, (size_t)n * sizeof(ConvState), st));
     // A_hat(0) = F[A] for every link (its node-0 buffer is the scratch)
     for (int i = 0; i < n; ++i) {
         cx<T>* scratch = psi + (long long)i * (M + 1) * N;
@@ -101,10 +152,16 @@ int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
         MPA_TRY(to_state_launch<T>(scratch, state + (long long)i * N, sizeof(T) == 4 ? psi0c + (long long)i * N : nullptr,
                                    N, st));
     }
-    for (long q = 0; q < g.n_int; ++q) {
-        int rc = mpa_levels<T>(s, M, b->n_iter, g.active[(size_t)q], psi, psi0c, state, nodes, loff + (size_t)q * n,
-                               gain + (size_t)q * n, mon, 1, nullptr, st);
+    if (g.persistent && persistent_ok(g, b->prec)) {
+        // every interval of every link in one launch
+        int rc = run_persistent(b, g, 1 << 30, st);
         if (rc) return rc;
+    } else {
+        for (long q = 0; q < g.n_int; ++q) {
+            int rc = mpa_levels<T>(s, M, b->n_iter, g.active[(size_t)q], psi, psi0c, state, nodes,
+                                   loff + (size_t)q * n, gain + (size_t)q * n, mon, 1, nullptr, st);
+            if (rc) return rc;
+        }
     }
     for (int i = 0; i < n; ++i) {
         cx<T>* scratch = psi + (long long)i * (M + 1) * N;
@@ -272,6 +329,23 @@ int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_
         off = align256(off + (size_t)n * sizeof(ConvState));
         g.off_dprev = off;
         if (n_iter > 1) off = align256(off + (size_t)n * N * sizeof(float2));
+        g.link_nint.resize((size_t)n);
+        for (int i = 0; i < n; ++i) g.link_nint[(size_t)i] = (int)b->links[(size_t)g.links[(size_t)i]].n_int;
+        if (precision == MPA_FP32 && g.sp.N <= (1ll << 14) && g.sp.N >= (1ll << KN_LOG_MIN)) {
+            // queue of the persistent kernel: one phase of tasks per link, plus slack
+            const long long rows = KN_TILE_ROWS(g.sp.logN), thr = KN_THREADS(g.sp.logN);
+            const long long nb = (M + 1 + rows - 1) / rows, ns = (long long)N / thr;
+            g.q_cap = (unsigned)((long long)n * (nb > ns ? nb : ns) + 4096);
+            g.off_qtask = off;
+            off = align256(off + (size_t)g.q_cap * sizeof(unsigned long long));
+            g.off_qseq = off;
+            off = align256(off + (size_t)g.q_cap * sizeof(unsigned int));
+            g.off_ctr = off;
+            off = align256(off + (size_t)(3 + n) * sizeof(unsigned int));
+            g.off_nint = off;
+            off = align256(off + (size_t)n * sizeof(int));
+            g.persistent = g.sp.onchip;
+        }
     }
     b->ws_need = off;
     *out = b;
@@ -295,6 +369,9 @@ int mpa_batch_set_workspace(mpa_batch* b, void* ws, size_t bytes) {
         MPA_TRY(cudaMemcpy(b->ws + g.off_gain, g.gain.data(), g.gain.size() * sizeof(double), cudaMemcpyHostToDevice));
         MPA_TRY(cudaMemset(b->ws + g.off_err, 0, sizeof(unsigned int)));
         MPA_TRY(cudaMemset(b->ws + g.off_conv, 0, g.links.size() * sizeof(ConvState)));
+        if (g.q_cap)
+            MPA_TRY(cudaMemcpy(b->ws + g.off_nint, g.link_nint.data(), g.link_nint.size() * sizeof(int),
+                               cudaMemcpyHostToDevice));
     }
     return MPA_OK;
 }
@@ -312,7 +389,24 @@ int mpa_batch_status(mpa_batch* b, mpa_stream stream) {
         all |= h[i];
         MPA_TRY(cudaMemsetAsync(b->ws + b->groups[i].off_err, 0, sizeof(unsigned int), st));
     }
-    return (all & ERR_NONFINITE) ? MPA_ERR_NONFINITE : (all & ERR_DIVERGED) ? MPA_ERR_DIVERGED : MPA_OK;
+    return (all & ERR_TIMEOUT) ? MPA_ERR_TIMEOUT
+         : (all & ERR_NONFINITE) ? MPA_ERR_NONFINITE
+         : (all & ERR_DIVERGED) ? MPA_ERR_DIVERGED
+                                : MPA_OK;
+}
+
+int mpa_batch_set_persistent(mpa_batch* b, int32_t on) {
+    if (!b) return MPA_ERR_INVALID_ARG;
+    release_graph(b);  // the captured launches follow the old choice
+    for (auto& g : b->groups) g.persistent = on != 0 && g.q_cap != 0;
+    return MPA_OK;
+}
+
+int mpa_batch_set_wait_limit(mpa_batch* b, int64_t polls) {
+    if (!b || polls < 1) return MPA_ERR_INVALID_ARG;
+    b->spin_limit = polls;
+    release_graph(b);  // the limit is a launch argument of the captured kernels
+    return MPA_OK;
 }
 
 int mpa_batch_propagate(mpa_batch* b, int32_t use_graph, mpa_stream stream) {
@@ -429,6 +523,24 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
             }
         }
         g.sp = rc == MPA_OK ? best : keep;
+        if (rc == MPA_OK && g.q_cap && persistent_ok(g, b->prec)) {
+            // the persistent kernel against the per-pass launches of the same
+            // node transform, on the group's first interval
+            float ms_p = 0.f;
+            for (int rep = 0; rep < 2 && rc == MPA_OK; ++rep) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) {
+                    rc = cuda_fail(cudaGetLastError());
+                    break;
+                }
+                rc = run_persistent(b, g, 1, st);
+                if (rc == MPA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms_p, e0, e1) != cudaSuccess))
+                    rc = cuda_fail(cudaGetLastError());
+            }
+            g.persistent = rc == MPA_OK && ms_p < best_ms;
+        } else {
+            g.persistent = false;
+        }
         if ((cudaMemsetAsync(b->ws + g.off_err, 0, sizeof(unsigned int), st) != cudaSuccess ||
              cudaMemsetAsync(b->ws + g.off_conv, 0, (size_t)n * sizeof(ConvState), st) != cudaSuccess) &&
             rc == MPA_OK)

@@ -95,6 +95,14 @@ template <typename T, int L> struct KRGeom {
 
 __device__ __forceinline__ long long signed_k(long long k, long long N) { return k < (N >> 1) ? k : k - N; }
 
+// Global load of data another CTA of the same (persistent) kernel may have
+// written: CG = true reads through L2 only (L1 is not coherent within a
+// kernel); separate launches use ordinary loads.
+template <bool CG, class V> __device__ __forceinline__ V ldx(const V* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // Kahan-compensated s += v (c carries the lost low-order part).
 template <typename T> __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
     const T y = v - c;
@@ -456,9 +464,10 @@ template <typename T, int L> struct KNGeom {
         ((size_t)TE + (TE >> P::PSH) + 1 + TwDims<L>::NLO + TwDims<L>::NHI) * sizeof(cx<T>);
 };
 
-template <typename T, int L>
-__global__ void __launch_bounds__(KNGeom<T, L>::NT, KNGeom<T, L>::NT <= 256 ? MPA_KR_MINB : 1)
-    kn_kernel(const KNParams<T> p) {
+// The node rows row0 .. row0 + G - 1 of a launch (one tile) through steps
+// 2-4 and the weight of Eq. (6); the block's threads and shared memory.
+template <typename T, int L, bool CG>
+__device__ __forceinline__ void kn_tile(const KNParams<T>& p, long long row0, unsigned char* smem_raw) {
     typedef cx<T> C;
     typedef KNGeom<T, L> Gm;
     typedef Tiling<T, 1> P;
@@ -467,12 +476,10 @@ __global__ void __launch_bounds__(KNGeom<T, L>::NT, KNGeom<T, L>::NT <= 256 ? MP
     typedef Xform<T, L, G, NT, P::RMAX, +1, LAYOUT_ROW, P::PSH, true> XF;
     static_assert(XI::RL == XF::R0, "inverse/forward junction radix");
     constexpr bool FAST = sizeof(T) == 4;  // FP32: finite-difference phases + polynomial exp
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     C* thi = s + TE + (TE >> P::PSH) + 1;
     C* tlo = thi + TwDims<L>::NHI;
     const int tid = threadIdx.x;
-    const long long row0 = (long long)blockIdx.x * G;
 
     tw_init<T, L>(thi, tlo, tid, NT);
     __syncthreads();
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(KNGeom<T, L>::NT, KNGeom<T, L>::NT <= 256 ? MP
 #pragma unroll
         for (int r = 0; r < XI::R0; ++r) {
             const int k = j + r * (L / XI::R0);
-            C v = ok ? src[k] : mkc(T(0), T(0));
+            C v = ok ? ldx<CG>(src + k) : mkc(T(0), T(0));
             C ph;
             if constexpr (FAST) ph = expi_turns_poly(th[r]);
             else ph = expi_turns<T>(phase_q64(signed_k(k, L), nc));
@@ -538,6 +545,13 @@ __global__ void __launch_bounds__(KNGeom<T, L>::NT, KNGeom<T, L>::NT <= 256 ? MP
             dst[k] = cscale(cmul(vout[q][r], cconj(ph)), (T)nc.post);
         }
     }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(KNGeom<T, L>::NT, KNGeom<T, L>::NT <= 256 ? MPA_KR_MINB : 1)
+    kn_kernel(const KNParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    kn_tile<T, L, false>(p, (long long)blockIdx.x * KNGeom<T, L>::G, smem_raw);
 }
 
 // ------------------------------------------------------------------
@@ -831,8 +845,8 @@ template <typename T> struct ScanParams {
 // Adds this block's sums to link l's accumulators; the last block of the
 // level closes the level (comparison with the previous one, reset).
 __device__ __forceinline__ void conv_close(ConvState* cs, unsigned int* err, double d2, double p2, int level,
-                                           int last_level, double floor_rel) {
-    __shared__ double red[2][8];
+                                           int last_level, double floor_rel, unsigned nblk) {
+    __shared__ double red[2][32];  // one entry per warp (up to 1024 threads)
     __shared__ bool last_block;
     // warp sums, then the block's 8 warp sums by thread 0
 #pragma unroll
@@ -855,7 +869,7 @@ __device__ __forceinline__ void conv_close(ConvState* cs, unsigned int* err, dou
         atomicAdd(&cs->acc_d, sd);
         atomicAdd(&cs->acc_p, sp);
         __threadfence();
-        last_block = atomicAdd(&cs->count, 1u) == gridDim.x - 1;
+        last_block = atomicAdd(&cs->count, 1u) == nblk - 1;
     }
     __syncthreads();
     if (threadIdx.x == 0 && last_block) {
@@ -875,32 +889,32 @@ __device__ __forceinline__ void conv_close(ConvState* cs, unsigned int* err, dou
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
+// Frequency k of link l (one thread each; a block of consecutive
+// frequencies, nblk blocks per link).  N is a multiple of the block size (a
+// power of two >= 256), so every thread has a frequency and takes part in
+// the block reduction of the increment check.
+template <typename T, bool CG>
+__device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long long k, unsigned nblk) {
     typedef cx<T> C;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    // N is a multiple of the block size (a power of two >= 256), so every
-    // thread has a frequency and takes part in the block reduction below
-    const int l = blockIdx.y;
     const long long lo = (long long)l * p.N;
     cx<T>* psi = p.psi + lo * (p.M + 1);
-    const C v0 = psi[k];
+    const C v0 = ldx<CG>(psi + k);
     T rx = T(0.5) * v0.x, ry = T(0.5) * v0.y, cxx = T(0), cyy = T(0);
-    const C p0 = p.psi0c[lo + k];
+    const C p0 = ldx<CG>(p.psi0c + lo + k);
     C vl = v0;
     // V_j are loaded SCAN_U nodes ahead of their use (more loads in flight
     // per thread; the loads never touch a node the loop has written)
     constexpr int U = 8;
     C nxt[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) nxt[u] = (1 + u <= p.M) ? psi[(long long)(1 + u) * p.N + k] : mkc(T(0), T(0));
+    for (int u = 0; u < U; ++u) nxt[u] = (1 + u <= p.M) ? ldx<CG>(psi + (long long)(1 + u) * p.N + k) : mkc(T(0), T(0));
     for (int jb = 1; jb <= p.M; jb += U) {
         C cur[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             cur[u] = nxt[u];
             const int jn = jb + U + u;
-            nxt[u] = (jn <= p.M) ? psi[(long long)jn * p.N + k] : mkc(T(0), T(0));
+            nxt[u] = (jn <= p.M) ? ldx<CG>(psi + (long long)jn * p.N + k) : mkc(T(0), T(0));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -928,16 +942,16 @@ __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
         // Picard increment at node M against the previous level's D
         double dx = sx, dy = sy;
         if (p.level > 0) {
-            const float2 d0 = p.dprev[lo + k];
+            const float2 d0 = ldx<CG>(p.dprev + lo + k);
             dx -= (double)d0.x;
             dy -= (double)d0.y;
         }
         if (p.level < p.n_iter - 1) p.dprev[lo + k] = make_float2((float)sx, (float)sy);
         const double px = (double)p0.x - sy, py = (double)p0.y + sx;
-        conv_close(p.conv + l, p.err, dx * dx + dy * dy, px * px + py * py, p.level, p.n_iter - 1, p.floor_rel);
+        conv_close(p.conv + l, p.err, dx * dx + dy * dy, px * px + py * py, p.level, p.n_iter - 1, p.floor_rel, nblk);
     }
     if (p.mode == 0) return;
-    const double2 s0 = p.state[lo + k];
+    const double2 s0 = ldx<CG>(p.state + lo + k);
     const double2 psiM = make_double2(s0.x - sy, s0.y + sx);
     if (p.mode == 2) {
         p.out[lo + k] = psiM;
@@ -951,6 +965,11 @@ __global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
     p.state[lo + k] = a;
     p.psi0c_out[lo + k] = mkc((T)a.x, (T)a.y);
     if (!(isfinite(a.x) && isfinite(a.y))) atomicOr(p.err, ERR_NONFINITE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) scan_kernel(const ScanParams<T> p) {
+    scan_freq<T, false>(p, blockIdx.y, (long long)blockIdx.x * blockDim.x + threadIdx.x, gridDim.x);
 }
 
 // out[c][r] = in[r][c] for an R x Cc matrix (32 x 32 tiles).

@@ -73,6 +73,14 @@ constexpr int KN_LOG_MIN = 8;
 template <typename T> constexpr int kn_log_max() { return sizeof(T) == 4 ? 16 : 13; }
 template <typename T> cudaError_t kn_launch(int logL, const KNParams<T>& p, cudaStream_t st);
 cudaError_t knc_launch(int logL, const KNParams<float>& p, cudaStream_t st);
+// Rows (nodes) per tile and threads per CTA of the FP32 on-chip transform
+// for N = 2^logL <= 2^14 (KNGeom<float, N>: tiles of 8192 elements, 32 per thread).
+#define KN_TILE_ROWS(logL) ((logL) >= 13 ? 1ll : (8192ll >> (logL)))
+#define KN_THREADS(logL) ((logL) >= 14 ? 512ll : 256ll)
+// Persistent batch kernel (kp.cuh): FP32, N = 2^logL <= 2^14, and its queue reset.
+struct KPParams;
+cudaError_t kp_launch(int logL, const KPParams& p, cudaStream_t st);
+cudaError_t kp_init_launch(unsigned int* q_seq, unsigned int q_cap, unsigned int* ctr, int n_ctr, cudaStream_t st);
 template <typename T> cudaError_t scan_launch(const ScanParams<T>& p, int links, cudaStream_t st);
 template <typename T> cudaError_t transpose_launch(const cx<T>* in, cx<T>* out, long long R, long long C, cudaStream_t st);
 template <typename T> cudaError_t to_state_launch(const cx<T>* in, double2* state, cx<T>* copy, long long N, cudaStream_t st);

@@ -713,6 +713,7 @@ const char* mpa_status_string(int status) {
         case MPA_ERR_NONFINITE: return "non-finite value produced";
         case MPA_ERR_DIVERGED: return "Picard iteration diverged (the increment grew between iterations)";
         case MPA_ERR_SCALES: return "scales outside the weak-nonlinearity regime of the method";
+        case MPA_ERR_TIMEOUT: return "a wait of the persistent batch kernel ran out (results incomplete)";
     }
     return "unknown status";
 }

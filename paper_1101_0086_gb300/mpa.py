@@ -59,7 +59,7 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
            "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split",
            "mpa_batch_autotune", "mpa_plan_contraction", "mpa_plan_check_scales", "mpa_batch_status",
-           "mpa_debug_fail_launch", "mpa_alu_peak")
+           "mpa_debug_fail_launch", "mpa_alu_peak", "mpa_batch_set_persistent", "mpa_batch_set_wait_limit")
 
 
 def library_path() -> str:
@@ -124,8 +124,10 @@ def lib() -> ctypes.CDLL:
         L.mpa_batch_status.argtypes = [vp, vp]
         L.mpa_debug_fail_launch.argtypes = [i64, i32]
         L.mpa_alu_peak.argtypes = [i32, ctypes.POINTER(dbl), vp]
+        L.mpa_batch_set_persistent.argtypes = [vp, i32]
+        L.mpa_batch_set_wait_limit.argtypes = [vp, i64]
         for f in ("mpa_plan_contraction", "mpa_plan_check_scales", "mpa_batch_status", "mpa_debug_fail_launch",
-                  "mpa_alu_peak"):
+                  "mpa_alu_peak", "mpa_batch_set_persistent", "mpa_batch_set_wait_limit"):
             getattr(L, f).restype = ctypes.c_int
         for f in ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace", "mpa_propagate",
                   "mpa_interval", "mpa_plan_status", "ss_workspace_size", "ss_propagate", "mpa_fft",
@@ -450,9 +452,20 @@ class Batch:
         _check(lib().mpa_batch_propagate(self._h, 1 if use_graph else 0, _stream(stream)), "mpa_batch_propagate")
 
     def status_code(self, stream=None) -> int:
-        """``mpa_batch_status``: 0, 6 (a link produced NaN/Inf) or 7 (a link's
-        Picard iteration diverged) since the last call; clears the flags."""
+        """``mpa_batch_status``: 0, 6 (a link produced NaN/Inf), 7 (a link's
+        Picard iteration diverged) or 9 (a wait of the persistent kernel ran
+        out) since the last call; clears the flags."""
         return int(lib().mpa_batch_status(self._h, _stream(stream)))
+
+    def set_persistent(self, on: bool) -> None:
+        """``mpa_batch_set_persistent``: the persistent work-queue kernel for
+        every eligible group (FP32, N <= 2^14) or none."""
+        _check(lib().mpa_batch_set_persistent(self._h, 1 if on else 0), "mpa_batch_set_persistent")
+
+    def set_wait_limit(self, polls: int) -> None:
+        """``mpa_batch_set_wait_limit``: polls (about 128 ns each) before a
+        wait of the persistent kernel gives up."""
+        _check(lib().mpa_batch_set_wait_limit(self._h, int(polls)), "mpa_batch_set_wait_limit")
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -435,3 +435,70 @@ def test_cluster_onchip_interval_matches_oracle(M, logn, Lk, Mn, n_iter, z0):
     b = dev(A0, "fp32")
     four.propagate(b, 0.0, 20.0)
     assert oracle.rel_l2(host(a), host(b)) < 1e-5
+
+
+# ------------------------------------------- persistent batch kernel
+def _small_specs(n=14):
+    """Links for the persistent kernel: N = 2^9 .. 2^14 (FP32 on-chip sizes),
+    channels 2-16, 1-4 spans, per-link sigma and power (the seeded batch
+    generator)."""
+    from paper_1101_0086_gb300.workloads import batch_links
+    return batch_links(n_links=n, seed=9, log2_n=(9, 14), spans=(1, 4))
+
+
+def test_persistent_batch_matches_launches_and_oracle(M):
+    """mpa_batch_set_persistent: every interval and iteration of the small
+    links in one persistent work-queue launch per size group, against the
+    per-pass launches of the same node transform and (two links) the oracle;
+    directly and through the captured graph (capture, then replay)."""
+    specs = _small_specs()
+    A = [sp.field() for sp in specs]
+    L, Mn, n_iter = 5.0, 20, 3
+    fa = [dev(a, "fp32") for a in A]
+    fb = [dev(a, "fp32") for a in A]
+    a = M.Batch([(sp.fiber, sp.T_ps, sp.length_km, f) for sp, f in zip(specs, fa)], L, Mn, n_iter)
+    b = M.Batch([(sp.fiber, sp.T_ps, sp.length_km, f) for sp, f in zip(specs, fb)], L, Mn, n_iter)
+    a.set_persistent(True)
+    b.set_persistent(False)
+    a.propagate(use_graph=False)
+    b.propagate(use_graph=False)
+    assert a.status_code() == 0 and b.status_code() == 0
+    for x, y in zip(fa, fb):
+        assert oracle.rel_l2(host(x), host(y)) < 1e-6
+    for i in (0, 5):
+        sp = specs[i]
+        ref = oracle.mpa(A[i], sp.fiber, sp.T_ps, 0.0, sp.length_km, L, Mn, n_iter)
+        assert oracle.rel_l2(host(fa[i]), ref) < TOL["fp32"], i
+    # the captured graph: the first call captures (and runs directly), the second replays
+    for _ in range(2):
+        for f, x in zip(fa, A):
+            f.copy_(dev(x, "fp32"))
+        a.propagate(use_graph=True)
+    assert a.status_code() == 0
+    for x, y in zip(fa, fb):
+        assert oracle.rel_l2(host(x), host(y)) < 1e-6
+
+
+def test_persistent_batch_wait_limit_reports_timeout(M):
+    """A wait limit of one poll makes the persistent kernel's queue waits run
+    out (consumers that start before their task is pushed): the kernel ends,
+    mpa_batch_status reports MPA_ERR_TIMEOUT, and with the normal limit the
+    next propagation is correct.  Nothing here faults or hangs: every wait is
+    bounded."""
+    specs = _small_specs(7)
+    A = [sp.field() for sp in specs]
+    L, Mn, n_iter = 5.0, 20, 2
+    f = [dev(a, "fp32") for a in A]
+    bt = M.Batch([(sp.fiber, sp.T_ps, sp.length_km, x) for sp, x in zip(specs, f)], L, Mn, n_iter)
+    bt.set_persistent(True)
+    bt.set_wait_limit(1)
+    bt.propagate(use_graph=False)
+    assert bt.status_code() == 9
+    bt.set_wait_limit(1 << 24)
+    for x, a in zip(f, A):
+        x.copy_(dev(a, "fp32"))
+    bt.propagate(use_graph=False)
+    assert bt.status_code() == 0
+    sp = specs[3]
+    ref = oracle.mpa(A[3], sp.fiber, sp.T_ps, 0.0, sp.length_km, L, Mn, n_iter)
+    assert oracle.rel_l2(host(f[3]), ref) < TOL["fp32"]
