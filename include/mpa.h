@@ -52,7 +52,7 @@ enum {
     MPA_ERR_NONFINITE = 6,     /* a NaN/Inf was produced (mpa_plan_status, mpa_batch_status) */
     MPA_ERR_DIVERGED = 7,      /* the Picard iteration did not contract (mpa_plan_status, mpa_batch_status) */
     MPA_ERR_SCALES = 8,        /* scales outside the weakly nonlinear regime (mpa_plan_check_scales) */
-    MPA_ERR_TIMEOUT = 9        /* a wait of the persistent batch kernel ran out (mpa_batch_status) */
+    MPA_ERR_TIMEOUT = 9        /* a bounded wait of a persistent kernel ran out (mpa_plan_status, mpa_batch_status) */
 };
 
 enum { MPA_FP32 = 0, MPA_FP64 = 1 };
@@ -176,7 +176,10 @@ MPA_API int mpa_plan_set_split(mpa_plan* plan, int32_t log2_n2);
  *                      this is what a too long interval or too strong
  *                      nonlinearity produces.  Needs n_iter >= 2 and the
  *                      level schedule (the wavefront schedule reports only
- *                      MPA_ERR_NONFINITE).
+ *                      MPA_ERR_NONFINITE);
+ *   MPA_ERR_TIMEOUT    a bounded wait of the staged row pass (four-step
+ *                      rows of 2^10 .. 2^13 points) ran out: the results
+ *                      are incomplete (not expected in normal operation).
  * MPA_ERR_NONFINITE takes precedence; else MPA_OK. */
 MPA_API int mpa_plan_status(mpa_plan* plan, mpa_stream stream);
 
@@ -279,7 +282,7 @@ MPA_API int mpa_batch_autotune(mpa_batch* batch, mpa_stream stream);
  * being captured by the caller. */
 MPA_API int mpa_batch_propagate(mpa_batch* batch, int32_t use_graph, mpa_stream stream);
 /* mpa_plan_status for all links of the batch: MPA_ERR_TIMEOUT (a wait of
- * the persistent kernel ran out: the results are incomplete), else
+ * a persistent kernel ran out: the results are incomplete), else
  * MPA_ERR_NONFINITE or MPA_ERR_DIVERGED if any link produced it since the
  * last call (synchronises the stream, clears the flags), else MPA_OK. */
 MPA_API int mpa_batch_status(mpa_batch* batch, mpa_stream stream);
@@ -297,6 +300,11 @@ MPA_API int mpa_batch_status(mpa_batch* batch, mpa_stream stream);
  * for every eligible group (on != 0) or none.  Both drop a captured graph.
  * The paper has no counterpart (the batching of independent problems). */
 MPA_API int mpa_batch_set_persistent(mpa_batch* batch, int32_t on);
+/* The wait limit (polls >= 0) of the batch's persistent kernels: the work
+ * queue above, and the staged row pass of four-step node transforms with
+ * rows of 2^10 .. 2^13 points, whose waits on its staging copies are bounded
+ * the same way (plans use 2^22 polls).  polls = 0 makes every such wait run
+ * out at once (for tests of MPA_ERR_TIMEOUT).  Drops a captured graph. */
 MPA_API int mpa_batch_set_wait_limit(mpa_batch* batch, int64_t polls);
 MPA_API void mpa_batch_destroy(mpa_batch* batch);
 
@@ -393,6 +401,18 @@ MPA_API int mpa_alu_peak(int32_t precision, double* flops_per_s, mpa_stream stre
 MPA_API void mpa_profile(int enable);
 MPA_API int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* bytes);
 MPA_API const char* mpa_profile_kind_name(int kind);
+
+/* Per-call timing (tooling): while mpa_profile is enabled, each call of
+ * mpa_propagate, mpa_interval, ss_propagate, mpa_propagate_checkpointed,
+ * mpa_adjoint, ss_adjoint, mpa_batch_propagate and mpa_fft made on a
+ * stream that is not capturing is bracketed by CUDA events on its stream
+ * (an entry point called from inside another is not timed separately).
+ * mpa_last_timing waits for the end event of the most recent timed call
+ * (any thread) and writes its device time in ms to *ms and the entry
+ * point's name (static storage) to *entry (may be NULL).
+ * MPA_ERR_INVALID_ARG if ms is NULL or no call was timed since
+ * mpa_profile(1); MPA_ERR_CUDA if an event failed. */
+MPA_API int mpa_last_timing(double* ms, const char** entry);
 
 #ifdef __cplusplus
 }

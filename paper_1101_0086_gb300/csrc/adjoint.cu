@@ -406,7 +406,7 @@ int mpa_adjoint_workspace_size(const mpa_plan* p, double z_from_km, double z_to_
 
 int mpa_propagate_checkpointed(mpa_plan* p, void* field, double z_from_km, double z_to_km, void* adj_ws,
                                size_t adj_bytes, mpa_stream stream) {
-    mpa::host::NvtxRange nv("mpa_propagate_checkpointed");
+    mpa::host::EntryRange nv("mpa_propagate_checkpointed", stream);
     if (!p || !field) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
     AdjLayout a;
@@ -422,7 +422,7 @@ int mpa_propagate_checkpointed(mpa_plan* p, void* field, double z_from_km, doubl
 int mpa_adjoint(mpa_plan* p, const void* field_in, const void* grad_out, void* grad_in, double z_from_km,
                 double z_to_km, void* adj_ws, size_t adj_bytes, double* grad_sigma, double* grad_beta2,
                 mpa_stream stream) {
-    mpa::host::NvtxRange nv("mpa_adjoint");
+    mpa::host::EntryRange nv("mpa_adjoint", stream);
     if (!p || !grad_out || !grad_in) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
     AdjLayout a;

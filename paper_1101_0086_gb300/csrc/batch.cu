@@ -52,8 +52,9 @@ bool persistent_ok(const Group& g, int prec) {
     return prec == MPA_FP32 && g.sp.onchip && g.sp.N <= (1ll << 14);
 }
 
-Monitor group_monitor(unsigned char* ws, const Group& g) {
+Monitor group_monitor(unsigned char* ws, const Group& g, long long spin_limit) {
     Monitor m{};
+    m.spin_limit = spin_limit;
     m.err = reinterpret_cast<unsigned int*>(ws + g.off_err);
     m.conv = reinterpret_cast<ConvState*>(ws + g.off_conv);
     m.dprev = reinterpret_cast<float2*>(ws + g.off_dprev);
@@ -140,7 +141,7 @@ int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
     const NodeC* nodes = reinterpret_cast<const NodeC*>(b->ws + g.off_nodes);
     const int* loff = reinterpret_cast<const int*>(b->ws + g.off_loff);
     const double* gain = reinterpret_cast<const double*>(b->ws + g.off_gain);
-    const Monitor mon = group_monitor(b->ws, g);
+    const Monitor mon = group_monitor(b->ws, g, b->spin_limit);
     // a fresh increment check per propagation (a run that ended early, e.g.
     // on a timeout, must not leave a half-counted level behind)
     MPA_TRY(cudaMemsetAsync(mon.conv, 0, (size_t)n * sizeof(ConvState), st));
@@ -403,14 +404,14 @@ int mpa_batch_set_persistent(mpa_batch* b, int32_t on) {
 }
 
 int mpa_batch_set_wait_limit(mpa_batch* b, int64_t polls) {
-    if (!b || polls < 1) return MPA_ERR_INVALID_ARG;
+    if (!b || polls < 0) return MPA_ERR_INVALID_ARG;
     b->spin_limit = polls;
     release_graph(b);  // the limit is a launch argument of the captured kernels
     return MPA_OK;
 }
 
 int mpa_batch_propagate(mpa_batch* b, int32_t use_graph, mpa_stream stream) {
-    NvtxRange nv("mpa_batch_propagate");
+    EntryRange nv("mpa_batch_propagate", stream);
     if (!b) return MPA_ERR_INVALID_ARG;
     if (!b->ws) return MPA_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -504,7 +505,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                                              reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
                                              reinterpret_cast<const int*>(b->ws + g.off_loff),
                                              reinterpret_cast<const double*>(b->ws + g.off_gain),
-                                             group_monitor(b->ws, g), 1, nullptr, st)
+                                             group_monitor(b->ws, g, b->spin_limit), 1, nullptr, st)
                          : mpa_levels<double>(g.sp, b->M, b->n_iter, g.active[0],
                                               reinterpret_cast<double2*>(b->ws + g.off_psi),
                                               reinterpret_cast<double2*>(b->ws + g.off_psi0c),
@@ -512,7 +513,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                                               reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
                                               reinterpret_cast<const int*>(b->ws + g.off_loff),
                                               reinterpret_cast<const double*>(b->ws + g.off_gain),
-                                              group_monitor(b->ws, g), 1, nullptr, st);
+                                              group_monitor(b->ws, g, b->spin_limit), 1, nullptr, st);
                 if (rc == MPA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
                     rc = cuda_fail(cudaGetLastError());

@@ -133,11 +133,43 @@ template <int R, int K, int S, class C> __device__ __forceinline__ C tw_const(C 
     }
 }
 
+// FP32 butterflies with a non-trivial constant twiddle (K/R not a multiple
+// of 1/4) as fused multiply-adds: x0 = e + w o with the twiddle's products
+// folded into the additions, x1 = 2 e - x0 (= e - w o): six FP32 operations
+// instead of eight (two products, two fused products and four additions).
+// The difference from x1 = e - w o is one rounding of x0, of the size of the
+// rounding of the product itself.  MPA_FMA_BFLY=0 keeps the plain form.
+#ifndef MPA_FMA_BFLY
+#define MPA_FMA_BFLY 1
+#endif
+template <int R, int K, int S> __device__ __forceinline__ void bfly_tw(float2& x0, float2& x1, float2 e, float2 o) {
+    constexpr int M32 = K * (32 / R);
+    float ax, ay;
+    if constexpr (M32 == 4 || M32 == 12) {
+        // w = c (re + S i), c = cos(pi/4): x0 = e + c (re o.x - S o.y, re o.y + S o.x)
+        constexpr float re = (M32 == 4) ? 1.f : -1.f;
+        const float c = (float)MPA_COS_PI_4;
+        ax = fmaf(c, re * o.x - float(S) * o.y, e.x);
+        ay = fmaf(c, re * o.y + float(S) * o.x, e.y);
+    } else {
+        const float cr = (float)Cs32<M32>::c, si = float(S) * (float)Cs32<M32>::s;
+        ax = fmaf(o.x, cr, fmaf(-o.y, si, e.x));
+        ay = fmaf(o.x, si, fmaf(o.y, cr, e.y));
+    }
+    x0 = make_float2(ax, ay);
+    x1 = make_float2(fmaf(2.f, e.x, -ax), fmaf(2.f, e.y, -ay));
+}
+
 template <int R, int S, int K, class C> __device__ __forceinline__ void dft_combine(C* x, const C* e, const C* o) {
     if constexpr (K < R / 2) {
-        const C t = tw_const<R, K, S>(o[K]);
-        x[K] = cadd(e[K], t);
-        x[K + R / 2] = csub(e[K], t);
+        constexpr int M32 = K * (32 / R);
+        if constexpr (MPA_FMA_BFLY && sizeof(C) == 8 && M32 != 0 && M32 != 8) {
+            bfly_tw<R, K, S>(x[K], x[K + R / 2], e[K], o[K]);
+        } else {
+            const C t = tw_const<R, K, S>(o[K]);
+            x[K] = cadd(e[K], t);
+            x[K + R / 2] = csub(e[K], t);
+        }
         dft_combine<R, S, K + 1>(x, e, o);
     }
 }
@@ -358,6 +390,24 @@ template <typename T> __device__ __forceinline__ cx<T> expi_ratio(long long e, i
     return mkc(c, s);
 }
 
+// ------------------------------------------------- thread groups
+// A transform runs on the whole block (GRP = 0: threadIdx.x, __syncthreads)
+// or on one of several NT-thread groups of the block (GRP = 1: the thread's
+// index within its group, and named barrier 1 + group over the group's NT
+// threads, so groups never wait on one another).
+template <int GRP, int NT> __device__ __forceinline__ int gtid() {
+    if constexpr (GRP == 0) return threadIdx.x;
+    else return threadIdx.x & (NT - 1);
+}
+template <int GRP, int NT> __device__ __forceinline__ void gsync() {
+    if constexpr (GRP == 0) {
+        __syncthreads();
+    } else {
+        static_assert((NT & (NT - 1)) == 0 && NT % 32 == 0, "groups of whole warps, a power of two");
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / NT)), "n"(NT) : "memory");
+    }
+}
+
 // ------------------------------------------------- shared-memory Stockham
 // Padding of the shared-memory tile: one extra element per 2^PSH elements
 // keeps every pass free of bank conflicts (PSH = log2 of the largest radix).
@@ -495,7 +545,7 @@ __device__ __forceinline__ void twiddle_row(cx<T>* v, int e1, const cx<T>* hi, c
 // read and write phases).  Butterfly j of transform g reads elements
 // j + r L/R, applies W_{NS R}^{S r (j mod NS)}, does the R-point DFT and
 // writes to (j - j mod NS) R + j mod NS + r NS.
-template <typename T, int L, int G, int NT, int R, int NS, int S, int LAYOUT, int PSH, bool SF>
+template <typename T, int L, int G, int NT, int R, int NS, int S, int LAYOUT, int PSH, bool SF, int GRP = 0>
 __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
     typedef cx<T> C;
     constexpr int NB = (L / R) * G;
@@ -504,7 +554,7 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
     C v[Q][R];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int b = threadIdx.x + q * NT;
+        const int b = gtid<GRP, NT>() + q * NT;
         const int j = LAYOUT == LAYOUT_COL ? b / G : b % (L / R);
         const int g = LAYOUT == LAYOUT_COL ? b % G : b / (L / R);
         typedef Slot<LAYOUT, L, G, PSH> SL;
@@ -519,10 +569,10 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
         if constexpr (NS > 1) twiddle_row<T, L, R, S>(v[q], (j & (NS - 1)) * (L / (NS * R)), hi, lo);
         Dft<R, S, C>::run(v[q]);
     }
-    __syncthreads();
+    gsync<GRP, NT>();
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int b = threadIdx.x + q * NT;
+        const int b = gtid<GRP, NT>() + q * NT;
         const int j = LAYOUT == LAYOUT_COL ? b / G : b % (L / R);
         const int g = LAYOUT == LAYOUT_COL ? b % G : b / (L / R);
         const int k = j & (NS - 1);
@@ -538,7 +588,7 @@ __device__ __forceinline__ void stockham_pass(cx<T>* s, const cx<T>* hi, const c
             for (int r = 0; r < R; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(dst + r * NS, g))] = v[q][r];
         }
     }
-    __syncthreads();
+    gsync<GRP, NT>();
 }
 
 // Pass schedule of a length-L transform with radices RMAX and one smaller
@@ -560,12 +610,13 @@ template <int L, int RMAX> struct Sched {
     template <bool SF> __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : ns<SF>(p - 1) * radix<SF>(p - 1); }
 };
 
-template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH, bool SF, int P, int NP>
+template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH, bool SF, int P, int NP, int GRP = 0>
 __device__ __forceinline__ void mid_passes(cx<T>* s, const cx<T>* hi, const cx<T>* lo) {
     if constexpr (P < NP - 1) {
         typedef Sched<L, RMAX> SC;
-        stockham_pass<T, L, G, NT, SC::template radix<SF>(P), SC::template ns<SF>(P), S, LAYOUT, PSH, SF>(s, hi, lo);
-        mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, P + 1, NP>(s, hi, lo);
+        stockham_pass<T, L, G, NT, SC::template radix<SF>(P), SC::template ns<SF>(P), S, LAYOUT, PSH, SF, GRP>(s, hi,
+                                                                                                              lo);
+        mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, P + 1, NP, GRP>(s, hi, lo);
     }
 }
 
@@ -584,8 +635,8 @@ template <int LAYOUT, int L, int G, int R> __device__ __forceinline__ void bmap(
 // j + r L/R0 of butterfly b = tid + q NT (R0 = first radix), vout[q][r]
 // receives output element j + r L/RL (RL = last radix).  Shared memory is
 // used by the middle passes only; the transform ends with a barrier so the
-// caller may reuse `s`.
-template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH, bool SF> struct Xform {
+// caller may reuse `s`.  GRP as for gtid/gsync.
+template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH, bool SF, int GRP = 0> struct Xform {
     typedef Sched<L, RMAX> SC;
     typedef cx<T> C;
     static constexpr int NP = SC::NP;
@@ -608,7 +659,7 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
 #pragma unroll
             for (int q = 0; q < Q0; ++q) {
                 int j, g;
-                bmap<LAYOUT, L, G, R0>(threadIdx.x + q * NT, j, g);
+                bmap<LAYOUT, L, G, R0>(gtid<GRP, NT>() + q * NT, j, g);
                 Dft<R0, S, C>::run(vin[q]);
                 // j R0 + r, r < R0: the shift always splits (j R0 is a multiple
                 // of 2^SH, or R0 divides 2^SH and r < R0 adds no carry)
@@ -622,13 +673,13 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
                     for (int r = 0; r < R0; ++r) s[phys<PSH>(eidx<LAYOUT, L, G>(j * R0 + r, g))] = vin[q][r];
                 }
             }
-            __syncthreads();
-            mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, 1, NP>(s, hi, lo);
+            gsync<GRP, NT>();
+            mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, 1, NP, GRP>(s, hi, lo);
             // last pass (NS = L/RL, so k = j): gather j + r L/RL, twiddle W_L^{S r j}, DFT
 #pragma unroll
             for (int q = 0; q < QL; ++q) {
                 int j, g;
-                bmap<LAYOUT, L, G, RL>(threadIdx.x + q * NT, j, g);
+                bmap<LAYOUT, L, G, RL>(gtid<GRP, NT>() + q * NT, j, g);
                 typedef Slot<LAYOUT, L, G, PSH> SL;
                 if constexpr (slot_site_on<LAYOUT, SF, 3>() && SL::template strided<L / RL, RL>()) {
                     const C* sb = s + SL::base(j, g);
@@ -641,7 +692,7 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
                 twiddle_row<T, L, RL, S>(vout[q], j, hi, lo);
                 Dft<RL, S, C>::run(vout[q]);
             }
-            __syncthreads();
+            gsync<GRP, NT>();
         }
     }
 };

@@ -25,6 +25,14 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// An entry point: its NVTX range and, while profiling is on, its per-call
+// CUDA-event timer.
+struct EntryRange {
+    EntryRange(const char* name, mpa_stream stream) : nv(name), timer(name, reinterpret_cast<cudaStream_t>(stream)) {}
+    NvtxRange nv;
+    CallTimer timer;
+};
+
 // Records the CUDA error string for mpa_last_cuda_error.
 int cuda_fail(cudaError_t e);
 
@@ -35,6 +43,9 @@ int cuda_fail(cudaError_t e);
     } while (0)
 
 inline constexpr double kPi = 3.14159265358979323846264338327950288;
+// default polls of each bounded wait of a persistent kernel (a few seconds
+// at most; a wait normally ends within microseconds)
+inline constexpr long long kSpinLimit = 1ll << 22;
 // amplifiers that may end one interval (a longer interval than the
 // amplifier spacing would cross one inside it, which is rejected)
 inline constexpr int kMaxAmpsPerInterval = 4;

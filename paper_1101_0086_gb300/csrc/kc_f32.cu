@@ -1,7 +1,53 @@
 // Column-pass launchers, float.
+#include "kcs.cuh"
 #include "launch.h"
 
 namespace mpa {
+
+// The staged persistent column pass (kcs.cuh) for the MPA passes with
+// columns of 2^8 or 2^9 points and tiles within one node (N1 a multiple of
+// the tile width), whenever the caller passes an error word for its bounded
+// waits; MPA_KC_STAGED=0 keeps kc_kernel everywhere.
+#ifndef MPA_KC_STAGED
+#define MPA_KC_STAGED 1
+#endif
+
+template <int L, int MODE>
+static cudaError_t kcs_one(const KCParams<float>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
+    typedef KCSGeom<L> SG;
+    static_assert(SG::smem_bytes <= 227u * 1024u, "staged column pass exceeds the shared memory of an SM");
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
+        return cudaFuncSetAttribute(kcs_kernel<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SG::smem_bytes);
+    });
+    if (ea != cudaSuccess) return ea;
+    const long long ntiles = p.ncols / KCGeom<float, L>::G;
+    if (ntiles <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);  // one CTA per SM
+    const bool prof = g_prof_on.load(std::memory_order_relaxed);
+    if (prof) prof_begin(st);
+    kcs_kernel<L, MODE><<<grid, SG::THREADS, SG::smem_bytes, st>>>(p);
+    if (prof) {
+        const double cs = (double)sizeof(cx<float>), tile = (double)p.ncols * L;
+        const double rd = p.src_stride == 0 ? (double)p.ncols / p.npl * L : tile;
+        prof_end(prof_kc_kind(MODE), st, (rd + tile) * cs);
+    }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+bool kc_staged(int mode, int logL, const KCParams<float>& p) {
+    if (!MPA_KC_STAGED || !p.err || (mode != KC_MPA_PRE && mode != KC_MPA_POST) || p.npl <= 0) return false;
+    if (logL == 8) return p.N1 % KCGeom<float, 256>::G == 0 && p.ncols % KCGeom<float, 256>::G == 0;
+    if (logL == 9) return p.N1 % KCGeom<float, 512>::G == 0 && p.ncols % KCGeom<float, 512>::G == 0;
+    return false;
+}
 
 template <int L, int MODE>
 static cudaError_t kc_one(const KCParams<float>& pin, cudaStream_t st) {
@@ -50,6 +96,10 @@ static cudaError_t kc_mode(int mode, const KCParams<float>& p, cudaStream_t st) 
 
 template <>
 cudaError_t kc_launch<float>(int mode, int logL, const KCParams<float>& p, cudaStream_t st) {
+    if (kc_staged(mode, logL, p)) {
+        if (logL == 8) return mode == KC_MPA_PRE ? kcs_one<256, KC_MPA_PRE>(p, st) : kcs_one<256, KC_MPA_POST>(p, st);
+        return mode == KC_MPA_PRE ? kcs_one<512, KC_MPA_PRE>(p, st) : kcs_one<512, KC_MPA_POST>(p, st);
+    }
     switch (logL) {
         case 4: return kc_mode<16>(mode, p, st);
         case 5: return kc_mode<32>(mode, p, st);

@@ -1,0 +1,222 @@
+// Staged, persistent column pass (FP32; the MPA column passes): the
+// arithmetic of kc_kernel in modes KC_MPA_PRE (phase exp(i beta_j + int G),
+// inverse column DFTs, outer factor W_N^{-n2 k1}) and KC_MPA_POST (forward
+// column DFTs, V_j of Eq. (6)) on the schedule of the staged row pass
+// (krs.cuh): one CTA per SM, two groups of NT threads taking the CTA's
+// tiles in turn, and one staging buffer that the next tile streams into
+// while the current ones are transformed.
+//
+// A column tile is G columns x L rows of one node (the tile never straddles
+// nodes: N1 is a multiple of G), i.e. L row segments of G complex64 at a
+// stride of N1 elements.  Such short strided segments are copied by the
+// NT threads of the group that releases the stage, 16 bytes per cp.async
+// (a bulk copy per segment was measured 2.3x slower: each bulk request has
+// a fixed cost), and each thread arrives on the receiving group's mbarrier
+// when its own copies have landed (cp.async.mbarrier.arrive.noinc; the
+// barrier counts NT arrivals per phase).  Waits are bounded as in krs.cuh;
+// every thread waits for its own copies before it returns.
+#pragma once
+
+#include "krs.cuh"
+
+namespace mpa {
+
+// Shared-memory layout: the stage (TE elements, row-major L x G), two
+// mbarriers, the twiddle tables of both groups, then per group its exchange
+// buffer and outer-factor tables.
+template <int L> struct KCSGeom {
+    typedef KCGeom<float, L> Gm;
+    typedef Tiling<float> P;
+    static constexpr size_t al(size_t x) { return (x + 127) & ~(size_t)127; }
+    static constexpr size_t STAGE_BYTES = (size_t)Gm::TE * sizeof(float2);
+    static constexpr size_t BAR_OFF = STAGE_BYTES;
+    static constexpr size_t TW_OFF = BAR_OFF + 128;
+    static constexpr size_t GRP_OFF = al(TW_OFF + (size_t)(TwDims<L>::NLO + TwDims<L>::NHI) * sizeof(float2));
+    static constexpr size_t S_ELEMS = (size_t)Gm::TE + (Gm::TE >> P::PSH) + 1;
+    static constexpr size_t GRP_BYTES = al((S_ELEMS + (size_t)Gm::G * (Gm::OLO + Gm::OHI)) * sizeof(float2));
+    static constexpr size_t smem_bytes = GRP_OFF + 2 * GRP_BYTES;
+    static constexpr int NT = Gm::NT, THREADS = 2 * Gm::NT;
+};
+
+// Source of column col (node and link from the launch layout, as kc_kernel).
+__device__ __forceinline__ const float2* kcs_src(const KCParams<float>& p, long long col, int& l, int& jn,
+                                                 long long& c) {
+    const int node = (int)(col >> p.logN1);
+    l = node / p.npl;
+    jn = node - l * p.npl;
+    c = col & (long long)(p.N1 - 1);
+    return (p.src0 && jn == 0) ? p.src0 + l * p.src0_lstride + c : p.src + l * p.src_lstride + jn * p.src_stride + c;
+}
+
+// 16-byte global -> shared copy through L2 (cp.async.cg)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+// barrier b receives one arrival from this thread once all of its earlier
+// cp.async copies have landed (the arrival is counted in b's expected count)
+__device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Group-wide: the NT threads start the copies of tile t (L row segments of
+// G elements) into the stage and each arrives on barrier b when its copies
+// have landed.
+template <int L>
+__device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float2* stage, unsigned long long* b,
+                                          int tid) {
+    constexpr int G = KCGeom<float, L>::G, NT = KCGeom<float, L>::NT;
+    constexpr int CPR = G * (int)sizeof(float2) / 16;  // 16-byte chunks per row segment
+    constexpr int NCH = L * CPR;
+    static_assert(NCH % NT == 0, "whole chunks per thread");
+    int l, jn;
+    long long c;
+    const char* src = reinterpret_cast<const char*>(kcs_src(p, (long long)t * G, l, jn, c));
+    char* dst = reinterpret_cast<char*>(stage);
+#pragma unroll
+    for (int k = 0; k < NCH / NT; ++k) {
+        const int id = tid + k * NT, row = id / CPR, ch = id % CPR;
+        cp_async16(dst + (size_t)row * G * sizeof(float2) + ch * 16,
+                   src + (long long)row * p.N1 * (long long)sizeof(float2) + ch * 16);
+    }
+    cp_async_arrive(b);
+}
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
+    kcs_kernel(const KCParams<float> p) {
+    static_assert(MODE == KC_MPA_PRE || MODE == KC_MPA_POST, "the MPA column passes");
+    typedef float2 C;
+    typedef KCGeom<float, L> Gm;
+    typedef KCSGeom<L> SG;
+    typedef Tiling<float> P;
+    constexpr int G = Gm::G, NT = Gm::NT;
+    constexpr bool INV = MODE == KC_MPA_PRE;
+    typedef Xform<float, L, G, NT, P::RMAX, +1, LAYOUT_COL, P::PSH, true, 1> XF;
+    typedef Xform<float, L, G, NT, P::RMAX, -1, LAYOUT_COL, P::PSH, false, 1> XI;
+    typedef typename std::conditional<INV, XI, XF>::type XA;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C* stage = reinterpret_cast<C*>(smem_raw);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + SG::BAR_OFF);
+    C* thi = reinterpret_cast<C*>(smem_raw + SG::TW_OFF);
+    C* tlo = thi + TwDims<L>::NHI;
+    const int grp = (int)(threadIdx.x / NT), tid = (int)(threadIdx.x & (NT - 1));
+    C* s = reinterpret_cast<C*>(smem_raw + SG::GRP_OFF + (size_t)grp * SG::GRP_BYTES);
+    C* olo = s + SG::S_ELEMS;   // [OLO][G]
+    C* ohi = olo + G * Gm::OLO; // [OHI][G]
+    const int ntiles = (int)(p.ncols / G);  // < 2^31: columns of a launch / G
+    const int N1m = p.N1 - 1;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], NT);
+        mbar_init(&bar[1], NT);
+        mbar_init_fence();
+    }
+    tw_init<float, L>(thi, tlo, (int)threadIdx.x, SG::THREADS);
+    __syncthreads();
+    // the first tile is copied by group 1 (whose own first tile comes later)
+    if (grp == 1 && (int)blockIdx.x < ntiles) kcs_fetch<L>(p, blockIdx.x, stage, &bar[0], tid);
+
+    unsigned k = 0;
+    for (int i = grp;; i += 2, ++k) {
+        const int t = (int)blockIdx.x + i * (int)gridDim.x;
+        if (t >= ntiles) break;
+        const long long col0 = (long long)t * G;
+        gsync<1, NT>();  // the group's previous tile no longer needs s, olo, ohi
+        if constexpr (INV) {
+            // W_N^{-n2 k1} for the tile's columns: olo[m][g] = W^{-k1 m}, ohi[h][g] = W^{-k1 32 h}
+            for (int e = tid; e < G * (Gm::OLO + Gm::OHI); e += NT) {
+                const int g = e % G, m = e / G;
+                const long long k1 = (col0 + g) & N1m;
+                if (m < Gm::OLO) olo[m * G + g] = expi_ratio<float>(-k1 * m, p.logN);
+                else ohi[(m - Gm::OLO) * G + g] = expi_ratio<float>(-k1 * ((long long)(m - Gm::OLO) << Gm::OSH), p.logN);
+            }
+        }
+        bool ok = false;
+        for (long long w = 0; w < p.spin_limit && !ok; ++w) ok = mbar_try_wait(&bar[grp], k & 1u);
+
+        // ---- element j + r L/R0 of column col0 + g, from the stage
+        C vin[XA::Q0][XA::R0];
+#pragma unroll
+        for (int q = 0; q < XA::Q0; ++q) {
+            int j, g;
+            bmap<LAYOUT_COL, L, G, XA::R0>(tid + q * NT, j, g);
+            if constexpr (INV) {
+                int l, jn;
+                long long c;
+                kcs_src(p, col0 + g, l, jn, c);
+                const NodeC nc = p.nodes[p.loff[l] + jn];
+                // phases in the order of their finite differences: s = -R0/2 .. R0/2-1,
+                // element r = (s + R0) mod R0 at k' = c + N1 (j + s L/R0)
+                const long long D = (long long)p.N1 * (L / XA::R0);
+                PhaseRun pr(c + (long long)j * p.N1 - (long long)(XA::R0 / 2) * D, D, nc);
+#pragma unroll
+                for (int u = 0; u < XA::R0; ++u) {
+                    const int r = (u + XA::R0 / 2) % XA::R0;
+                    const int row = j + r * (L / XA::R0);
+                    const C v = ok ? stage[row * G + g] : mkc(0.f, 0.f);
+                    // MPA step 2: A_hat_j = psi_j exp(i beta(w, z_j) + int G)
+                    vin[q][r] = cscale(cmul(v, expi_turns_poly(pr.next())), (float)nc.pre);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < XA::R0; ++r) {
+                    const int row = j + r * (L / XA::R0);
+                    vin[q][r] = ok ? stage[row * G + g] : mkc(0.f, 0.f);
+                }
+            }
+        }
+        // every thread of the group has its part of the tile (and the tables are written)
+        if (gsync_any<NT>(!ok)) {
+            if (tid == 0) atomicOr(p.err, ERR_TIMEOUT);
+            break;
+        }
+        {
+            const int tn = t + (int)gridDim.x;
+            if (tn < ntiles) kcs_fetch<L>(p, tn, stage, &bar[grp ^ 1], tid);
+        }
+
+        constexpr int QO = XA::QL, RO = XA::RL;
+        C vout[QO][RO];
+        XA::run(vin, vout, s, thi, tlo);
+
+        // ---- epilogue and store: element j + r L/RO of column col0 + g
+#pragma unroll
+        for (int q = 0; q < QO; ++q) {
+            int j, g;
+            bmap<LAYOUT_COL, L, G, RO>(tid + q * NT, j, g);
+            int l, jn;
+            long long c;
+            kcs_src(p, col0 + g, l, jn, c);
+            C* dst = p.dst + l * p.dst_lstride + jn * p.dst_stride + c;
+            if constexpr (INV) {
+                constexpr bool HOIST = (L / RO) % Gm::OLO == 0;
+                C wlo = mkc(1.f, 0.f);
+                if constexpr (HOIST) wlo = olo[(j & (Gm::OLO - 1)) * G + g];
+#pragma unroll
+                for (int r = 0; r < RO; ++r) {
+                    const int row = j + r * (L / RO);
+                    // four-step factor W_N^{-n2 k1}, n2 = row
+                    C w = HOIST ? wlo : olo[(row & (Gm::OLO - 1)) * G + g];
+                    if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
+                    dst[(long long)row * p.N1] = cmul(vout[q][r], w);
+                }
+            } else {
+                const NodeC nc = p.nodes[p.loff[l] + jn];
+                const long long D = (long long)p.N1 * (L / RO);
+                PhaseRun pr(c + (long long)j * p.N1 - (long long)(RO / 2) * D, D, nc);
+#pragma unroll
+                for (int u = 0; u < RO; ++u) {
+                    const int r = (u + RO / 2) % RO;
+                    const int row = j + r * (L / RO);
+                    // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
+                    dst[(long long)row * p.N1] = cscale(cmul(vout[q][r], cconj(expi_turns_poly(pr.next()))), (float)nc.post);
+                }
+            }
+        }
+    }
+    // this thread's copies must land before the block's shared memory is released
+    cp_async_wait_all();
+}
+
+}  // namespace mpa

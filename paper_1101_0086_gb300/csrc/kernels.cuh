@@ -52,6 +52,8 @@ template <typename T> struct KCParams {
     const NodeC* nodes;     // MPA: constants of link l, node jn at nodes[loff[l] + jn]
     const int* loff;
     NodeC flow;             // SS: constants of the linear step
+    unsigned int* err;      // error word of the staged column pass (null: kc_kernel only)
+    long long spin_limit;   // polls of each bounded wait of the staged column pass
 };
 
 template <typename T> struct KRParams {
@@ -63,6 +65,8 @@ template <typename T> struct KRParams {
     T inv_n;  // 1/N
     T rot;    // SS: int sigma over the step
     cx<T>* keep;  // KR_MPA_KEEP: receives A(t), rows laid out as data
+    unsigned int* err;       // error word of the staged row pass (null: kr_kernel only)
+    long long spin_limit;    // polls of each bounded wait of the staged row pass
 };
 
 // Column pass geometry for column length L: G columns per tile, NT threads.
@@ -806,7 +810,8 @@ __global__ void __launch_bounds__(KCWGeom<L>::NT, KCWGeom<L>::NT <= 256 ? MPA_KC
 // rel_n with rel_{n-1}: an increment that does not shrink, while above the
 // rounding floor of the working precision, sets bit 1 of the error word
 // (MPA_ERR_DIVERGED); a non-finite interval result sets bit 0.
-enum { ERR_NONFINITE = 1u, ERR_DIVERGED = 2u };
+// ERR_TIMEOUT (bit 2): a bounded wait of a persistent kernel ran out.
+enum { ERR_NONFINITE = 1u, ERR_DIVERGED = 2u, ERR_TIMEOUT = 4u };
 struct ConvState {
     double acc_d, acc_p;  // this level: sum |Delta|^2, sum |psi_M|^2
     double prev_rel;      // rel of the previous level of this interval
@@ -820,6 +825,7 @@ struct Monitor {
     unsigned int* err;
     ConvState* conv;
     float2* dprev;
+    long long spin_limit;  // polls of each bounded wait of a persistent kernel
 };
 
 template <typename T> struct ScanParams {

@@ -31,8 +31,6 @@
 
 namespace mpa {
 
-enum { ERR_TIMEOUT = 4u };
-
 struct KPParams {
     float2* psi;          // link l's node j at psi + (l (M+1) + j) N
     float2* psi0c;        // link l at + l N

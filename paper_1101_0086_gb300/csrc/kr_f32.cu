@@ -1,7 +1,50 @@
 // Row-pass launchers, float.
+#include "krs.cuh"
 #include "launch.h"
 
 namespace mpa {
+
+// The staged persistent row pass (krs.cuh) for rows of 2^10 .. 2^13 points
+// in the MPA and split-step modes, whenever the caller passes an error word
+// for its bounded waits; MPA_KR_STAGED=0 keeps kr_kernel everywhere.
+#ifndef MPA_KR_STAGED
+#define MPA_KR_STAGED 1
+#endif
+
+template <int L, int MODE>
+static cudaError_t krs_one(const KRParams<float>& p, cudaStream_t st) {
+    if (const cudaError_t eg = launch_gate()) return eg;
+    typedef KRSGeom<L> SG;
+    static_assert(SG::smem_bytes <= 227u * 1024u, "staged row pass exceeds the shared memory of an SM");
+    static AttrOnce once;
+    const cudaError_t ea = attrs_once(once, [] {
+        return cudaFuncSetAttribute(krs_kernel<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SG::smem_bytes);
+    });
+    if (ea != cudaSuccess) return ea;
+    const long long ntiles = (p.nrows + KRGeom<float, L>::G - 1) / KRGeom<float, L>::G;
+    if (ntiles <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);  // one CTA per SM
+    const bool prof = g_prof_on.load(std::memory_order_relaxed);
+    if (prof) prof_begin(st);
+    krs_kernel<L, MODE><<<grid, SG::THREADS, SG::smem_bytes, st>>>(p, p.spin_limit);
+    if (prof) prof_end(prof_kr_kind(MODE), st, 2.0 * (double)p.nrows * L * sizeof(cx<float>));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t krs_mode(int mode, const KRParams<float>& p, cudaStream_t st) {
+    return mode == KR_MPA ? krs_one<L, KR_MPA>(p, st) : krs_one<L, KR_SS>(p, st);
+}
+
+bool kr_staged(int mode, int logL, const KRParams<float>& p) {
+    return MPA_KR_STAGED && p.err && (mode == KR_MPA || mode == KR_SS) && logL >= 10 && logL <= 13;
+}
 
 template <int L, int MODE>
 static cudaError_t kr_one(const KRParams<float>& p, cudaStream_t st) {
@@ -40,6 +83,14 @@ static cudaError_t kr_mode(int mode, const KRParams<float>& p, cudaStream_t st) 
 
 template <>
 cudaError_t kr_launch<float>(int mode, int logL, const KRParams<float>& p, cudaStream_t st) {
+    if (kr_staged(mode, logL, p)) {
+        switch (logL) {
+            case 10: return krs_mode<1024>(mode, p, st);
+            case 11: return krs_mode<2048>(mode, p, st);
+            case 12: return krs_mode<4096>(mode, p, st);
+            case 13: return krs_mode<8192>(mode, p, st);
+        }
+    }
     switch (logL) {
         case 4: return kr_mode<16>(mode, p, st);
         case 5: return kr_mode<32>(mode, p, st);

@@ -54,6 +54,24 @@ extern std::atomic<bool> g_prof_on;
 void prof_begin(cudaStream_t st);
 void prof_end(int kind, cudaStream_t st, double bytes);
 int prof_kc_kind(int mode);
+// Per-call timer of the entry points (mpa_last_timing): while profiling is
+// on, the outermost timed entry point of a thread records a CUDA event on
+// its stream at construction and at destruction (not on a capturing stream).
+class CallTimer {
+  public:
+    CallTimer(const char* name, cudaStream_t st);
+    ~CallTimer();
+    CallTimer(const CallTimer&) = delete;
+    CallTimer& operator=(const CallTimer&) = delete;
+
+  private:
+    const char* name_;
+    cudaStream_t st_;
+    cudaEvent_t a_ = nullptr;
+};
+void call_timing_reset();
+// the most recent timed call: *have = false if there is none
+cudaError_t call_timing_read(double* ms, const char** entry, bool* have);
 int prof_kr_kind(int mode);
 cudaError_t prof_read(int kind, double* ms, long long* n, double* bytes);
 void prof_reset();
@@ -66,6 +84,10 @@ template <typename T> constexpr int kr_log_max() { return sizeof(T) == 4 ? 14 : 
 
 template <typename T> cudaError_t kc_launch(int mode, int logL, const KCParams<T>& p, cudaStream_t st);
 template <typename T> cudaError_t kr_launch(int mode, int logL, const KRParams<T>& p, cudaStream_t st);
+// whether kr_launch<float> takes the staged persistent row pass (krs.cuh)
+bool kr_staged(int mode, int logL, const KRParams<float>& p);
+// whether kc_launch<float> takes the staged persistent column pass (kcs.cuh)
+bool kc_staged(int mode, int logL, const KCParams<float>& p);
 // On-chip whole node transform for N = 2^logL, 2^8 <= N <= 2^kn_log_max:
 // one CTA per node up to 2^14 (FP32) / 2^13 (FP64), a cluster of 2 or 4 CTAs
 // over distributed shared memory for FP32 2^15 and 2^16 (knc_launch).

@@ -83,6 +83,75 @@ void prof_end(int kind, cudaStream_t st, double bytes) {
     if (P.pending.size() > 4096) P.drain();
 }
 
+namespace {
+struct CallTiming {
+    std::mutex mu;
+    cudaEvent_t a = nullptr, b = nullptr;  // the most recent timed call
+    const char* name = nullptr;
+};
+CallTiming& call_timing() {
+    static CallTiming c;
+    return c;
+}
+thread_local int t_call_depth = 0;
+}  // namespace
+
+CallTimer::CallTimer(const char* name, cudaStream_t st) : name_(name), st_(st) {
+    if (t_call_depth++ > 0 || !g_prof_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();  // keep a failed query out of the launchers' error checks
+        return;
+    }
+    if (cudaEventCreate(&a_) != cudaSuccess || cudaEventRecord(a_, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (a_) cudaEventDestroy(a_);
+        a_ = nullptr;
+    }
+}
+
+CallTimer::~CallTimer() {
+    --t_call_depth;
+    if (!a_) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess || cudaEventRecord(b, st_) != cudaSuccess) {
+        cudaGetLastError();
+        if (b) cudaEventDestroy(b);
+        cudaEventDestroy(a_);
+        return;
+    }
+    CallTiming& C = call_timing();
+    std::lock_guard<std::mutex> g(C.mu);
+    if (C.a) cudaEventDestroy(C.a);
+    if (C.b) cudaEventDestroy(C.b);
+    C.a = a_;
+    C.b = b;
+    C.name = name_;
+}
+
+void call_timing_reset() {
+    CallTiming& C = call_timing();
+    std::lock_guard<std::mutex> g(C.mu);
+    if (C.a) cudaEventDestroy(C.a);
+    if (C.b) cudaEventDestroy(C.b);
+    C.a = C.b = nullptr;
+    C.name = nullptr;
+}
+
+cudaError_t call_timing_read(double* ms, const char** entry, bool* have) {
+    CallTiming& C = call_timing();
+    std::lock_guard<std::mutex> g(C.mu);
+    *have = C.b != nullptr;
+    if (!*have) return cudaSuccess;
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(C.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, C.a, C.b);
+    if (e != cudaSuccess) return e;
+    *ms = (double)t;
+    if (entry) *entry = C.name;
+    return cudaSuccess;
+}
+
 int prof_kc_kind(int mode) {
     return mode == KC_MPA_PRE ? PK_KC_MPA_PRE : mode == KC_MPA_POST ? PK_KC_MPA_POST
          : mode == KC_SS_STEP ? PK_KC_SS : PK_KC_FFT;

@@ -78,8 +78,12 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi
         c.npl = npl;
         c.nodes = nodes;
         c.loff = loff;
+        c.err = mon.err;
+        c.spin_limit = mon.spin_limit;
         MPA_TRY(kc_launch<T>(KC_MPA_PRE, s.logN2, c, st));
         KRParams<T> r{psi, (long long)nl * npl * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
+        r.err = mon.err;
+        r.spin_limit = mon.spin_limit;
         MPA_TRY(kr_launch<T>(KR_MPA, s.logN1, r, st));
         c.src = psi;
         c.src_stride = N;
@@ -127,6 +131,7 @@ Monitor monitor(const mpa_plan* p) {
     m.err = reinterpret_cast<unsigned int*>(p->ws + p->off_err);
     m.conv = reinterpret_cast<ConvState*>(p->ws + p->off_conv);
     m.dprev = reinterpret_cast<float2*>(p->ws + p->off_dprev);
+    m.spin_limit = kSpinLimit;
     return m;
 }
 
@@ -578,7 +583,7 @@ int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
 }
 
 int mpa_propagate(mpa_plan* p, void* field, double z_from_km, double z_to_km, mpa_stream stream) {
-    NvtxRange nv("mpa_propagate");
+    EntryRange nv("mpa_propagate", stream);
     if (!p || !field) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -587,7 +592,7 @@ int mpa_propagate(mpa_plan* p, void* field, double z_from_km, double z_to_km, mp
 }
 
 int mpa_interval(mpa_plan* p, const void* psi0, void* psiM, double z0_km, mpa_stream stream) {
-    NvtxRange nv("mpa_interval");
+    EntryRange nv("mpa_interval", stream);
     if (!p || !psi0 || !psiM) return MPA_ERR_INVALID_ARG;
     if (!p->ws) return MPA_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -659,7 +664,7 @@ int ss_workspace_size(int64_t N, int32_t precision, size_t* bytes) {
 
 int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision, void* field,
                  double z_from_km, double z_to_km, void* workspace, size_t ws_bytes, mpa_stream stream) {
-    NvtxRange nv("ss_propagate");
+    EntryRange nv("ss_propagate", stream);
     if (!map || !field || !workspace || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
     if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
     HostMap m;
@@ -678,6 +683,7 @@ int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km,
 
 int mpa_fft(int64_t N, int32_t precision, int32_t sign, void* data, void* workspace, size_t ws_bytes,
             mpa_stream stream) {
+    EntryRange nv("mpa_fft", stream);
     if (!data || !workspace || (sign != 1 && sign != -1)) return MPA_ERR_INVALID_ARG;
     if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
     Split s;
@@ -723,7 +729,10 @@ const char* mpa_last_cuda_error(void) { return mpa::host::g_cuda_err.c_str(); }
 int64_t mpa_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 void mpa_profile(int enable) {
-    if (enable) prof_reset();
+    if (enable) {
+        prof_reset();
+        call_timing_reset();
+    }
     g_prof_on.store(enable != 0);
 }
 
@@ -734,6 +743,14 @@ int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* byte
     *launches = n;
     if (e != cudaSuccess) return cuda_fail(e);
     return MPA_OK;
+}
+
+int mpa_last_timing(double* ms, const char** entry) {
+    if (!ms) return MPA_ERR_INVALID_ARG;
+    bool have = false;
+    const cudaError_t e = call_timing_read(ms, entry, &have);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return have ? MPA_OK : MPA_ERR_INVALID_ARG;
 }
 
 const char* mpa_profile_kind_name(int kind) {

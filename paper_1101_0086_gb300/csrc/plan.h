@@ -31,9 +31,13 @@ namespace host {
 // The plan's run-time check words (error word, increment check).
 Monitor monitor(const mpa_plan* p);
 
-// MPA_ERR_NONFINITE or MPA_ERR_DIVERGED for the bits of an error word.
+// MPA_ERR_TIMEOUT, MPA_ERR_NONFINITE or MPA_ERR_DIVERGED for the bits of an
+// error word (in that order of precedence: a timed-out wait leaves results
+// incomplete).
 inline int status_of_error_word(unsigned int h) {
-    return (h & ERR_NONFINITE) ? MPA_ERR_NONFINITE : (h & ERR_DIVERGED) ? MPA_ERR_DIVERGED : MPA_OK;
+    return (h & ERR_TIMEOUT) ? MPA_ERR_TIMEOUT
+         : (h & ERR_NONFINITE) ? MPA_ERR_NONFINITE
+         : (h & ERR_DIVERGED) ? MPA_ERR_DIVERGED : MPA_OK;
 }
 
 // Index of the interval start z0 within the DM period (its node table).

@@ -256,7 +256,7 @@ int ss_adjoint_workspace_size(const mpa_fiber_map* map, int64_t N, int32_t preci
 int ss_adjoint(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision, const void* field_in,
                const void* grad_out, void* grad_in, double z_from_km, double z_to_km, int32_t ckpt_steps,
                void* workspace, size_t ws_bytes, double* grad_sigma, double* grad_beta2, mpa_stream stream) {
-    mpa::host::NvtxRange nv("ss_adjoint");
+    mpa::host::EntryRange nv("ss_adjoint", stream);
     if (!map || !field_in || !grad_out || !grad_in || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
     if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
     HostMap m;

@@ -59,7 +59,8 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "mpa_plan_n_segments", "mpa_adjoint_workspace_size", "mpa_propagate_checkpointed", "mpa_adjoint",
            "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split",
            "mpa_batch_autotune", "mpa_plan_contraction", "mpa_plan_check_scales", "mpa_batch_status",
-           "mpa_debug_fail_launch", "mpa_alu_peak", "mpa_batch_set_persistent", "mpa_batch_set_wait_limit")
+           "mpa_debug_fail_launch", "mpa_alu_peak", "mpa_batch_set_persistent", "mpa_batch_set_wait_limit",
+           "mpa_last_timing")
 
 
 def library_path() -> str:
@@ -123,6 +124,7 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(i32)]
         L.mpa_batch_status.argtypes = [vp, vp]
         L.mpa_debug_fail_launch.argtypes = [i64, i32]
+        L.mpa_last_timing.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_char_p)]
         L.mpa_alu_peak.argtypes = [i32, ctypes.POINTER(dbl), vp]
         L.mpa_batch_set_persistent.argtypes = [vp, i32]
         L.mpa_batch_set_wait_limit.argtypes = [vp, i64]
@@ -463,8 +465,9 @@ class Batch:
         _check(lib().mpa_batch_set_persistent(self._h, 1 if on else 0), "mpa_batch_set_persistent")
 
     def set_wait_limit(self, polls: int) -> None:
-        """``mpa_batch_set_wait_limit``: polls (about 128 ns each) before a
-        wait of the persistent kernel gives up."""
+        """``mpa_batch_set_wait_limit``: polls before a wait of the batch's
+        persistent kernels (work queue, staged row pass) gives up; 0 makes
+        every such wait run out at once."""
         _check(lib().mpa_batch_set_wait_limit(self._h, int(polls)), "mpa_batch_set_wait_limit")
 
     def close(self) -> None:
@@ -581,6 +584,17 @@ def profile_read() -> dict:
             out[name.decode()] = (float(ms.value), int(n.value), float(b.value))
         k += 1
     return out
+
+
+def last_timing():
+    """``mpa_last_timing``: (entry-point name, device ms) of the most recent
+    entry-point call timed while ``profile(True)`` is on, or None if none was."""
+    ms, name = ctypes.c_double(), ctypes.c_char_p()
+    rc = lib().mpa_last_timing(ctypes.byref(ms), ctypes.byref(name))
+    if rc == 1:
+        return None
+    _check(rc, "mpa_last_timing")
+    return name.value.decode(), float(ms.value)
 
 
 def debug_fail_launch(after_launches: int, cuda_error: int = 2) -> None:

@@ -44,9 +44,20 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_status_strings(L):
-    for s in range(0, 9):
+    for s in range(0, 10):
         assert L.mpa_status_string(s) and L.mpa_status_string(s) != b"unknown status"
     assert L.mpa_status_string(99) == b"unknown status"
+
+
+def test_last_timing_without_a_timed_call(L):
+    """mpa_last_timing reports no call before any entry point has been timed
+    (mpa_profile(1) resets it) and refuses a NULL output."""
+    import ctypes as C
+    L.mpa_profile(1)
+    ms, name = C.c_double(-1.0), C.c_char_p()
+    assert L.mpa_last_timing(C.byref(ms), C.byref(name)) == 1 and ms.value == -1.0
+    assert L.mpa_last_timing(None, None) == 1
+    L.mpa_profile(0)
 
 
 def test_injected_launch_failure_reaches_the_caller_without_a_gpu(L):

@@ -502,3 +502,31 @@ def test_persistent_batch_wait_limit_reports_timeout(M):
     sp = specs[3]
     ref = oracle.mpa(A[3], sp.fiber, sp.T_ps, 0.0, sp.length_km, L, Mn, n_iter)
     assert oracle.rel_l2(host(f[3]), ref) < TOL["fp32"]
+
+
+def test_staged_row_pass_wait_limit_reports_timeout(M):
+    """Links of 2^19 and 2^20 modes take four-step node transforms whose row
+    pass is the staged persistent kernel (rows of 2^10 points at the default
+    split, through a shared staging buffer filled by bulk asynchronous copies).  A wait
+    limit of zero polls makes each of its waits run out at once: the groups
+    stop after waiting for the copies they started, mpa_batch_status reports
+    MPA_ERR_TIMEOUT, and with the normal limit the next propagation matches
+    the oracle.  Nothing faults or hangs: every wait is bounded."""
+    from paper_1101_0086_gb300.workloads import batch_links
+    specs = batch_links(n_links=2, seed=2, log2_n=(19, 20), spans=(1, 1))
+    assert sorted(sp.N for sp in specs) == [1 << 19, 1 << 20]
+    A = [sp.field() for sp in specs]
+    L, Mn, n_iter, z = 5.0, 8, 2, 5.0
+    f = [dev(a, "fp32") for a in A]
+    bt = M.Batch([(sp.fiber, sp.T_ps, z, x) for sp, x in zip(specs, f)], L, Mn, n_iter)
+    bt.set_wait_limit(0)
+    bt.propagate(use_graph=False)
+    assert bt.status_code() == 9
+    bt.set_wait_limit(1 << 22)
+    for x, a in zip(f, A):
+        x.copy_(dev(a, "fp32"))
+    bt.propagate(use_graph=False)
+    assert bt.status_code() == 0
+    for i, sp in enumerate(specs):
+        ref = oracle.mpa(A[i], sp.fiber, sp.T_ps, 0.0, z, L, Mn, n_iter)
+        assert oracle.rel_l2(host(f[i]), ref) < TOL["fp32"], i

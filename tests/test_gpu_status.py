@@ -155,3 +155,28 @@ def test_alu_peaks_are_plausible_for_a_gb300(M):
     # 152 SMs at up to 2.07 GHz: FP32 FMA <= 128 lanes/SM (80.5 TFLOP/s); FP64 far lower on this part
     assert 1e13 < f32 < 9e13, f32
     assert 1e10 < f64 < f32, f64
+
+
+def test_per_call_timing_brackets_the_kernels_of_the_call(M):
+    """mpa_last_timing: the device time of the last entry point called while
+    profiling is on covers the summed kernel times of that call."""
+    import torch
+    fib = dm_map(2)
+    plan = M.Plan(fib, N, T, 5.0, 20, 2, precision="fp32")
+    f = dev(field(), "fp32")
+    plan.propagate(f, 0.0, 50.0)  # first launches (attributes) outside the timing
+    torch.cuda.synchronize()
+    M.profile(True)
+    try:
+        assert M.last_timing() is None  # reset by profile(True)
+        plan.propagate(f, 0.0, 50.0)
+        name, ms = M.last_timing()
+        kern = sum(v[0] for v in M.profile_read().values())
+        assert name == "mpa_propagate"
+        assert kern > 0 and ms >= 0.9 * kern, (ms, kern)
+        assert ms < 1e3
+    finally:
+        M.profile(False)
+    # not timed once profiling is off: the last timed call stays
+    plan.propagate(f, 0.0, 50.0)
+    assert M.last_timing()[0] == "mpa_propagate"
