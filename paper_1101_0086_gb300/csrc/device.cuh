@@ -646,8 +646,20 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
     static constexpr int QL = (L / RL) * G / NT;
     static_assert((L / R0) * G % NT == 0 && (L / RL) * G % NT == 0, "butterflies must divide among threads");
 
+    struct NoHook {
+        __device__ __forceinline__ void operator()() const {}
+    };
     static __device__ __forceinline__ void run(C (&vin)[Q0][R0], C (&vout)[QL][RL], C* s, const C* hi, const C* lo) {
+        run(vin, vout, s, hi, lo, NoHook());
+    }
+    // hook() runs once the first pass has left the registers for shared
+    // memory (after its barrier; at the start for a single-pass transform),
+    // where the caller's own work needs the fewest registers.
+    template <class Hook>
+    static __device__ __forceinline__ void run(C (&vin)[Q0][R0], C (&vout)[QL][RL], C* s, const C* hi, const C* lo,
+                                               Hook&& hook) {
         if constexpr (NP == 1) {
+            hook();
 #pragma unroll
             for (int q = 0; q < Q0; ++q) {
                 Dft<R0, S, C>::run(vin[q]);
@@ -674,6 +686,7 @@ template <typename T, int L, int G, int NT, int RMAX, int S, int LAYOUT, int PSH
                 }
             }
             gsync<GRP, NT>();
+            hook();
             mid_passes<T, L, G, NT, RMAX, S, LAYOUT, PSH, SF, 1, NP, GRP>(s, hi, lo);
             // last pass (NS = L/RL, so k = j): gather j + r L/RL, twiddle W_L^{S r j}, DFT
 #pragma unroll

@@ -5,7 +5,7 @@
 namespace mpa {
 
 // The staged persistent column pass (kcs.cuh) for the MPA passes with
-// columns of 2^8 or 2^9 points and tiles within one node (N1 a multiple of
+// columns of 2^8 .. 2^10 points and tiles within one node (N1 a multiple of
 // the tile width), whenever the caller passes an error word for its bounded
 // waits; MPA_KC_STAGED=0 keeps kc_kernel everywhere.
 #ifndef MPA_KC_STAGED
@@ -42,11 +42,22 @@ static cudaError_t kcs_one(const KCParams<float>& p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int L> static bool kcs_fits(const KCParams<float>& p) {
+    return p.N1 % KCGeom<float, L>::G == 0 && p.ncols % KCGeom<float, L>::G == 0;
+}
+
 bool kc_staged(int mode, int logL, const KCParams<float>& p) {
     if (!MPA_KC_STAGED || !p.err || (mode != KC_MPA_PRE && mode != KC_MPA_POST) || p.npl <= 0) return false;
-    if (logL == 8) return p.N1 % KCGeom<float, 256>::G == 0 && p.ncols % KCGeom<float, 256>::G == 0;
-    if (logL == 9) return p.N1 % KCGeom<float, 512>::G == 0 && p.ncols % KCGeom<float, 512>::G == 0;
+    switch (logL) {
+        case 8: return kcs_fits<256>(p);
+        case 9: return kcs_fits<512>(p);
+        case 10: return kcs_fits<1024>(p);
+    }
     return false;
+}
+
+template <int L> static cudaError_t kcs_mode(int mode, const KCParams<float>& p, cudaStream_t st) {
+    return mode == KC_MPA_PRE ? kcs_one<L, KC_MPA_PRE>(p, st) : kcs_one<L, KC_MPA_POST>(p, st);
 }
 
 template <int L, int MODE>
@@ -97,8 +108,11 @@ static cudaError_t kc_mode(int mode, const KCParams<float>& p, cudaStream_t st) 
 template <>
 cudaError_t kc_launch<float>(int mode, int logL, const KCParams<float>& p, cudaStream_t st) {
     if (kc_staged(mode, logL, p)) {
-        if (logL == 8) return mode == KC_MPA_PRE ? kcs_one<256, KC_MPA_PRE>(p, st) : kcs_one<256, KC_MPA_POST>(p, st);
-        return mode == KC_MPA_PRE ? kcs_one<512, KC_MPA_PRE>(p, st) : kcs_one<512, KC_MPA_POST>(p, st);
+        switch (logL) {
+            case 8: return kcs_mode<256>(mode, p, st);
+            case 9: return kcs_mode<512>(mode, p, st);
+            case 10: return kcs_mode<1024>(mode, p, st);
+        }
     }
     switch (logL) {
         case 4: return kc_mode<16>(mode, p, st);

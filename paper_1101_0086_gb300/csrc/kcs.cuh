@@ -7,8 +7,8 @@
 // while the current ones are transformed.
 //
 // A column tile is G columns x L rows of one node (the tile never straddles
-// nodes: N1 is a multiple of G), i.e. L row segments of G complex64 at a
-// stride of N1 elements.  Such short strided segments are copied by the
+// nodes: N1 is a multiple of G), i.e. L row segments of G complex64 (64 to
+// 256 bytes for L = 2^10 .. 2^8) at a stride of N1 elements.  Such short strided segments are copied by the
 // NT threads of the group that releases the stage, 16 bytes per cp.async
 // (a bulk copy per segment was measured 2.3x slower: each bulk request has
 // a fixed cost), and each thread arrives on the receiving group's mbarrier
@@ -22,15 +22,18 @@
 namespace mpa {
 
 // Shared-memory layout: the stage (TE elements, row-major L x G), two
-// mbarriers, the twiddle tables of both groups, then per group its exchange
-// buffer and outer-factor tables.
+// mbarriers, four slots of node constants (those of CTA-local tile i in
+// slot i mod 4, copied with the tile), the twiddle tables of both groups,
+// then per group its exchange buffer and outer-factor tables.
 template <int L> struct KCSGeom {
     typedef KCGeom<float, L> Gm;
     typedef Tiling<float> P;
     static constexpr size_t al(size_t x) { return (x + 127) & ~(size_t)127; }
     static constexpr size_t STAGE_BYTES = (size_t)Gm::TE * sizeof(float2);
     static constexpr size_t BAR_OFF = STAGE_BYTES;
-    static constexpr size_t TW_OFF = BAR_OFF + 128;
+    static constexpr size_t NODE_OFF = BAR_OFF + 16;  // 4 NodeC slots: tile i's node constants in slot i mod 4
+    static constexpr size_t TW_OFF = BAR_OFF + 256;
+    static_assert(sizeof(NodeC) == 48 && 16 + 4 * sizeof(NodeC) <= 256, "node-constant slots");
     static constexpr size_t GRP_OFF = al(TW_OFF + (size_t)(TwDims<L>::NLO + TwDims<L>::NHI) * sizeof(float2));
     static constexpr size_t S_ELEMS = (size_t)Gm::TE + (Gm::TE >> P::PSH) + 1;
     static constexpr size_t GRP_BYTES = al((S_ELEMS + (size_t)Gm::G * (Gm::OLO + Gm::OHI)) * sizeof(float2));
@@ -60,11 +63,12 @@ __device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Group-wide: the NT threads start the copies of tile t (L row segments of
-// G elements) into the stage and each arrives on barrier b when its copies
+// G elements) into the stage, and three of them the copy of the tile's node
+// constants into `slot`; each thread arrives on barrier b when its copies
 // have landed.
 template <int L>
-__device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float2* stage, unsigned long long* b,
-                                          int tid) {
+__device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float2* stage, NodeC* slot,
+                                          unsigned long long* b, int tid) {
     constexpr int G = KCGeom<float, L>::G, NT = KCGeom<float, L>::NT;
     constexpr int CPR = G * (int)sizeof(float2) / 16;  // 16-byte chunks per row segment
     constexpr int NCH = L * CPR;
@@ -79,6 +83,9 @@ __device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float
         cp_async16(dst + (size_t)row * G * sizeof(float2) + ch * 16,
                    src + (long long)row * p.N1 * (long long)sizeof(float2) + ch * 16);
     }
+    if (tid < (int)(sizeof(NodeC) / 16))
+        cp_async16(reinterpret_cast<char*>(slot) + 16 * tid,
+                   reinterpret_cast<const char*>(p.nodes + p.loff[l] + jn) + 16 * tid);
     cp_async_arrive(b);
 }
 
@@ -95,13 +102,14 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
     typedef Xform<float, L, G, NT, P::RMAX, +1, LAYOUT_COL, P::PSH, true, 1> XF;
     typedef Xform<float, L, G, NT, P::RMAX, -1, LAYOUT_COL, P::PSH, false, 1> XI;
     typedef typename std::conditional<INV, XI, XF>::type XA;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    C* stage = reinterpret_cast<C*>(smem_raw);
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + SG::BAR_OFF);
-    C* thi = reinterpret_cast<C*>(smem_raw + SG::TW_OFF);
+    extern __shared__ __align__(128) unsigned char smem_staged[];
+    C* stage = reinterpret_cast<C*>(smem_staged);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_staged + SG::BAR_OFF);
+    NodeC* nslot = reinterpret_cast<NodeC*>(smem_staged + SG::NODE_OFF);
+    C* thi = reinterpret_cast<C*>(smem_staged + SG::TW_OFF);
     C* tlo = thi + TwDims<L>::NHI;
     const int grp = (int)(threadIdx.x / NT), tid = (int)(threadIdx.x & (NT - 1));
-    C* s = reinterpret_cast<C*>(smem_raw + SG::GRP_OFF + (size_t)grp * SG::GRP_BYTES);
+    C* s = reinterpret_cast<C*>(smem_staged + SG::GRP_OFF + (size_t)grp * SG::GRP_BYTES);
     C* olo = s + SG::S_ELEMS;   // [OLO][G]
     C* ohi = olo + G * Gm::OLO; // [OHI][G]
     const int ntiles = (int)(p.ncols / G);  // < 2^31: columns of a launch / G
@@ -115,7 +123,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
     tw_init<float, L>(thi, tlo, (int)threadIdx.x, SG::THREADS);
     __syncthreads();
     // the first tile is copied by group 1 (whose own first tile comes later)
-    if (grp == 1 && (int)blockIdx.x < ntiles) kcs_fetch<L>(p, blockIdx.x, stage, &bar[0], tid);
+    if (grp == 1 && (int)blockIdx.x < ntiles) kcs_fetch<L>(p, blockIdx.x, stage, &nslot[0], &bar[0], tid);
 
     unsigned k = 0;
     for (int i = grp;; i += 2, ++k) {
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
                 int l, jn;
                 long long c;
                 kcs_src(p, col0 + g, l, jn, c);
-                const NodeC nc = p.nodes[p.loff[l] + jn];
+                const NodeC nc = nslot[i & 3];  // copied with the tile
                 // phases in the order of their finite differences: s = -R0/2 .. R0/2-1,
                 // element r = (s + R0) mod R0 at k' = c + N1 (j + s L/R0)
                 const long long D = (long long)p.N1 * (L / XA::R0);
@@ -171,14 +179,21 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
             if (tid == 0) atomicOr(p.err, ERR_TIMEOUT);
             break;
         }
-        {
+        // The next tile's copies start here, or (LATE) once the first transform
+        // pass has moved the tile out of the registers: the inverse pass of
+        // 256-point columns spills registers if they start here, while the
+        // others lose time if they start later (the other group waits).
+        constexpr bool LATE = INV && L == 256;
+        auto fetch_next = [&] {
             const int tn = t + (int)gridDim.x;
-            if (tn < ntiles) kcs_fetch<L>(p, tn, stage, &bar[grp ^ 1], tid);
-        }
-
+            if (tn < ntiles) kcs_fetch<L>(p, tn, stage, &nslot[(i + 1) & 3], &bar[grp ^ 1], tid);
+        };
+        if constexpr (!LATE) fetch_next();
         constexpr int QO = XA::QL, RO = XA::RL;
         C vout[QO][RO];
-        XA::run(vin, vout, s, thi, tlo);
+        XA::run(vin, vout, s, thi, tlo, [&] {
+            if constexpr (LATE) fetch_next();
+        });
 
         // ---- epilogue and store: element j + r L/RO of column col0 + g
 #pragma unroll
@@ -202,7 +217,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
                     dst[(long long)row * p.N1] = cmul(vout[q][r], w);
                 }
             } else {
-                const NodeC nc = p.nodes[p.loff[l] + jn];
+                const NodeC nc = nslot[i & 3];  // copied with the tile
                 const long long D = (long long)p.N1 * (L / RO);
                 PhaseRun pr(c + (long long)j * p.N1 - (long long)(RO / 2) * D, D, nc);
 #pragma unroll

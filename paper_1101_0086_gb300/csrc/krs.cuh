@@ -9,8 +9,10 @@
 // buffer that the two groups share, by bulk asynchronous copies
 // (cp.async.bulk) whose bytes complete a phase of the receiving group's
 // mbarrier.  A group waits for its tile, copies it from the stage into
-// registers, and once all of its threads have done so (named barrier), one
-// of them starts the copy of tile i + 1 (the other group's) into the stage.
+// registers, and once all of its threads have done so (named barrier) and
+// the first transform pass has moved the data on into the group's exchange
+// buffer, one of them starts the copy of tile i + 1 (the other group's)
+// into the stage.
 // Each group transforms in its own exchange buffer with its own named
 // barrier, so the next tile streams in and the two groups' transforms
 // interleave on the SM while results go straight from registers to HBM.
@@ -120,13 +122,13 @@ __global__ void __launch_bounds__(KRSGeom<L>::THREADS, 1) krs_kernel(const KRPar
     typedef Xform<float, L, G, NT, P::RMAX, -1, LAYOUT_ROW, P::PSH, false, 1> XI;
     typedef Xform<float, L, G, NT, P::RMAX, +1, LAYOUT_ROW, P::PSH, true, 1> XF;
     static_assert(XI::RL == XF::R0, "inverse/forward junction radix");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    C* stage = reinterpret_cast<C*>(smem_raw);
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + SG::BAR_OFF);
-    C* thi = reinterpret_cast<C*>(smem_raw + SG::TW_OFF);
+    extern __shared__ __align__(128) unsigned char smem_staged[];
+    C* stage = reinterpret_cast<C*>(smem_staged);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_staged + SG::BAR_OFF);
+    C* thi = reinterpret_cast<C*>(smem_staged + SG::TW_OFF);
     C* tlo = thi + TwDims<L>::NHI;
     const int grp = (int)(threadIdx.x / NT), tid = (int)(threadIdx.x & (NT - 1));
-    C* s = reinterpret_cast<C*>(smem_raw + SG::GRP_OFF + (size_t)grp * SG::GRP_BYTES);
+    C* s = reinterpret_cast<C*>(smem_staged + SG::GRP_OFF + (size_t)grp * SG::GRP_BYTES);
     C* olo = s + SG::S_ELEMS;   // [G][OLO]
     C* ohi = olo + G * Gm::OLO; // [G][OHI]
     const int ntiles = (int)((p.nrows + G - 1) / G);  // < 2^31: rows of a launch / G
@@ -174,17 +176,16 @@ __global__ void __launch_bounds__(KRSGeom<L>::THREADS, 1) krs_kernel(const KRPar
             if (tid == 0) atomicOr(p.err, ERR_TIMEOUT);
             break;
         }
-        if (tid == 0) {
+        C vm[XI::QL][XI::RL];
+        // the next tile's copy starts once the first pass has left the registers
+        XI::run(vin, vm, s, thi, tlo, [&] {
             const int tn = t + (int)gridDim.x;
-            if (tn < ntiles) {
+            if (tid == 0 && tn < ntiles) {
                 fence_proxy_async_smem();
                 krs_fetch<L>(p, tn, stage, &bar[grp ^ 1]);
                 last_copy = i + 1;
             }
-        }
-
-        C vm[XI::QL][XI::RL];
-        XI::run(vin, vm, s, thi, tlo);
+        });
 #pragma unroll
         for (int q = 0; q < XI::QL; ++q) {
 #pragma unroll
