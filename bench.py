@@ -154,7 +154,8 @@ def source_hash() -> str:
     the FP32 instantiations of the column, row and on-chip passes)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1101_0086_gb300", "csrc")
-    for f in ("device.cuh", "kernels.cuh", "knc.cuh", "kc_f32.cu", "kr_f32.cu", "kn_f32.cu", "knc_f32.cu"):
+    for f in ("device.cuh", "kernels.cuh", "knc.cuh", "krs.cuh", "kcs.cuh", "kc_f32.cu", "kr_f32.cu", "kn_f32.cu",
+              "knc_f32.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

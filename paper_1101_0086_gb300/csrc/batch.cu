@@ -39,6 +39,8 @@ struct Group {
     long n_int = 0;
     size_t off_psi = 0, off_state = 0, off_psi0c = 0, off_nodes = 0, off_loff = 0, off_gain = 0, off_err = 0;
     size_t off_conv = 0, off_dprev = 0;  // Picard increment check: ConvState and D at node M per link
+    bool has_work = false;               // second set of node buffers (tile layout of the staged column passes)
+    size_t off_work = 0;
     // persistent work-queue kernel (FP32 groups on the single-CTA on-chip transform)
     bool persistent = false;
     unsigned int q_cap = 0;
@@ -159,8 +161,9 @@ int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
         if (rc) return rc;
     } else {
         for (long q = 0; q < g.n_int; ++q) {
-            int rc = mpa_levels<T>(s, M, b->n_iter, g.active[(size_t)q], psi, psi0c, state, nodes,
-                                   loff + (size_t)q * n, gain + (size_t)q * n, mon, 1, nullptr, st);
+            int rc = mpa_levels<T>(s, M, b->n_iter, g.active[(size_t)q], psi,
+                                   g.has_work ? reinterpret_cast<cx<T>*>(b->ws + g.off_work) : nullptr, psi0c, state,
+                                   nodes, loff + (size_t)q * n, gain + (size_t)q * n, mon, 1, nullptr, st);
             if (rc) return rc;
         }
     }
@@ -314,6 +317,9 @@ int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_
         }
         g.off_psi = off;
         off = align256(off + (size_t)n * (M + 1) * N * b->csize);
+        g.has_work = wants_work_buffers(N, precision);
+        g.off_work = off;
+        if (g.has_work) off = align256(off + (size_t)n * (M + 1) * N * b->csize);
         g.off_state = off;
         off = align256(off + (size_t)n * N * sizeof(double2));
         g.off_psi0c = precision == MPA_FP32 ? off : g.off_state;
@@ -500,6 +506,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                 rc = b->prec == MPA_FP32
                          ? mpa_levels<float>(g.sp, b->M, b->n_iter, g.active[0],
                                              reinterpret_cast<float2*>(b->ws + g.off_psi),
+                                             g.has_work ? reinterpret_cast<float2*>(b->ws + g.off_work) : nullptr,
                                              reinterpret_cast<float2*>(b->ws + g.off_psi0c),
                                              reinterpret_cast<double2*>(b->ws + g.off_state),
                                              reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
@@ -507,7 +514,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                                              reinterpret_cast<const double*>(b->ws + g.off_gain),
                                              group_monitor(b->ws, g, b->spin_limit), 1, nullptr, st)
                          : mpa_levels<double>(g.sp, b->M, b->n_iter, g.active[0],
-                                              reinterpret_cast<double2*>(b->ws + g.off_psi),
+                                              reinterpret_cast<double2*>(b->ws + g.off_psi), nullptr,
                                               reinterpret_cast<double2*>(b->ws + g.off_psi0c),
                                               reinterpret_cast<double2*>(b->ws + g.off_state),
                                               reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),

@@ -621,7 +621,7 @@ __device__ __forceinline__ void mid_passes(cx<T>* s, const cx<T>* hi, const cx<T
 }
 
 // Butterfly b of a radix-R pass -> (j, g).
-template <int LAYOUT, int L, int G, int R> __device__ __forceinline__ void bmap(int b, int& j, int& g) {
+template <int LAYOUT, int L, int G, int R> __host__ __device__ __forceinline__ void bmap(int b, int& j, int& g) {
     if constexpr (LAYOUT == LAYOUT_COL) {
         j = b / G;
         g = b % G;

@@ -250,11 +250,18 @@ inline int fft_inverse(const Split& s, cx<T>* spec, cx<T>* out, cudaStream_t st)
 }
 
 // One level-synchronous interval (MPA steps 2-7) for nl links stored
-// link-major; defined in plan.cu for float and double.
+// link-major; defined in plan.cu for float and double.  `work` (may be null)
+// is a second set of node buffers of psi's size: with it, FP32 levels whose
+// column passes run staged keep the node spectra in psi in the tile layout
+// of the staged column pass and transform in `work` (a pass that changes
+// the layout cannot work in place).
 template <typename T>
-int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi0c, double2* state,
+int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* work, cx<T>* psi0c, double2* state,
                const NodeC* nodes, const int* loff, const double* gain, const Monitor& mon, int scan_mode,
                double2* out, cudaStream_t st);
+// Whether a plan or batch group of N modes in this precision gets the
+// second set of node buffers (the staged column passes need N1 >= 32).
+inline bool wants_work_buffers(long long N, int prec) { return prec == MPA_FP32 && N >= (1ll << 13); }
 
 // Relative Picard increment below which a non-shrinking increment is
 // rounding noise of the node-M sums rather than divergence.

@@ -42,6 +42,8 @@ static cudaError_t kcs_one(const KCParams<float>& p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+static constexpr int ilog2_const(int x) { return x <= 1 ? 0 : 1 + ilog2_const(x / 2); }
+
 template <int L> static bool kcs_fits(const KCParams<float>& p) {
     return p.N1 % KCGeom<float, L>::G == 0 && p.ncols % KCGeom<float, L>::G == 0;
 }
@@ -54,6 +56,15 @@ bool kc_staged(int mode, int logL, const KCParams<float>& p) {
         case 10: return kcs_fits<1024>(p);
     }
     return false;
+}
+
+int kcs_tile_log_cols(int logL) {
+    switch (logL) {
+        case 8: return ilog2_const(KCGeom<float, 256>::G);
+        case 9: return ilog2_const(KCGeom<float, 512>::G);
+        case 10: return ilog2_const(KCGeom<float, 1024>::G);
+    }
+    return -1;
 }
 
 template <int L> static cudaError_t kcs_mode(int mode, const KCParams<float>& p, cudaStream_t st) {

@@ -41,14 +41,34 @@ template <int L> struct KCSGeom {
     static constexpr int NT = Gm::NT, THREADS = 2 * Gm::NT;
 };
 
-// Source of column col (node and link from the launch layout, as kc_kernel).
-__device__ __forceinline__ const float2* kcs_src(const KCParams<float>& p, long long col, int& l, int& jn,
-                                                 long long& c) {
+// Node and link of column col (the launch layout of kc_kernel), c its column
+// within the node.
+__host__ __device__ __forceinline__ void kcs_node(const KCParams<float>& p, long long col, int& l, int& jn, long long& c) {
     const int node = (int)(col >> p.logN1);
     l = node / p.npl;
     jn = node - l * p.npl;
     c = col & (long long)(p.N1 - 1);
-    return (p.src0 && jn == 0) ? p.src0 + l * p.src0_lstride + c : p.src + l * p.src_lstride + jn * p.src_stride + c;
+}
+// Where the tile of G columns starting at column c of (link l, node jn)
+// begins and the distance between its rows, in elements: natural order
+// (row stride N1) or the tile layout (the tile's G x L elements contiguous
+// at c L, row stride G).
+template <int L, int G>
+__host__ __device__ __forceinline__ const float2* kcs_src(const KCParams<float>& p, int l, int jn, long long c,
+                                                          long long& rs) {
+    if (p.src0 && jn == 0) {
+        rs = p.N1;
+        return p.src0 + l * p.src0_lstride + c;
+    }
+    const float2* b = p.src + l * p.src_lstride + jn * p.src_stride;
+    rs = p.tiled_in ? G : p.N1;
+    return p.tiled_in ? b + c * L : b + c;
+}
+template <int L, int G>
+__host__ __device__ __forceinline__ float2* kcs_dst(const KCParams<float>& p, int l, int jn, long long c, long long& rs) {
+    float2* b = p.dst + l * p.dst_lstride + jn * p.dst_stride;
+    rs = p.tiled_out ? G : p.N1;
+    return p.tiled_out ? b + c * L : b + c;
 }
 
 // 16-byte global -> shared copy through L2 (cp.async.cg)
@@ -74,20 +94,41 @@ __device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float
     constexpr int NCH = L * CPR;
     static_assert(NCH % NT == 0, "whole chunks per thread");
     int l, jn;
-    long long c;
-    const char* src = reinterpret_cast<const char*>(kcs_src(p, (long long)t * G, l, jn, c));
+    long long c, rs;
+    kcs_node(p, (long long)t * G, l, jn, c);
+    const char* src = reinterpret_cast<const char*>(kcs_src<L, G>(p, l, jn, c, rs));
     char* dst = reinterpret_cast<char*>(stage);
 #pragma unroll
     for (int k = 0; k < NCH / NT; ++k) {
         const int id = tid + k * NT, row = id / CPR, ch = id % CPR;
         cp_async16(dst + (size_t)row * G * sizeof(float2) + ch * 16,
-                   src + (long long)row * p.N1 * (long long)sizeof(float2) + ch * 16);
+                   src + (long long)row * rs * (long long)sizeof(float2) + ch * 16);
     }
     if (tid < (int)(sizeof(NodeC) / 16))
         cp_async16(reinterpret_cast<char*>(slot) + 16 * tid,
                    reinterpret_cast<const char*>(p.nodes + p.loff[l] + jn) + 16 * tid);
     cp_async_arrive(b);
 }
+
+// Group-wide: asks L2 for tile t's row segments (cp.async.bulk.prefetch), so
+// that the copies of the tile, started one tile later, find them there.
+template <int L>
+__device__ __forceinline__ void kcs_prefetch(const KCParams<float>& p, int t, int tid) {
+    constexpr int G = KCGeom<float, L>::G, NT = KCGeom<float, L>::NT;
+    int l, jn;
+    long long c, rs;
+    kcs_node(p, (long long)t * G, l, jn, c);
+    const float2* src = kcs_src<L, G>(p, l, jn, c, rs);
+    for (int row = tid; row < L; row += NT) prefetch_l2(src + (long long)row * rs, (unsigned)(G * sizeof(float2)));
+}
+
+// L2 prefetch of the tile after next in the staged column passes (bit 0:
+// inverse pass, bit 1: forward pass).  Measured on the 2^20 link: slower in
+// both passes (inverse 69 -> 81 ms, forward 54 -> 75 ms per 100 km at the
+// 2^10 x 2^10 split), so off.
+#ifndef MPA_KCS_L2PF
+#define MPA_KCS_L2PF 0
+#endif
 
 template <int L, int MODE>
 __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
@@ -152,7 +193,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
             if constexpr (INV) {
                 int l, jn;
                 long long c;
-                kcs_src(p, col0 + g, l, jn, c);
+                kcs_node(p, col0 + g, l, jn, c);
                 const NodeC nc = nslot[i & 3];  // copied with the tile
                 // phases in the order of their finite differences: s = -R0/2 .. R0/2-1,
                 // element r = (s + R0) mod R0 at k' = c + N1 (j + s L/R0)
@@ -187,6 +228,11 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
         auto fetch_next = [&] {
             const int tn = t + (int)gridDim.x;
             if (tn < ntiles) kcs_fetch<L>(p, tn, stage, &nslot[(i + 1) & 3], &bar[grp ^ 1], tid);
+            constexpr bool PF = (MPA_KCS_L2PF >> (INV ? 0 : 1)) & 1;
+            if constexpr (PF) {
+                const int tp = tn + (int)gridDim.x;
+                if (tp < ntiles) kcs_prefetch<L>(p, tp, tid);
+            }
         };
         if constexpr (!LATE) fetch_next();
         constexpr int QO = XA::QL, RO = XA::RL;
@@ -201,9 +247,10 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
             int j, g;
             bmap<LAYOUT_COL, L, G, RO>(tid + q * NT, j, g);
             int l, jn;
-            long long c;
-            kcs_src(p, col0 + g, l, jn, c);
-            C* dst = p.dst + l * p.dst_lstride + jn * p.dst_stride + c;
+            long long c, rs;
+            kcs_node(p, col0 + g, l, jn, c);
+            // natural order, or the tile layout: column c - g of the tile block, element g
+            C* dst = kcs_dst<L, G>(p, l, jn, c - g, rs) + g;
             if constexpr (INV) {
                 constexpr bool HOIST = (L / RO) % Gm::OLO == 0;
                 C wlo = mkc(1.f, 0.f);
@@ -214,7 +261,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
                     // four-step factor W_N^{-n2 k1}, n2 = row
                     C w = HOIST ? wlo : olo[(row & (Gm::OLO - 1)) * G + g];
                     if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
-                    dst[(long long)row * p.N1] = cmul(vout[q][r], w);
+                    dst[(long long)row * rs] = cmul(vout[q][r], w);
                 }
             } else {
                 const NodeC nc = nslot[i & 3];  // copied with the tile
@@ -225,7 +272,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
                     const int r = (u + RO / 2) % RO;
                     const int row = j + r * (L / RO);
                     // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
-                    dst[(long long)row * p.N1] = cscale(cmul(vout[q][r], cconj(expi_turns_poly(pr.next()))), (float)nc.post);
+                    dst[(long long)row * rs] = cscale(cmul(vout[q][r], cconj(expi_turns_poly(pr.next()))), (float)nc.post);
                 }
             }
         }

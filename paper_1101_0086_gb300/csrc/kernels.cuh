@@ -54,6 +54,11 @@ template <typename T> struct KCParams {
     NodeC flow;             // SS: constants of the linear step
     unsigned int* err;      // error word of the staged column pass (null: kc_kernel only)
     long long spin_limit;   // polls of each bounded wait of the staged column pass
+    // staged column pass only: sources other than src0 (tiled_in) / the
+    // destination (tiled_out) hold node spectra in the tile layout (column
+    // block b = k1 / G of a node as G x N2 contiguous elements, element
+    // (k2, k1 mod G) at b G N2 + k2 G + k1 mod G) instead of natural order
+    int tiled_in, tiled_out;
 };
 
 template <typename T> struct KRParams {
@@ -828,6 +833,16 @@ struct Monitor {
     long long spin_limit;  // polls of each bounded wait of a persistent kernel
 };
 
+// Natural index k = k1 + N1 k2 of position i of a node spectrum held in the
+// tile layout of the staged column pass: column blocks of G = 2^logG columns,
+// each G x N2 (N2 = 2^logL) contiguous, element (k2, k1 mod G) of block
+// k1 / G at (k1 / G) G N2 + k2 G + k1 mod G.
+__host__ __device__ __forceinline__ long long tile_to_natural(long long i, int logG, int logL, long long N) {
+    const long long tb = i >> (logG + logL), rem = i & ((1ll << (logG + logL)) - 1);
+    const long long k2 = rem >> logG, k1 = (tb << logG) + (rem & ((1ll << logG) - 1));
+    return k1 + k2 * (N >> logL);
+}
+
 template <typename T> struct ScanParams {
     cx<T>* psi;          // link l's node j at psi + (l (M+1) + j) N
     long long N;
@@ -846,6 +861,10 @@ template <typename T> struct ScanParams {
     float2* dprev;       // D^{(n)} at node M, link l at + l N (written unless last level)
     int level, n_iter;
     double floor_rel;    // increments below this relative size are rounding, not divergence
+    // tile_logG > 0: psi and dprev hold node spectra in the tile layout of the
+    // staged column pass (G = 2^tile_logG columns of N2 = 2^tile_logL rows,
+    // N1 = N / N2 columns); psi0c, state and out stay in natural order
+    int tile_logG, tile_logL;
 };
 
 // Adds this block's sums to link l's accumulators; the last block of the
@@ -900,11 +919,13 @@ __device__ __forceinline__ void conv_close(ConvState* cs, unsigned int* err, dou
 // power of two >= 256), so every thread has a frequency and takes part in
 // the block reduction of the increment check.
 template <typename T, bool CG>
-__device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long long k, unsigned nblk) {
+__device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long long i, unsigned nblk) {
     typedef cx<T> C;
     const long long lo = (long long)l * p.N;
     cx<T>* psi = p.psi + lo * (p.M + 1);
-    const C v0 = ldx<CG>(psi + k);
+    // i: position in the node buffers; k: the frequency there (natural order)
+    const long long k = p.tile_logG > 0 ? tile_to_natural(i, p.tile_logG, p.tile_logL, p.N) : i;
+    const C v0 = ldx<CG>(psi + i);
     T rx = T(0.5) * v0.x, ry = T(0.5) * v0.y, cxx = T(0), cyy = T(0);
     const C p0 = ldx<CG>(p.psi0c + lo + k);
     C vl = v0;
@@ -913,14 +934,14 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
     constexpr int U = 8;
     C nxt[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) nxt[u] = (1 + u <= p.M) ? ldx<CG>(psi + (long long)(1 + u) * p.N + k) : mkc(T(0), T(0));
+    for (int u = 0; u < U; ++u) nxt[u] = (1 + u <= p.M) ? ldx<CG>(psi + (long long)(1 + u) * p.N + i) : mkc(T(0), T(0));
     for (int jb = 1; jb <= p.M; jb += U) {
         C cur[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             cur[u] = nxt[u];
             const int jn = jb + U + u;
-            nxt[u] = (jn <= p.M) ? ldx<CG>(psi + (long long)jn * p.N + k) : mkc(T(0), T(0));
+            nxt[u] = (jn <= p.M) ? ldx<CG>(psi + (long long)jn * p.N + i) : mkc(T(0), T(0));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -930,7 +951,7 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
             if (p.mode == 0) {
                 // psi_0 + i (R + V_j/2), R = running sum (compensation removed)
                 const T sx = (rx - cxx) + T(0.5) * vl.x, sy = (ry - cyy) + T(0.5) * vl.y;
-                psi[(long long)j * p.N + k] = mkc(p0.x - sy, p0.y + sx);
+                psi[(long long)j * p.N + i] = mkc(p0.x - sy, p0.y + sx);
             }
             if constexpr (sizeof(T) == 4) {
                 kahan_add(rx, cxx, vl.x);
@@ -948,11 +969,11 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
         // Picard increment at node M against the previous level's D
         double dx = sx, dy = sy;
         if (p.level > 0) {
-            const float2 d0 = ldx<CG>(p.dprev + lo + k);
+            const float2 d0 = ldx<CG>(p.dprev + lo + i);
             dx -= (double)d0.x;
             dy -= (double)d0.y;
         }
-        if (p.level < p.n_iter - 1) p.dprev[lo + k] = make_float2((float)sx, (float)sy);
+        if (p.level < p.n_iter - 1) p.dprev[lo + i] = make_float2((float)sx, (float)sy);
         const double px = (double)p0.x - sy, py = (double)p0.y + sx;
         conv_close(p.conv + l, p.err, dx * dx + dy * dy, px * px + py * py, p.level, p.n_iter - 1, p.floor_rel, nblk);
     }

@@ -88,6 +88,9 @@ template <typename T> cudaError_t kr_launch(int mode, int logL, const KRParams<T
 bool kr_staged(int mode, int logL, const KRParams<float>& p);
 // whether kc_launch<float> takes the staged persistent column pass (kcs.cuh)
 bool kc_staged(int mode, int logL, const KCParams<float>& p);
+// log2 of the columns per tile of the staged column pass for 2^logL-point
+// columns (the tile layout's G), or -1 where there is none
+int kcs_tile_log_cols(int logL);
 // On-chip whole node transform for N = 2^logL, 2^8 <= N <= 2^kn_log_max:
 // one CTA per node up to 2^14 (FP32) / 2^13 (FP64), a cluster of 2 or 4 CTAs
 // over distributed shared memory for FP32 2^15 and 2^16 (knc_launch).

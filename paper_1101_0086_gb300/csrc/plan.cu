@@ -36,11 +36,12 @@ namespace host {
 // Every iteration covers nodes 0..M of every link; node 0 always reads
 // psi_0, so V_0 (identical at every iteration) is simply recomputed.
 template <typename T>
-int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi0c, double2* state,
+int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* work, cx<T>* psi0c, double2* state,
                const NodeC* nodes, const int* loff, const double* gain, const Monitor& mon, int scan_mode,
                double2* out, cudaStream_t st) {
     const long long N = s.N;
     const int npl = M + 1;
+    int tile_log_g = 0;  // > 0: node spectra between the passes in the staged column pass's tile layout
     for (int n = 0; n < n_iter; ++n) {
         if (s.onchip) {
             // steps 2-4 and the weight of Eq. (6), one launch for every node of every link
@@ -80,15 +81,27 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi
         c.loff = loff;
         c.err = mon.err;
         c.spin_limit = mon.spin_limit;
+        if constexpr (sizeof(T) == 4)
+            tile_log_g = work && kc_staged(KC_MPA_POST, s.logN2, c) ? kcs_tile_log_cols(s.logN2) : 0;
+        // Tile layout: the forward pass writes V_j into psi in the tile layout
+        // of the staged column pass, the scan keeps it for psi^{(n+1)}, and the
+        // next inverse pass reads whole tiles from psi and writes the natural
+        // order into `work`, where the row pass and the forward pass run.
+        cx<T>* xw = tile_log_g > 0 ? work : psi;
+        c.tiled_in = n > 0 && tile_log_g > 0;
+        c.dst = xw;
         MPA_TRY(kc_launch<T>(KC_MPA_PRE, s.logN2, c, st));
-        KRParams<T> r{psi, (long long)nl * npl * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
+        KRParams<T> r{xw, (long long)nl * npl * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
         r.err = mon.err;
         r.spin_limit = mon.spin_limit;
         MPA_TRY(kr_launch<T>(KR_MPA, s.logN1, r, st));
-        c.src = psi;
+        c.src = xw;
         c.src_stride = N;
         c.src_lstride = (long long)npl * N;
         c.src0 = nullptr;
+        c.dst = psi;
+        c.tiled_in = 0;
+        c.tiled_out = tile_log_g > 0;
         MPA_TRY(kc_launch<T>(KC_MPA_POST, s.logN2, c, st));
         }
         // step 5 (Eq. (6)); on the last iteration fused with step 7
@@ -110,15 +123,17 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* psi
         q.level = n;
         q.n_iter = n_iter;
         q.floor_rel = kDivergenceFloor;
+        q.tile_logG = tile_log_g;
+        q.tile_logL = s.logN2;
         MPA_TRY(scan_launch<T>(q, nl, st));
     }
     return MPA_OK;
 }
 
-template int mpa_levels<float>(const Split&, int, int, int, float2*, float2*, double2*, const NodeC*, const int*,
-                               const double*, const Monitor&, int, double2*, cudaStream_t);
-template int mpa_levels<double>(const Split&, int, int, int, double2*, double2*, double2*, const NodeC*, const int*,
-                                const double*, const Monitor&, int, double2*, cudaStream_t);
+template int mpa_levels<float>(const Split&, int, int, int, float2*, float2*, float2*, double2*, const NodeC*,
+                               const int*, const double*, const Monitor&, int, double2*, cudaStream_t);
+template int mpa_levels<double>(const Split&, int, int, int, double2*, double2*, double2*, double2*, const NodeC*,
+                                const int*, const double*, const Monitor&, int, double2*, cudaStream_t);
 
 }  // namespace host
 }  // namespace mpa
@@ -155,6 +170,7 @@ int run_interval(mpa_plan* p, int type, long n_amp, int scan_mode, double2* out,
     const double* gains = reinterpret_cast<const double*>(p->ws + p->off_gains);
     if (n_amp < 0 || n_amp >= kMaxAmpsPerInterval) return MPA_ERR_GRID;
     return mpa_levels<T>(p->sp, p->M, p->n_iter, 1, reinterpret_cast<cx<T>*>(p->ws + p->off_psi),
+                         p->has_work ? reinterpret_cast<cx<T>*>(p->ws + p->off_work2) : nullptr,
                          reinterpret_cast<cx<T>*>(p->ws + p->off_psi0c),
                          reinterpret_cast<double2*>(p->ws + p->off_state),
                          reinterpret_cast<const NodeC*>(p->ws + p->off_nodes), toff + type, gains + n_amp,
@@ -446,7 +462,9 @@ int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_pl
         return MPA_OK;
     }
     p->off_psi = 0;
-    p->off_state = align256(p->off_psi + (size_t)(M + 1) * N * p->csize);
+    p->has_work = wants_work_buffers(p->sp.N, p->prec);
+    p->off_work2 = align256(p->off_psi + (size_t)(M + 1) * N * p->csize);
+    p->off_state = p->has_work ? align256(p->off_work2 + (size_t)(M + 1) * N * p->csize) : p->off_work2;
     p->off_psi0c = align256(p->off_state + N * sizeof(double2));
     const size_t psi0c_bytes = p->prec == MPA_FP32 ? N * sizeof(float2) : 0;
     if (p->prec == MPA_FP64) p->off_psi0c = p->off_state;  // the FP64 state is its own working copy

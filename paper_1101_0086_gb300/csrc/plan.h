@@ -17,6 +17,8 @@ struct mpa_plan {
     size_t csize;               // bytes per complex sample
     size_t off_psi, off_state, off_psi0c, off_nodes, off_err, off_toff, off_gains, ws_need;
     size_t off_conv = 0, off_dprev = 0;  // Picard increment check (ConvState, D at node M)
+    bool has_work = false;               // second set of node buffers (tile layout of the staged column passes)
+    size_t off_work2 = 0;
     // wavefront schedule (FP32): S = n_iter slots of B node buffers
     bool wf = false;
     int B = 0;
