@@ -741,6 +741,29 @@ def run_grad(args, world, rank, local):
                 gi, gs, gb = mpa.ss_adjoint(a, g_out, fib, w.T_ps, w.ss_dz_km, 0.0, km, stream=stream)
             return loss, gi - direct, gs, gb, out, g_out
 
+        if meth == "mpa":
+            # the forward autotuner ranks splits by the forward pass alone; a
+            # gradient also runs the reverse kernels, so the split is chosen
+            # among the tuner's and its neighbours by timing one gradient each
+            # (before the timed region, like the tuner itself)
+            tuned = plan.log2_n2
+            cand = sorted({c for c in (tuned, tuned - 1, tuned - 2, tuned + 1) if c >= 4})
+            best, best_t = tuned, float("inf")
+            for c in cand:
+                try:
+                    plan.set_split(c)
+                except mpa.MPAError:
+                    continue
+                step()
+                s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                step()
+                e0.record(stream)
+                torch.cuda.synchronize()
+                if s0.elapsed_time(e0) < best_t:
+                    best, best_t = c, s0.elapsed_time(e0)
+            plan.set_split(best)
+            head["split"] = f"N1 x N2 = 2^{int(np.log2(N)) - best} x 2^{best} (fastest gradient of splits {cand})"
         reps = args.steps if meth == "mpa" else 1
         for _ in range(args.warmup if meth == "mpa" else 1):
             step()
@@ -790,13 +813,14 @@ def run_grad(args, world, rank, local):
                                  "launches_per_gradient": launches / reps,
                                  "grad_sigma_first": [float(x) for x in gs[:2]],
                                  "grad_beta2_first": [float(x) for x in gb[:2]], "kernels": kern}
+    split = head.pop("split", None)
     line = {"metric": "gradient evaluations in mode*km/s (forward with checkpoints + loss + reverse pass)",
             "value": res[next(iter(res))]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "N": N, "km": km, "n_segments": 2 * n_spans,
                        "loss": "mean |D^-1 A_out - A_in|^2, D = exact linear flow",
-                       "l2": "inputs larger than L2 (each gradient moves tens of GB)"},
+                       "l2": "inputs larger than L2 (each gradient moves tens of GB)", "split": split},
             **head, "methods": res}
     print(json.dumps(line), flush=True)
     return 0

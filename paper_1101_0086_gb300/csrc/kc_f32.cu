@@ -5,7 +5,7 @@
 namespace mpa {
 
 // The staged persistent column pass (kcs.cuh) for the MPA passes with
-// columns of 2^8 .. 2^10 points and tiles within one node (N1 a multiple of
+// columns of 2^8 .. 2^11 points and tiles within one node (N1 a multiple of
 // the tile width), whenever the caller passes an error word for its bounded
 // waits; MPA_KC_STAGED=0 keeps kc_kernel everywhere.
 #ifndef MPA_KC_STAGED
@@ -23,7 +23,7 @@ static cudaError_t kcs_one(const KCParams<float>& p, cudaStream_t st) {
                                     (int)SG::smem_bytes);
     });
     if (ea != cudaSuccess) return ea;
-    const long long ntiles = p.ncols / KCGeom<float, L>::G;
+    const long long ntiles = p.ncols / KCSTile<L>::G;
     if (ntiles <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -45,7 +45,7 @@ static cudaError_t kcs_one(const KCParams<float>& p, cudaStream_t st) {
 static constexpr int ilog2_const(int x) { return x <= 1 ? 0 : 1 + ilog2_const(x / 2); }
 
 template <int L> static bool kcs_fits(const KCParams<float>& p) {
-    return p.N1 % KCGeom<float, L>::G == 0 && p.ncols % KCGeom<float, L>::G == 0;
+    return p.N1 % KCSTile<L>::G == 0 && p.ncols % KCSTile<L>::G == 0;
 }
 
 bool kc_staged(int mode, int logL, const KCParams<float>& p) {
@@ -54,15 +54,17 @@ bool kc_staged(int mode, int logL, const KCParams<float>& p) {
         case 8: return kcs_fits<256>(p);
         case 9: return kcs_fits<512>(p);
         case 10: return kcs_fits<1024>(p);
+        case 11: return kcs_fits<2048>(p);
     }
     return false;
 }
 
 int kcs_tile_log_cols(int logL) {
     switch (logL) {
-        case 8: return ilog2_const(KCGeom<float, 256>::G);
-        case 9: return ilog2_const(KCGeom<float, 512>::G);
-        case 10: return ilog2_const(KCGeom<float, 1024>::G);
+        case 8: return ilog2_const(KCSTile<256>::G);
+        case 9: return ilog2_const(KCSTile<512>::G);
+        case 10: return ilog2_const(KCSTile<1024>::G);
+        case 11: return ilog2_const(KCSTile<2048>::G);
     }
     return -1;
 }
@@ -123,6 +125,7 @@ cudaError_t kc_launch<float>(int mode, int logL, const KCParams<float>& p, cudaS
             case 8: return kcs_mode<256>(mode, p, st);
             case 9: return kcs_mode<512>(mode, p, st);
             case 10: return kcs_mode<1024>(mode, p, st);
+            case 11: return kcs_mode<2048>(mode, p, st);
         }
     }
     switch (logL) {

@@ -7,8 +7,8 @@
 // while the current ones are transformed.
 //
 // A column tile is G columns x L rows of one node (the tile never straddles
-// nodes: N1 is a multiple of G), i.e. L row segments of G complex64 (64 to
-// 256 bytes for L = 2^10 .. 2^8) at a stride of N1 elements.  Such short strided segments are copied by the
+// nodes: N1 is a multiple of G), i.e. L row segments of G complex64 (32 to
+// 256 bytes for L = 2^11 .. 2^8) at a stride of N1 elements.  Such short strided segments are copied by the
 // NT threads of the group that releases the stage, 16 bytes per cp.async
 // (a bulk copy per segment was measured 2.3x slower: each bulk request has
 // a fixed cost), and each thread arrives on the receiving group's mbarrier
@@ -21,12 +21,22 @@
 
 namespace mpa {
 
+// Tile of the staged column pass: G = 8192 / L columns (at least 4) of L
+// rows, 32 elements per thread; the per-tile kc_kernel keeps G >= 8, which
+// makes 2^11-point column tiles 16384 elements, too large to stage.  The
+// outer-factor split is kc_kernel's.
+template <int L> struct KCSTile {
+    typedef KCGeom<float, L> K;
+    static constexpr int G = (8192 / L) > 4 ? (8192 / L) : 4, TE = G * L, NT = TE / Tiling<float>::E;
+    static constexpr int OSH = K::OSH, OLO = K::OLO, OHI = K::OHI;
+};
+
 // Shared-memory layout: the stage (TE elements, row-major L x G), two
 // mbarriers, four slots of node constants (those of CTA-local tile i in
 // slot i mod 4, copied with the tile), the twiddle tables of both groups,
 // then per group its exchange buffer and outer-factor tables.
 template <int L> struct KCSGeom {
-    typedef KCGeom<float, L> Gm;
+    typedef KCSTile<L> Gm;
     typedef Tiling<float> P;
     static constexpr size_t al(size_t x) { return (x + 127) & ~(size_t)127; }
     static constexpr size_t STAGE_BYTES = (size_t)Gm::TE * sizeof(float2);
@@ -89,7 +99,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int L>
 __device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float2* stage, NodeC* slot,
                                           unsigned long long* b, int tid) {
-    constexpr int G = KCGeom<float, L>::G, NT = KCGeom<float, L>::NT;
+    constexpr int G = KCSTile<L>::G, NT = KCSTile<L>::NT;
     constexpr int CPR = G * (int)sizeof(float2) / 16;  // 16-byte chunks per row segment
     constexpr int NCH = L * CPR;
     static_assert(NCH % NT == 0, "whole chunks per thread");
@@ -114,7 +124,7 @@ __device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float
 // that the copies of the tile, started one tile later, find them there.
 template <int L>
 __device__ __forceinline__ void kcs_prefetch(const KCParams<float>& p, int t, int tid) {
-    constexpr int G = KCGeom<float, L>::G, NT = KCGeom<float, L>::NT;
+    constexpr int G = KCSTile<L>::G, NT = KCSTile<L>::NT;
     int l, jn;
     long long c, rs;
     kcs_node(p, (long long)t * G, l, jn, c);
@@ -135,7 +145,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
     kcs_kernel(const KCParams<float> p) {
     static_assert(MODE == KC_MPA_PRE || MODE == KC_MPA_POST, "the MPA column passes");
     typedef float2 C;
-    typedef KCGeom<float, L> Gm;
+    typedef KCSTile<L> Gm;
     typedef KCSGeom<L> SG;
     typedef Tiling<float> P;
     constexpr int G = Gm::G, NT = Gm::NT;
@@ -171,6 +181,10 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
         const int t = (int)blockIdx.x + i * (int)gridDim.x;
         if (t >= ntiles) break;
         const long long col0 = (long long)t * G;
+        // the tile's link, node and first column within the node (a tile never straddles nodes)
+        int tl, tjn;
+        long long tc0;
+        kcs_node(p, col0, tl, tjn, tc0);
         gsync<1, NT>();  // the group's previous tile no longer needs s, olo, ohi
         if constexpr (INV) {
             // W_N^{-n2 k1} for the tile's columns: olo[m][g] = W^{-k1 m}, ohi[h][g] = W^{-k1 32 h}
@@ -191,9 +205,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
             int j, g;
             bmap<LAYOUT_COL, L, G, XA::R0>(tid + q * NT, j, g);
             if constexpr (INV) {
-                int l, jn;
-                long long c;
-                kcs_node(p, col0 + g, l, jn, c);
+                const long long c = tc0 + g;
                 const NodeC nc = nslot[i & 3];  // copied with the tile
                 // phases in the order of their finite differences: s = -R0/2 .. R0/2-1,
                 // element r = (s + R0) mod R0 at k' = c + N1 (j + s L/R0)
@@ -222,9 +234,9 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
         }
         // The next tile's copies start here, or (LATE) once the first transform
         // pass has moved the tile out of the registers: the inverse pass of
-        // 256-point columns spills registers if they start here, while the
-        // others lose time if they start later (the other group waits).
-        constexpr bool LATE = INV && L == 256;
+        // 256- and 2048-point columns spills registers if they start here,
+        // while the others lose time if they start later (the other group waits).
+        constexpr bool LATE = INV && (L == 256 || L == 2048);
         auto fetch_next = [&] {
             const int tn = t + (int)gridDim.x;
             if (tn < ntiles) kcs_fetch<L>(p, tn, stage, &nslot[(i + 1) & 3], &bar[grp ^ 1], tid);
@@ -246,11 +258,10 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
         for (int q = 0; q < QO; ++q) {
             int j, g;
             bmap<LAYOUT_COL, L, G, RO>(tid + q * NT, j, g);
-            int l, jn;
-            long long c, rs;
-            kcs_node(p, col0 + g, l, jn, c);
-            // natural order, or the tile layout: column c - g of the tile block, element g
-            C* dst = kcs_dst<L, G>(p, l, jn, c - g, rs) + g;
+            const long long c = tc0 + g;
+            long long rs;
+            // natural order, or the tile layout: the tile block at column tc0, element g
+            C* dst = kcs_dst<L, G>(p, tl, tjn, tc0, rs) + g;
             if constexpr (INV) {
                 constexpr bool HOIST = (L / RO) % Gm::OLO == 0;
                 C wlo = mkc(1.f, 0.f);

@@ -72,7 +72,7 @@ template <int L> void row_pass() {
 
 template <int L> void column_pass() {
     typedef KCSGeom<L> SG;
-    typedef KCGeom<float, L> Gm;
+    typedef KCSTile<L> Gm;
     typedef Tiling<float> P;
     const size_t C = sizeof(float2);
     std::vector<Region> r = {{0, SG::STAGE_BYTES}, {SG::BAR_OFF, SG::BAR_OFF + 16},
@@ -120,7 +120,7 @@ template <int L> void column_pass() {
 // the same element coincide, and the scan maps that position back to
 // k = k1 + N1 k2 (a bijection over the node).
 template <int L> void tile_layout(int logN) {
-    typedef KCGeom<float, L> Gm;
+    typedef KCSTile<L> Gm;
     constexpr int G = Gm::G;
     int logG = 0, logL = 0;
     while ((1 << logG) < G) ++logG;
@@ -167,6 +167,8 @@ int main() {
     tile_layout<512>(20);
     tile_layout<1024>(20);
     tile_layout<1024>(24);
+    tile_layout<2048>(22);
+    tile_layout<2048>(24);
     row_pass<1024>();
     row_pass<2048>();
     row_pass<4096>();
@@ -174,6 +176,7 @@ int main() {
     column_pass<256>();
     column_pass<512>();
     column_pass<1024>();
+    column_pass<2048>();
     std::printf("checked %lld\n", g_checked);
     return 0;
 }
