@@ -164,17 +164,20 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         int j, g;
         bmap<LAYOUT_COL, L, G, XA::R0>(tid + q * NT, j, g);
         const long long c = (col0 + g) & N1m;
-        unsigned long long th[XA::R0];
-        if constexpr (FAST && INV) phase_run<XA::R0>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::R0), nc, th);
+        // FP32 phases streamed in the order of their finite differences:
+        // s = -R0/2 .. R0/2-1, element r = (s + R0) mod R0 (no phase array held)
+        const long long D = (long long)p.N1 * (L / XA::R0);
+        PhaseRun pr(c + (long long)j * p.N1 - (long long)(XA::R0 / 2) * D, D, nc);
 #pragma unroll
-        for (int r = 0; r < XA::R0; ++r) {
+        for (int u = 0; u < XA::R0; ++u) {
+            const int r = (u + XA::R0 / 2) % XA::R0;
             const long long idx = c + (long long)(j + r * (L / XA::R0)) * p.N1;
             C v = gn[idx];
             if constexpr (INV) {
                 const long long kk = signed_k(idx, p.N);
                 acc.add(ksq<T>(kk) * im_conj_mul(v, aux[idx]));
                 C ph;
-                if constexpr (FAST) ph = expi_turns_poly(th[r]);
+                if constexpr (FAST) ph = expi_turns_poly(pr.next());
                 else ph = expi_turns<T>(phase_q64(kk, nc));
                 v = cscale(cmul(v, ph), (T)ac.dzp);
             }
@@ -191,13 +194,14 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         int j, g;
         bmap<LAYOUT_COL, L, G, XA::RL>(tid + q * NT, j, g);
         const long long c = (col0 + g) & N1m;
-        unsigned long long th[XA::RL];
-        if constexpr (FAST && !INV) phase_run<XA::RL>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::RL), nc, th);
+        const long long D = (long long)p.N1 * (L / XA::RL);
+        PhaseRun pr(c + (long long)j * p.N1 - (long long)(XA::RL / 2) * D, D, nc);
         constexpr bool HOIST = (L / XA::RL) % Gm::OLO == 0;  // one low-table lookup per butterfly
         C wlo = mkc(T(1), T(0));
         if constexpr (INV && HOIST) wlo = olo[(j & (Gm::OLO - 1)) * G + g];
 #pragma unroll
-        for (int r = 0; r < XA::RL; ++r) {
+        for (int u = 0; u < XA::RL; ++u) {
+            const int r = (u + XA::RL / 2) % XA::RL;  // the phase order, as in the load
             const int row = j + r * (L / XA::RL);
             const long long idx = c + (long long)row * p.N1;
             C v = vout[q][r];
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
             } else {
                 const long long kk = signed_k(idx, p.N);
                 C ph;
-                if constexpr (FAST) ph = expi_turns_poly(th[r]);
+                if constexpr (FAST) ph = expi_turns_poly(pr.next());
                 else ph = expi_turns<T>(phase_q64(kk, nc));
                 v = cscale(cmul(v, cconj(ph)), post);
                 acc.add(-ksq<T>(kk) * im_conj_mul(v, aux[idx]));
