@@ -52,7 +52,8 @@ enum {
     MPA_ERR_NONFINITE = 6,     /* a NaN/Inf was produced (mpa_plan_status, mpa_batch_status) */
     MPA_ERR_DIVERGED = 7,      /* the Picard iteration did not contract (mpa_plan_status, mpa_batch_status) */
     MPA_ERR_SCALES = 8,        /* scales outside the weakly nonlinear regime (mpa_plan_check_scales) */
-    MPA_ERR_TIMEOUT = 9        /* a bounded wait of a persistent kernel ran out (mpa_plan_status, mpa_batch_status) */
+    MPA_ERR_TIMEOUT = 9,       /* a bounded wait of a persistent kernel ran out (mpa_plan_status, mpa_batch_status) */
+    MPA_ERR_BOUNDS = 10        /* debug build: an access outside the checked range was skipped (mpa_plan_status) */
 };
 
 enum { MPA_FP32 = 0, MPA_FP64 = 1 };
@@ -413,6 +414,22 @@ MPA_API const char* mpa_profile_kind_name(int kind);
  * MPA_ERR_INVALID_ARG if ms is NULL or no call was timed since
  * mpa_profile(1); MPA_ERR_CUDA if an event failed. */
 MPA_API int mpa_last_timing(double* ms, const char** entry);
+
+/* Debug build (tooling; the library compiled with MPA_DEBUG_BOUNDS=1, a
+ * separate libmpa_debug.so): every global access of the MPA passes, the
+ * scan and the on-chip node transform of plans and batches (not of the
+ * persistent batch kernel, the transforms, the split-step or the reverse
+ * mode) is checked against the plan's or batch's workspace; an access
+ * outside it is skipped (a load reads zero) and reported as MPA_ERR_BOUNDS
+ * by mpa_plan_status / mpa_batch_status, instead of touching memory.
+ * mpa_debug_bounds_checked returns 1 in such a build, 0 otherwise.
+ * mpa_debug_set_bounds narrows a plan's checked range to [workspace + lo,
+ * workspace + hi) (lo = hi = 0: the whole workspace), for tests that make
+ * the check fire without any access leaving the workspace; no effect in
+ * release builds.  MPA_ERR_INVALID_ARG for lo > hi or hi beyond the
+ * workspace, MPA_ERR_WORKSPACE without one. */
+MPA_API int32_t mpa_debug_bounds_checked(void);
+MPA_API int mpa_debug_set_bounds(mpa_plan* plan, size_t lo, size_t hi);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmpa.so")
 BUILD = os.path.join(HERE, "_build")
+# the bounds-checking debug build (MPA_DEBUG_BOUNDS=1), beside the release one
+OUT_DEBUG = os.path.join(HERE, "libmpa_debug.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC] + os.environ.get("MPA_NVCC_FLAGS", "").split()
@@ -37,17 +40,22 @@ def _stale(obj: str, deps) -> bool:
     return not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Compile every translation unit that changed and link the library;
+    debug=True builds libmpa_debug.so with the bounds checks of the MPA
+    passes (MPA_DEBUG_BOUNDS=1) in its own object directory."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    out, bdir = (OUT_DEBUG, BUILD_DEBUG) if debug else (OUT, BUILD)
+    flags = FLAGS + (["-DMPA_DEBUG_BOUNDS=1"] if debug else [])
+    os.makedirs(bdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "mpa.h"))
     objs, cmds = [], []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmds.append([nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj])
+            cmds.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])
     if cmds:
         with cf.ThreadPoolExecutor(max_workers=jobs or min(len(cmds), os.cpu_count() or 4)) as ex:
             futs = [ex.submit(subprocess.run, c, capture_output=True, text=True) for c in cmds]
@@ -57,12 +65,12 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode:
                     raise RuntimeError("nvcc failed: " + " ".join(c))
-    if force or cmds or not os.path.exists(OUT):
-        tmp = OUT + ".tmp"
+    if force or cmds or not os.path.exists(out):
+        tmp = out + ".tmp"
         subprocess.run([nvcc, *ARCH, "-shared", "-Xlinker", "--version-script=" + os.path.join(CSRC, "exports.map"),
                         "-o", tmp, *objs], check=True)
-        os.replace(tmp, OUT)
-    return OUT
+        os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

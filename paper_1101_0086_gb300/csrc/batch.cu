@@ -54,9 +54,11 @@ bool persistent_ok(const Group& g, int prec) {
     return prec == MPA_FP32 && g.sp.onchip && g.sp.N <= (1ll << 14);
 }
 
-Monitor group_monitor(unsigned char* ws, const Group& g, long long spin_limit) {
+Monitor group_monitor(unsigned char* ws, size_t ws_bytes, const Group& g, long long spin_limit) {
     Monitor m{};
     m.spin_limit = spin_limit;
+    m.dbg = DbgRange{reinterpret_cast<const char*>(ws), reinterpret_cast<const char*>(ws + ws_bytes),
+                     reinterpret_cast<unsigned int*>(ws + g.off_err)};
     m.err = reinterpret_cast<unsigned int*>(ws + g.off_err);
     m.conv = reinterpret_cast<ConvState*>(ws + g.off_conv);
     m.dprev = reinterpret_cast<float2*>(ws + g.off_dprev);
@@ -73,6 +75,7 @@ struct mpa_batch {
     std::vector<Link> links;
     std::vector<Group> groups;
     size_t ws_need = 0;
+    size_t ws_bytes = 0;
     unsigned char* ws = nullptr;
     cudaGraphExec_t graph = nullptr;
     long long graph_kernels = 0;  // kernel nodes per replay
@@ -143,7 +146,7 @@ int run_group(mpa_batch* b, Group& g, cudaStream_t st) {
     const NodeC* nodes = reinterpret_cast<const NodeC*>(b->ws + g.off_nodes);
     const int* loff = reinterpret_cast<const int*>(b->ws + g.off_loff);
     const double* gain = reinterpret_cast<const double*>(b->ws + g.off_gain);
-    const Monitor mon = group_monitor(b->ws, g, b->spin_limit);
+    const Monitor mon = group_monitor(b->ws, b->ws_bytes, g, b->spin_limit);
     // a fresh increment check per propagation (a run that ended early, e.g.
     // on a timeout, must not leave a half-counted level behind)
     MPA_TRY(cudaMemsetAsync(mon.conv, 0, (size_t)n * sizeof(ConvState), st));
@@ -370,6 +373,7 @@ int mpa_batch_set_workspace(mpa_batch* b, void* ws, size_t bytes) {
     if (bytes < b->ws_need || ((uintptr_t)ws & 255u) != 0) return MPA_ERR_WORKSPACE;
     release_graph(b);
     b->ws = reinterpret_cast<unsigned char*>(ws);
+    b->ws_bytes = bytes;
     for (auto& g : b->groups) {
         MPA_TRY(cudaMemcpy(b->ws + g.off_nodes, g.nodes.data(), g.nodes.size() * sizeof(NodeC), cudaMemcpyHostToDevice));
         MPA_TRY(cudaMemcpy(b->ws + g.off_loff, g.loff.data(), g.loff.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -397,6 +401,7 @@ int mpa_batch_status(mpa_batch* b, mpa_stream stream) {
         MPA_TRY(cudaMemsetAsync(b->ws + b->groups[i].off_err, 0, sizeof(unsigned int), st));
     }
     return (all & ERR_TIMEOUT) ? MPA_ERR_TIMEOUT
+         : (all & ERR_BOUNDS) ? MPA_ERR_BOUNDS
          : (all & ERR_NONFINITE) ? MPA_ERR_NONFINITE
          : (all & ERR_DIVERGED) ? MPA_ERR_DIVERGED
                                 : MPA_OK;
@@ -512,7 +517,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                                              reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
                                              reinterpret_cast<const int*>(b->ws + g.off_loff),
                                              reinterpret_cast<const double*>(b->ws + g.off_gain),
-                                             group_monitor(b->ws, g, b->spin_limit), 1, nullptr, st)
+                                             group_monitor(b->ws, b->ws_bytes, g, b->spin_limit), 1, nullptr, st)
                          : mpa_levels<double>(g.sp, b->M, b->n_iter, g.active[0],
                                               reinterpret_cast<double2*>(b->ws + g.off_psi), nullptr,
                                               reinterpret_cast<double2*>(b->ws + g.off_psi0c),
@@ -520,7 +525,7 @@ int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {
                                               reinterpret_cast<const NodeC*>(b->ws + g.off_nodes),
                                               reinterpret_cast<const int*>(b->ws + g.off_loff),
                                               reinterpret_cast<const double*>(b->ws + g.off_gain),
-                                              group_monitor(b->ws, g, b->spin_limit), 1, nullptr, st);
+                                              group_monitor(b->ws, b->ws_bytes, g, b->spin_limit), 1, nullptr, st);
                 if (rc == MPA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
                     rc = cuda_fail(cudaGetLastError());

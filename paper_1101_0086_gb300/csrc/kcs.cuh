@@ -111,13 +111,14 @@ __device__ __forceinline__ void kcs_fetch(const KCParams<float>& p, int t, float
 #pragma unroll
     for (int k = 0; k < NCH / NT; ++k) {
         const int id = tid + k * NT, row = id / CPR, ch = id % CPR;
-        cp_async16(dst + (size_t)row * G * sizeof(float2) + ch * 16,
-                   src + (long long)row * rs * (long long)sizeof(float2) + ch * 16);
+        const char* from = src + (long long)row * rs * (long long)sizeof(float2) + ch * 16;
+        if (MPA_DBG_OK(p.dbg, from, 16)) cp_async16(dst + (size_t)row * G * sizeof(float2) + ch * 16, from);
     }
-    if (tid < (int)(sizeof(NodeC) / 16))
-        cp_async16(reinterpret_cast<char*>(slot) + 16 * tid,
-                   reinterpret_cast<const char*>(p.nodes + p.loff[l] + jn) + 16 * tid);
-    cp_async_arrive(b);
+    if (tid < (int)(sizeof(NodeC) / 16) && MPA_DBG_OK(p.dbg, p.loff + l, sizeof(int))) {
+        const char* from = reinterpret_cast<const char*>(p.nodes + p.loff[l] + jn) + 16 * tid;
+        if (MPA_DBG_OK(p.dbg, from, 16)) cp_async16(reinterpret_cast<char*>(slot) + 16 * tid, from);
+    }
+    cp_async_arrive(b);  // arrives once this thread's issued copies have landed (none: at once)
 }
 
 // Group-wide: asks L2 for tile t's row segments (cp.async.bulk.prefetch), so
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
                     // four-step factor W_N^{-n2 k1}, n2 = row
                     C w = HOIST ? wlo : olo[(row & (Gm::OLO - 1)) * G + g];
                     if constexpr (Gm::OHI > 1) w = cmul(ohi[(row >> Gm::OSH) * G + g], w);
-                    dst[(long long)row * rs] = cmul(vout[q][r], w);
+                    if (MPA_DBG_OK(p.dbg, dst + (long long)row * rs, sizeof(C))) dst[(long long)row * rs] = cmul(vout[q][r], w);
                 }
             } else {
                 const NodeC nc = nslot[i & 3];  // copied with the tile
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(KCSGeom<L>::THREADS, 1)
                     const int r = (u + RO / 2) % RO;
                     const int row = j + r * (L / RO);
                     // V_j = sigma(z_j) dz F[|A_j|^2 A_j] exp(-i beta(w, z_j) - int G)   (Eq. (6))
-                    dst[(long long)row * rs] = cscale(cmul(vout[q][r], cconj(expi_turns_poly(pr.next()))), (float)nc.post);
+                    const C v = cscale(cmul(vout[q][r], cconj(expi_turns_poly(pr.next()))), (float)nc.post);
+                    if (MPA_DBG_OK(p.dbg, dst + (long long)row * rs, sizeof(C))) dst[(long long)row * rs] = v;
                 }
             }
         }

@@ -33,6 +33,35 @@ enum { KC_MPA_PRE = 0, KC_MPA_POST = 1, KC_SS_STEP = 2, KC_FWD = 3, KC_INV = 4 }
 // forward recompute keeps it for the adjoint of the Kerr term)
 enum { KR_MPA = 0, KR_SS = 1, KR_FWD = 2, KR_INV = 3, KR_MPA_KEEP = 4 };
 
+// Debug build (MPA_DEBUG_BOUNDS=1): the global accesses of the MPA passes,
+// the scan and the on-chip node transform are checked against the range of
+// the launch's buffers (a plan's or batch's workspace, [lo, hi)); an access
+// outside it sets ERR_BOUNDS in the error word and is skipped (a load reads
+// zero), so a bad index is reported instead of touching memory it should
+// not.  lo == nullptr (launches on caller buffers) checks nothing.  Release
+// builds compile every check to true.
+#ifndef MPA_DEBUG_BOUNDS
+#define MPA_DEBUG_BOUNDS 0
+#endif
+enum { ERR_BOUNDS = 8u };
+struct DbgRange {
+    const char* lo;
+    const char* hi;
+    unsigned int* err;
+};
+__device__ __forceinline__ bool dbg_in(const DbgRange& d, const void* a, size_t bytes) {
+    if (!d.lo) return true;
+    const char* c = static_cast<const char*>(a);
+    if (c >= d.lo && c + bytes <= d.hi) return true;
+    atomicOr(d.err, (unsigned)ERR_BOUNDS);
+    return false;
+}
+#if MPA_DEBUG_BOUNDS
+#define MPA_DBG_OK(d, ptr, bytes) ::mpa::dbg_in((d), (ptr), (bytes))
+#else
+#define MPA_DBG_OK(d, ptr, bytes) true
+#endif
+
 // A launch covers nl links x npl nodes each (node index within the launch
 // n = l npl + jn); a single link is nl = 1.
 template <typename T> struct KCParams {
@@ -59,6 +88,7 @@ template <typename T> struct KCParams {
     // block b = k1 / G of a node as G x N2 contiguous elements, element
     // (k2, k1 mod G) at b G N2 + k2 G + k1 mod G) instead of natural order
     int tiled_in, tiled_out;
+    DbgRange dbg;  // checked range of the debug build
 };
 
 template <typename T> struct KRParams {
@@ -72,6 +102,7 @@ template <typename T> struct KRParams {
     cx<T>* keep;  // KR_MPA_KEEP: receives A(t), rows laid out as data
     unsigned int* err;       // error word of the staged row pass (null: kr_kernel only)
     long long spin_limit;    // polls of each bounded wait of the staged row pass
+    DbgRange dbg;            // checked range of the debug build
 };
 
 // Column pass geometry for column length L: G columns per tile, NT threads.
@@ -199,15 +230,19 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         const long long c = col & N1m;
         const C* src = (p.src0 && jn == 0) ? p.src0 + l * p.src0_lstride + c
                                            : p.src + l * p.src_lstride + jn * p.src_stride + c;
-        NodeC nc;
-        if constexpr (MODE == KC_MPA_PRE) nc = p.nodes[p.loff[l] + jn];
+        NodeC nc{};
+        if constexpr (MODE == KC_MPA_PRE) {
+            if (MPA_DBG_OK(p.dbg, p.loff + l, sizeof(int)) && MPA_DBG_OK(p.dbg, p.nodes + p.loff[l] + jn, sizeof(NodeC)))
+                nc = p.nodes[p.loff[l] + jn];
+        }
         unsigned long long th[XA::R0];
         if constexpr (FAST && MODE == KC_MPA_PRE)
             phase_run<XA::R0>(c + (long long)j * p.N1, (long long)p.N1 * (L / XA::R0), nc, th);
 #pragma unroll
         for (int r = 0; r < XA::R0; ++r) {
             const int row = j + r * (L / XA::R0);
-            C v = ok ? src[(long long)row * p.N1] : mkc(T(0), T(0));
+            C v = ok && MPA_DBG_OK(p.dbg, src + (long long)row * p.N1, sizeof(C)) ? src[(long long)row * p.N1]
+                                                                                  : mkc(T(0), T(0));
             if constexpr (MODE == KC_MPA_PRE) {
                 // MPA step 2: A_hat_j = psi_j exp(i beta(w, z_j) + int G)
                 C ph;
@@ -286,8 +321,11 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
         const int l = node / p.npl, jn = node - l * p.npl;
         const long long c = col & N1m;
         C* dst = p.dst + l * p.dst_lstride + jn * p.dst_stride + c;
-        NodeC nc;
-        if constexpr (MODE == KC_MPA_POST) nc = p.nodes[p.loff[l] + jn];
+        NodeC nc{};
+        if constexpr (MODE == KC_MPA_POST) {
+            if (MPA_DBG_OK(p.dbg, p.loff + l, sizeof(int)) && MPA_DBG_OK(p.dbg, p.nodes + p.loff[l] + jn, sizeof(NodeC)))
+                nc = p.nodes[p.loff[l] + jn];
+        }
         unsigned long long th[RO];
         if constexpr (FAST && MODE == KC_MPA_POST)
             phase_run<RO>(c + (long long)j * p.N1, (long long)p.N1 * (L / RO), nc, th);
@@ -313,7 +351,7 @@ __global__ void __launch_bounds__(KCGeom<T, L>::NT, KCGeom<T, L>::NT <= 256 ? MP
                 else ph = expi_turns<T>(phase_q64(signed_k(c + (long long)row * p.N1, p.N), nc));
                 v = cscale(cmul(v, cconj(ph)), (T)nc.post);
             }
-            dst[(long long)row * p.N1] = v;
+            if (MPA_DBG_OK(p.dbg, dst + (long long)row * p.N1, sizeof(C))) dst[(long long)row * p.N1] = v;
         }
     }
 }
@@ -362,7 +400,9 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
         const bool ok = row0 + g < p.nrows;
         const C* src = p.data + (row0 + g) * L;
 #pragma unroll
-        for (int r = 0; r < XA::R0; ++r) vin[q][r] = ok ? src[j + r * (L / XA::R0)] : mkc(T(0), T(0));
+        for (int r = 0; r < XA::R0; ++r)
+            vin[q][r] = ok && MPA_DBG_OK(p.dbg, src + j + r * (L / XA::R0), sizeof(C)) ? src[j + r * (L / XA::R0)]
+                                                                                     : mkc(T(0), T(0));
     }
 
     if constexpr (sizeof(T) == 4 && MPA_L2PF_KR > 0) {
@@ -395,7 +435,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
             for (int r = 0; r < XI::RL; ++r) {
                 C a = cscale(vm[q][r], p.inv_n);  // A(t) (MPA step 3 / SS inverse)
                 if constexpr (MODE == KR_MPA_KEEP) {
-                    if (kp) kp[jk + r * (L / XI::RL)] = a;
+                    if (kp && MPA_DBG_OK(p.dbg, kp + jk + r * (L / XI::RL), sizeof(C))) kp[jk + r * (L / XI::RL)] = a;
                 }
                 const T pw = a.x * a.x + a.y * a.y;
                 if constexpr (MODE == KR_MPA || MODE == KR_MPA_KEEP) {
@@ -435,7 +475,7 @@ __global__ void __launch_bounds__(KRGeom<T, L>::NT, KRGeom<T, L>::NT <= 256 ? MP
             } else {
                 v = cscale(v, p.inv_n);
             }
-            dst[l] = v;
+            if (MPA_DBG_OK(p.dbg, dst + l, sizeof(C))) dst[l] = v;
         }
     }
 }
@@ -463,6 +503,7 @@ template <typename T> struct KNParams {
     const NodeC* nodes;  // link l, node jn at nodes[loff[l] + jn]
     const int* loff;
     T inv_n;
+    DbgRange dbg;  // checked range of the debug build
 };
 
 template <typename T, int L> struct KNGeom {
@@ -504,13 +545,15 @@ __device__ __forceinline__ void kn_tile(const KNParams<T>& p, long long row0, un
         const int node = ok ? (int)row : 0;
         const int l = node / p.npl, jn = node - l * p.npl;
         const C* src = (p.src0 && jn == 0) ? p.src0 + l * p.src0_lstride : p.src + l * p.src_lstride + jn * p.src_stride;
-        const NodeC nc = p.nodes[p.loff[l] + jn];
+        NodeC nc{};
+        if (MPA_DBG_OK(p.dbg, p.loff + l, sizeof(int)) && MPA_DBG_OK(p.dbg, p.nodes + p.loff[l] + jn, sizeof(NodeC)))
+            nc = p.nodes[p.loff[l] + jn];
         unsigned long long th[XI::R0];
         if constexpr (FAST) phase_run<XI::R0>(j, L / XI::R0, nc, th);
 #pragma unroll
         for (int r = 0; r < XI::R0; ++r) {
             const int k = j + r * (L / XI::R0);
-            C v = ok ? ldx<CG>(src + k) : mkc(T(0), T(0));
+            C v = ok && MPA_DBG_OK(p.dbg, src + k, sizeof(C)) ? ldx<CG>(src + k) : mkc(T(0), T(0));
             C ph;
             if constexpr (FAST) ph = expi_turns_poly(th[r]);
             else ph = expi_turns<T>(phase_q64(signed_k(k, L), nc));
@@ -542,7 +585,9 @@ __device__ __forceinline__ void kn_tile(const KNParams<T>& p, long long row0, un
         const int node = (int)row;
         const int l = node / p.npl, jn = node - l * p.npl;
         C* dst = p.dst + l * p.dst_lstride + jn * p.dst_stride;
-        const NodeC nc = p.nodes[p.loff[l] + jn];
+        NodeC nc{};
+        if (MPA_DBG_OK(p.dbg, p.loff + l, sizeof(int)) && MPA_DBG_OK(p.dbg, p.nodes + p.loff[l] + jn, sizeof(NodeC)))
+            nc = p.nodes[p.loff[l] + jn];
         unsigned long long th[XF::RL];
         if constexpr (FAST) phase_run<XF::RL>(j, L / XF::RL, nc, th);
 #pragma unroll
@@ -551,7 +596,7 @@ __device__ __forceinline__ void kn_tile(const KNParams<T>& p, long long row0, un
             C ph;
             if constexpr (FAST) ph = expi_turns_poly(th[r]);
             else ph = expi_turns<T>(phase_q64(signed_k(k, L), nc));
-            dst[k] = cscale(cmul(vout[q][r], cconj(ph)), (T)nc.post);
+            if (MPA_DBG_OK(p.dbg, dst + k, sizeof(C))) dst[k] = cscale(cmul(vout[q][r], cconj(ph)), (T)nc.post);
         }
     }
 }
@@ -831,6 +876,7 @@ struct Monitor {
     ConvState* conv;
     float2* dprev;
     long long spin_limit;  // polls of each bounded wait of a persistent kernel
+    DbgRange dbg;          // the debug build's checked range (the workspace)
 };
 
 // Natural index k = k1 + N1 k2 of position i of a node spectrum held in the
@@ -865,6 +911,7 @@ template <typename T> struct ScanParams {
     // staged column pass (G = 2^tile_logG columns of N2 = 2^tile_logL rows,
     // N1 = N / N2 columns); psi0c, state and out stay in natural order
     int tile_logG, tile_logL;
+    DbgRange dbg;  // checked range of the debug build
 };
 
 // Adds this block's sums to link l's accumulators; the last block of the
@@ -941,15 +988,16 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
     cx<T>* psi = p.psi + lo * (p.M + 1);
     // i: position in the node buffers; k: the frequency there (natural order)
     const long long k = p.tile_logG > 0 ? tile_to_natural(i, p.tile_logG, p.tile_logL, p.N) : i;
-    const C v0 = ldx<CG>(psi + i);
+    const C zero = mkc(T(0), T(0));
+    const C v0 = MPA_DBG_OK(p.dbg, psi + i, sizeof(C)) ? ldx<CG>(psi + i) : zero;
     T rx = T(0.5) * v0.x, ry = T(0.5) * v0.y, cxx = T(0), cyy = T(0);
-    const C p0 = ldx<CG>(p.psi0c + lo + k);
+    const C p0 = MPA_DBG_OK(p.dbg, p.psi0c + lo + k, sizeof(C)) ? ldx<CG>(p.psi0c + lo + k) : zero;
     C vl = v0;
     // node j: psi^{(n+1)}_j = psi_0 + i (R + V_j/2), then R += V_j (Kahan in FP32)
     auto node = [&](int j) {
         if (p.mode == 0) {
             const T sx = (rx - cxx) + T(0.5) * vl.x, sy = (ry - cyy) + T(0.5) * vl.y;
-            psi[(long long)j * p.N + i] = mkc(p0.x - sy, p0.y + sx);
+            if (MPA_DBG_OK(p.dbg, psi + (long long)j * p.N + i, sizeof(C))) psi[(long long)j * p.N + i] = mkc(p0.x - sy, p0.y + sx);
         }
         if constexpr (sizeof(T) == 4) {
             kahan_add(rx, cxx, vl.x);
@@ -964,7 +1012,8 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
         C* mine = ring + threadIdx.x;
 #pragma unroll
         for (int u = 0; u < S; ++u) {
-            if (1 + u <= p.M) cp_async8(mine + u * blockDim.x, psi + (long long)(1 + u) * p.N + i);
+            if (1 + u <= p.M && MPA_DBG_OK(p.dbg, psi + (long long)(1 + u) * p.N + i, sizeof(C)))
+                cp_async8(mine + u * blockDim.x, psi + (long long)(1 + u) * p.N + i);
             cp_async_commit();
         }
         for (int j = 1; j <= p.M; ++j) {
@@ -973,7 +1022,8 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
             vl = *slot;
             node(j);
             // the slot's value is consumed (node() used it): refill it with node j + S
-            if (j + S <= p.M) cp_async8(slot, psi + (long long)(j + S) * p.N + i);
+            if (j + S <= p.M && MPA_DBG_OK(p.dbg, psi + (long long)(j + S) * p.N + i, sizeof(C)))
+                cp_async8(slot, psi + (long long)(j + S) * p.N + i);
             cp_async_commit();
         }
         cp_async_wait_group<0>();
@@ -984,14 +1034,18 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
         C nxt[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            nxt[u] = (1 + u <= p.M) ? ldx<CG>(psi + (long long)(1 + u) * p.N + i) : mkc(T(0), T(0));
+            nxt[u] = (1 + u <= p.M && MPA_DBG_OK(p.dbg, psi + (long long)(1 + u) * p.N + i, sizeof(C)))
+                         ? ldx<CG>(psi + (long long)(1 + u) * p.N + i)
+                         : zero;
         for (int jb = 1; jb <= p.M; jb += U) {
             C cur[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 cur[u] = nxt[u];
                 const int jn = jb + U + u;
-                nxt[u] = (jn <= p.M) ? ldx<CG>(psi + (long long)jn * p.N + i) : mkc(T(0), T(0));
+                nxt[u] = (jn <= p.M && MPA_DBG_OK(p.dbg, psi + (long long)jn * p.N + i, sizeof(C)))
+                             ? ldx<CG>(psi + (long long)jn * p.N + i)
+                             : zero;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -1009,28 +1063,33 @@ __device__ __forceinline__ void scan_freq(const ScanParams<T>& p, int l, long lo
         // Picard increment at node M against the previous level's D
         double dx = sx, dy = sy;
         if (p.level > 0) {
-            const float2 d0 = ldx<CG>(p.dprev + lo + i);
+            const float2 d0 = MPA_DBG_OK(p.dbg, p.dprev + lo + i, sizeof(float2)) ? ldx<CG>(p.dprev + lo + i)
+                                                                                 : make_float2(0.f, 0.f);
             dx -= (double)d0.x;
             dy -= (double)d0.y;
         }
-        if (p.level < p.n_iter - 1) p.dprev[lo + i] = make_float2((float)sx, (float)sy);
+        if (p.level < p.n_iter - 1 && MPA_DBG_OK(p.dbg, p.dprev + lo + i, sizeof(float2)))
+            p.dprev[lo + i] = make_float2((float)sx, (float)sy);
         const double px = (double)p0.x - sy, py = (double)p0.y + sx;
         conv_close(p.conv + l, p.err, dx * dx + dy * dy, px * px + py * py, p.level, p.n_iter - 1, p.floor_rel, nblk);
     }
     if (p.mode == 0) return;
-    const double2 s0 = ldx<CG>(p.state + lo + k);
+    const double2 s0 = MPA_DBG_OK(p.dbg, p.state + lo + k, sizeof(double2)) ? ldx<CG>(p.state + lo + k)
+                                                                          : make_double2(0.0, 0.0);
     const double2 psiM = make_double2(s0.x - sy, s0.y + sx);
     if (p.mode == 2) {
-        p.out[lo + k] = psiM;
+        p.out[lo + k] = psiM;  // the caller's buffer (mpa_interval), outside the workspace
         return;
     }
     // step 7 and the lumped gain
-    const NodeC nodeM = p.nodes[p.loff[l] + p.M];
+    NodeC nodeM{};
+    if (MPA_DBG_OK(p.dbg, p.loff + l, sizeof(int)) && MPA_DBG_OK(p.dbg, p.nodes + p.loff[l] + p.M, sizeof(NodeC)))
+        nodeM = p.nodes[p.loff[l] + p.M];
     const double2 ph = expi_turns<double>(phase_q64(signed_k(k, p.N), nodeM));
-    const double g = nodeM.pre * p.gain[l];
+    const double g = nodeM.pre * (MPA_DBG_OK(p.dbg, p.gain + l, sizeof(double)) ? p.gain[l] : 0.0);
     const double2 a = make_double2(g * (psiM.x * ph.x - psiM.y * ph.y), g * (psiM.x * ph.y + psiM.y * ph.x));
-    p.state[lo + k] = a;
-    p.psi0c_out[lo + k] = mkc((T)a.x, (T)a.y);
+    if (MPA_DBG_OK(p.dbg, p.state + lo + k, sizeof(double2))) p.state[lo + k] = a;
+    if (MPA_DBG_OK(p.dbg, p.psi0c_out + lo + k, sizeof(C))) p.psi0c_out[lo + k] = mkc((T)a.x, (T)a.y);
     if (!(isfinite(a.x) && isfinite(a.y))) atomicOr(p.err, ERR_NONFINITE);
 }
 

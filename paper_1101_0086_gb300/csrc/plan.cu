@@ -59,6 +59,7 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* wor
             k.nodes = nodes;
             k.loff = loff;
             k.inv_n = (T)(1.0 / (double)N);
+            k.dbg = mon.dbg;
             MPA_TRY(kn_launch<T>(s.logN, k, st));
         } else {
         // steps 2-4 at every node (one launch per pass for all links)
@@ -81,6 +82,7 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* wor
         c.loff = loff;
         c.err = mon.err;
         c.spin_limit = mon.spin_limit;
+        c.dbg = mon.dbg;
         if constexpr (sizeof(T) == 4)
             tile_log_g = work && kc_staged(KC_MPA_POST, s.logN2, c) ? kcs_tile_log_cols(s.logN2) : 0;
         // Tile layout: the forward pass writes V_j into psi in the tile layout
@@ -94,6 +96,7 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* wor
         KRParams<T> r{xw, (long long)nl * npl * s.N2, N, s.logN, (int)s.N2, (T)(1.0 / (double)N), T(0)};
         r.err = mon.err;
         r.spin_limit = mon.spin_limit;
+        r.dbg = mon.dbg;
         MPA_TRY(kr_launch<T>(KR_MPA, s.logN1, r, st));
         c.src = xw;
         c.src_stride = N;
@@ -125,6 +128,7 @@ int mpa_levels(const Split& s, int M, int n_iter, int nl, cx<T>* psi, cx<T>* wor
         q.floor_rel = kDivergenceFloor;
         q.tile_logG = tile_log_g;
         q.tile_logL = s.logN2;
+        q.dbg = mon.dbg;
         MPA_TRY(scan_launch<T>(q, nl, st));
     }
     return MPA_OK;
@@ -147,6 +151,8 @@ Monitor monitor(const mpa_plan* p) {
     m.conv = reinterpret_cast<ConvState*>(p->ws + p->off_conv);
     m.dprev = reinterpret_cast<float2*>(p->ws + p->off_dprev);
     m.spin_limit = kSpinLimit;
+    const size_t hi = p->dbg_hi ? p->dbg_hi : p->ws_bytes;
+    m.dbg = DbgRange{reinterpret_cast<const char*>(p->ws + p->dbg_lo), reinterpret_cast<const char*>(p->ws + hi), m.err};
     return m;
 }
 
@@ -737,7 +743,8 @@ const char* mpa_status_string(int status) {
         case MPA_ERR_NONFINITE: return "non-finite value produced";
         case MPA_ERR_DIVERGED: return "Picard iteration diverged (the increment grew between iterations)";
         case MPA_ERR_SCALES: return "scales outside the weak-nonlinearity regime of the method";
-        case MPA_ERR_TIMEOUT: return "a wait of the persistent batch kernel ran out (results incomplete)";
+        case MPA_ERR_TIMEOUT: return "a bounded wait of a persistent kernel ran out (results incomplete)";
+        case MPA_ERR_BOUNDS: return "debug build: an access outside the checked buffer range was skipped";
     }
     return "unknown status";
 }
@@ -760,6 +767,17 @@ int mpa_profile_read(int kind, double* total_ms, int64_t* launches, double* byte
     cudaError_t e = prof_read(kind, total_ms, &n, bytes);
     *launches = n;
     if (e != cudaSuccess) return cuda_fail(e);
+    return MPA_OK;
+}
+
+int32_t mpa_debug_bounds_checked(void) { return MPA_DEBUG_BOUNDS ? 1 : 0; }
+
+int mpa_debug_set_bounds(mpa_plan* p, size_t lo, size_t hi) {
+    if (!p || lo > hi) return MPA_ERR_INVALID_ARG;
+    if (!p->ws) return MPA_ERR_WORKSPACE;
+    if (hi > p->ws_bytes) return MPA_ERR_INVALID_ARG;
+    p->dbg_lo = lo;
+    p->dbg_hi = hi;  // 0 (with lo 0): the whole workspace
     return MPA_OK;
 }
 

@@ -19,6 +19,7 @@ struct mpa_plan {
     size_t off_conv = 0, off_dprev = 0;  // Picard increment check (ConvState, D at node M)
     bool has_work = false;               // second set of node buffers (tile layout of the staged column passes)
     size_t off_work2 = 0;
+    size_t dbg_lo = 0, dbg_hi = 0;       // debug build: checked range within the workspace (hi 0: all of it)
     // wavefront schedule (FP32): S = n_iter slots of B node buffers
     bool wf = false;
     int B = 0;
@@ -33,11 +34,12 @@ namespace host {
 // The plan's run-time check words (error word, increment check).
 Monitor monitor(const mpa_plan* p);
 
-// MPA_ERR_TIMEOUT, MPA_ERR_NONFINITE or MPA_ERR_DIVERGED for the bits of an
-// error word (in that order of precedence: a timed-out wait leaves results
-// incomplete).
+// MPA_ERR_TIMEOUT, MPA_ERR_BOUNDS, MPA_ERR_NONFINITE or MPA_ERR_DIVERGED for
+// the bits of an error word (in that order of precedence: a timed-out wait
+// or a skipped access leaves results incomplete).
 inline int status_of_error_word(unsigned int h) {
     return (h & ERR_TIMEOUT) ? MPA_ERR_TIMEOUT
+         : (h & ERR_BOUNDS) ? MPA_ERR_BOUNDS
          : (h & ERR_NONFINITE) ? MPA_ERR_NONFINITE
          : (h & ERR_DIVERGED) ? MPA_ERR_DIVERGED : MPA_OK;
 }

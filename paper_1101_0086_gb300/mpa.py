@@ -14,7 +14,9 @@ from typing import Optional
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SO = os.path.join(_HERE, "libmpa.so")
+# MPA_LIB selects another build of the library (e.g. the bounds-checking
+# libmpa_debug.so of build(debug=True)); the default is the release build.
+_SO = os.environ.get("MPA_LIB") or os.path.join(_HERE, "libmpa.so")
 _lib: Optional[ctypes.CDLL] = None
 
 FP32, FP64 = 0, 1
@@ -60,7 +62,7 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split",
            "mpa_batch_autotune", "mpa_plan_contraction", "mpa_plan_check_scales", "mpa_batch_status",
            "mpa_debug_fail_launch", "mpa_alu_peak", "mpa_batch_set_persistent", "mpa_batch_set_wait_limit",
-           "mpa_last_timing")
+           "mpa_last_timing", "mpa_debug_bounds_checked", "mpa_debug_set_bounds")
 
 
 def library_path() -> str:
@@ -125,6 +127,8 @@ def lib() -> ctypes.CDLL:
         L.mpa_batch_status.argtypes = [vp, vp]
         L.mpa_debug_fail_launch.argtypes = [i64, i32]
         L.mpa_last_timing.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_char_p)]
+        L.mpa_debug_bounds_checked.restype = i32
+        L.mpa_debug_set_bounds.argtypes = [vp, ctypes.c_size_t, ctypes.c_size_t]
         L.mpa_alu_peak.argtypes = [i32, ctypes.POINTER(dbl), vp]
         L.mpa_batch_set_persistent.argtypes = [vp, i32]
         L.mpa_batch_set_wait_limit.argtypes = [vp, i64]
@@ -229,6 +233,11 @@ class Plan:
         self._split = int(l2.value)
         return int(l2.value)
 
+    def debug_set_bounds(self, lo: int = 0, hi: int = 0) -> None:
+        """``mpa_debug_set_bounds``: in a bounds-checking build, accept only
+        accesses within workspace bytes [lo, hi) (0, 0: all of it)."""
+        _check(lib().mpa_debug_set_bounds(self._h, int(lo), int(hi)), "mpa_debug_set_bounds")
+
     def set_split(self, log2_n2: int) -> None:
         """``mpa_plan_set_split``: use column length 2^log2_n2 (no timing)."""
         _check(lib().mpa_plan_set_split(self._h, int(log2_n2)), "mpa_plan_set_split")
@@ -301,7 +310,9 @@ class Plan:
         return True
 
     def status_code(self, stream=None) -> int:
-        """The raw status of ``mpa_plan_status`` (0, 6 non-finite, 7 diverged)."""
+        """The raw status of ``mpa_plan_status``: 0, 6 (non-finite), 7 (diverged),
+        9 (a bounded wait ran out) or 10 (debug build: an access outside the
+        checked range was skipped); clears the flags."""
         return int(lib().mpa_plan_status(self._h, _stream(stream)))
 
     def contraction(self, stream=None) -> float:
@@ -455,8 +466,9 @@ class Batch:
 
     def status_code(self, stream=None) -> int:
         """``mpa_batch_status``: 0, 6 (a link produced NaN/Inf), 7 (a link's
-        Picard iteration diverged) or 9 (a wait of the persistent kernel ran
-        out) since the last call; clears the flags."""
+        Picard iteration diverged), 9 (a bounded wait of a persistent kernel
+        ran out) or 10 (debug build: an access outside the workspace was
+        skipped) since the last call; clears the flags."""
         return int(lib().mpa_batch_status(self._h, _stream(stream)))
 
     def set_persistent(self, on: bool) -> None:
@@ -584,6 +596,12 @@ def profile_read() -> dict:
             out[name.decode()] = (float(ms.value), int(n.value), float(b.value))
         k += 1
     return out
+
+
+def debug_bounds_checked() -> bool:
+    """Whether the loaded library checks the MPA passes' accesses
+    (``mpa_debug_bounds_checked``: the debug build)."""
+    return bool(lib().mpa_debug_bounds_checked())
 
 
 def last_timing():

@@ -44,9 +44,23 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_status_strings(L):
-    for s in range(0, 10):
+    for s in range(0, 11):
         assert L.mpa_status_string(s) and L.mpa_status_string(s) != b"unknown status"
     assert L.mpa_status_string(99) == b"unknown status"
+
+
+def test_release_build_has_no_bounds_checks(L):
+    """mpa_debug_bounds_checked is 0 in the release library; the range setter
+    validates its arguments on the host (a plan without workspace, lo > hi)."""
+    assert L.mpa_debug_bounds_checked() == 0
+    fib = dm_map(1)
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 10, 2)
+    assert rc == 0
+    L.mpa_debug_set_bounds.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t]
+    assert L.mpa_debug_set_bounds(h, 0, 0) == 3  # no workspace yet
+    assert L.mpa_debug_set_bounds(None, 0, 0) == 1
+    assert L.mpa_debug_set_bounds(h, 8, 4) == 1  # lo > hi
+    L.mpa_plan_destroy(h)
 
 
 def test_last_timing_without_a_timed_call(L):
