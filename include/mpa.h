@@ -179,7 +179,7 @@ MPA_API int mpa_plan_set_split(mpa_plan* plan, int32_t log2_n2);
  *                      level schedule (the wavefront schedule reports only
  *                      MPA_ERR_NONFINITE);
  *   MPA_ERR_TIMEOUT    a bounded wait of the staged row pass (four-step
- *                      rows of 2^10 .. 2^13 points) ran out: the results
+ *                      rows of 2^9 .. 2^13 points) ran out: the results
  *                      are incomplete (not expected in normal operation).
  * MPA_ERR_NONFINITE takes precedence; else MPA_OK. */
 MPA_API int mpa_plan_status(mpa_plan* plan, mpa_stream stream);
@@ -303,7 +303,7 @@ MPA_API int mpa_batch_status(mpa_batch* batch, mpa_stream stream);
 MPA_API int mpa_batch_set_persistent(mpa_batch* batch, int32_t on);
 /* The wait limit (polls >= 0) of the batch's persistent kernels: the work
  * queue above, and the staged row pass of four-step node transforms with
- * rows of 2^10 .. 2^13 points, whose waits on its staging copies are bounded
+ * rows of 2^9 .. 2^13 points, whose waits on its staging copies are bounded
  * the same way (plans use 2^22 polls).  polls = 0 makes every such wait run
  * out at once (for tests of MPA_ERR_TIMEOUT).  Drops a captured graph. */
 MPA_API int mpa_batch_set_wait_limit(mpa_batch* batch, int64_t polls);

@@ -4,7 +4,7 @@
 
 namespace mpa {
 
-// The staged persistent row pass (krs.cuh) for rows of 2^10 .. 2^13 points
+// The staged persistent row pass (krs.cuh) for rows of 2^9 .. 2^13 points
 // in the MPA and split-step modes, whenever the caller passes an error word
 // for its bounded waits; MPA_KR_STAGED=0 keeps kr_kernel everywhere.
 #ifndef MPA_KR_STAGED
@@ -43,7 +43,7 @@ static cudaError_t krs_mode(int mode, const KRParams<float>& p, cudaStream_t st)
 }
 
 bool kr_staged(int mode, int logL, const KRParams<float>& p) {
-    return MPA_KR_STAGED && p.err && (mode == KR_MPA || mode == KR_SS) && logL >= 10 && logL <= 13;
+    return MPA_KR_STAGED && p.err && (mode == KR_MPA || mode == KR_SS) && logL >= 9 && logL <= 13;
 }
 
 template <int L, int MODE>
@@ -85,6 +85,7 @@ template <>
 cudaError_t kr_launch<float>(int mode, int logL, const KRParams<float>& p, cudaStream_t st) {
     if (kr_staged(mode, logL, p)) {
         switch (logL) {
+            case 9: return krs_mode<512>(mode, p, st);
             case 10: return krs_mode<1024>(mode, p, st);
             case 11: return krs_mode<2048>(mode, p, st);
             case 12: return krs_mode<4096>(mode, p, st);

@@ -82,12 +82,22 @@ template <int NT> __device__ __forceinline__ bool gsync_any(bool v) {
 
 constexpr long long KRS_DRAIN_POLLS = 1ll << 24;
 
-// Shared-memory layout of the staged row pass for row length L (tiles of
-// KRGeom<float, L>): the stage (TE elements), two mbarriers, the twiddle
-// tables shared by both groups, then per group its exchange buffer and
-// outer-factor tables.
+// Tile of the staged row pass: kr_kernel's G rows of L (8192 elements, 32
+// per thread), with the outer factor W_N^{n2 k1} split at k1 = 32 h + m
+// (kr_kernel splits at 128): tables of G (32 + L/32) entries per tile
+// instead of G (128 + L/128), built per tile, and one low-table lookup per
+// butterfly of the last radix-32 pass.
+template <int L> struct KRSTile {
+    typedef KRGeom<float, L> K;
+    static constexpr int G = K::G, TE = K::TE, NT = K::NT;
+    static constexpr int OSH = 5, OLO = L < 32 ? L : 32, OHI = L > 32 ? L / 32 : 1;
+};
+
+// Shared-memory layout of the staged row pass for row length L: the stage
+// (TE elements), two mbarriers, the twiddle tables shared by both groups,
+// then per group its exchange buffer and outer-factor tables.
 template <int L> struct KRSGeom {
-    typedef KRGeom<float, L> Gm;
+    typedef KRSTile<L> Gm;
     typedef Tiling<float, 1> P;
     static constexpr size_t al(size_t x) { return (x + 127) & ~(size_t)127; }
     static constexpr size_t STAGE_BYTES = (size_t)Gm::TE * sizeof(float2);
@@ -122,7 +132,7 @@ template <int L, int MODE>
 __global__ void __launch_bounds__(KRSGeom<L>::THREADS, 1) krs_kernel(const KRParams<float> p, long long spin_limit) {
     static_assert(MODE == KR_MPA || MODE == KR_SS, "inverse, pointwise step and forward");
     typedef float2 C;
-    typedef KRGeom<float, L> Gm;
+    typedef KRSTile<L> Gm;
     typedef KRSGeom<L> SG;
     typedef Tiling<float, 1> P;
     constexpr int G = Gm::G, NT = Gm::NT;
@@ -159,7 +169,7 @@ __global__ void __launch_bounds__(KRSGeom<L>::THREADS, 1) krs_kernel(const KRPar
         if (t >= ntiles) break;
         const long long row0 = (long long)t * G;
         gsync<1, NT>();  // the group's previous tile no longer needs s, olo, ohi
-        // W_N^{+n2 k1} for the tile's rows: olo[g][m] = W^{n2 m}, ohi[g][h] = W^{n2 128 h}
+        // W_N^{+n2 k1} for the tile's rows: olo[g][m] = W^{n2 m}, ohi[g][h] = W^{n2 32 h}
         for (int e = tid; e < G * (Gm::OLO + Gm::OHI); e += NT) {
             const int g = e / (Gm::OLO + Gm::OHI), m = e % (Gm::OLO + Gm::OHI);
             const long long n2 = (row0 + g) & (p.N2 - 1);

@@ -41,7 +41,7 @@ static void disjoint(const std::vector<Region>& r, size_t total, int L) {
 
 template <int L> void row_pass() {
     typedef KRSGeom<L> SG;
-    typedef KRGeom<float, L> Gm;
+    typedef KRSTile<L> Gm;
     typedef Tiling<float, 1> P;
     const size_t C = sizeof(float2);
     std::vector<Region> r = {{0, SG::STAGE_BYTES}, {SG::BAR_OFF, SG::BAR_OFF + 16},
@@ -169,6 +169,7 @@ int main() {
     tile_layout<1024>(24);
     tile_layout<2048>(22);
     tile_layout<2048>(24);
+    row_pass<512>();
     row_pass<1024>();
     row_pass<2048>();
     row_pass<4096>();
