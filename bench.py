@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--impl", default="mpa", choices=["mpa", "reference"])
     ap.add_argument("--workload", default="1",
                     help="1: the 2^20 link (default); 0, 2: the other single links; 3: 256 batched links; "
-                         "4: gradients of the 2^20 16-channel link")
+                         "4: gradients of the 2^20 16-channel link; or a single-link workload file "
+                         "(configs/<name>.json)")
     ap.add_argument("--km", type=float, default=None, help="propagate this many km per step (default: whole link)")
     ap.add_argument("--ss-km", type=float, default=25.0, help="km of split-step timed as the comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -20,6 +20,7 @@ this library is benchmarked on.
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
 from typing import List, Sequence, Tuple
 
@@ -33,6 +34,8 @@ __all__ = [
     "wdm_field",
     "dm_map",
     "workload",
+    "load_workload",
+    "save_workload",
     "WORKLOADS",
 ]
 
@@ -185,6 +188,46 @@ class Workload:
     def length_km(self) -> float:
         return self.fiber.length_km
 
+    def to_dict(self) -> dict:
+        """Plain-JSON form (the fiber map as its segment list)."""
+        d = dataclasses.asdict(self)
+        d["fiber"]["segments"] = [dataclasses.asdict(seg) for seg in self.fiber.segments]
+        return d
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Workload":
+        """Inverse of :meth:`to_dict`; a "note" key is allowed and ignored,
+        any other unknown or missing key is an error."""
+        d = {k: v for k, v in d.items() if k != "note"}
+        names = {f.name for f in dataclasses.fields(cls)}
+        if set(d) != names:
+            raise ValueError(f"workload keys: missing {sorted(names - set(d))}, unknown {sorted(set(d) - names)}")
+        fd = dict(d["fiber"])
+        segs = tuple(Segment(**seg) for seg in fd.pop("segments"))
+        fiber = FiberMap(segs, float(fd.pop("gamma_per_km")), float(fd.pop("z_a_km")), int(fd.pop("n_periods")))
+        if fd:
+            raise ValueError(f"unknown fiber keys {sorted(fd)}")
+        ints = {"N", "n_channels", "n_symbols", "seed", "mpa_M", "mpa_n_iter"}
+        kw = {k: (int(v) if k in ints else v if k in ("name", "modulation") else float(v))
+              for k, v in d.items() if k != "fiber"}
+        return cls(fiber=fiber, **kw)
+
+
+def load_workload(path: str) -> Workload:
+    """Workload from a JSON file written by :func:`save_workload` (or by hand
+    in the same form)."""
+    with open(path) as f:
+        return Workload.from_dict(json.load(f))
+
+
+def save_workload(w: Workload, path: str, note: str = "") -> None:
+    d = w.to_dict()
+    if note:
+        d = {"note": note, **d}
+    with open(path, "w") as f:
+        json.dump(d, f, indent=1)
+        f.write("\n")
+
 
 def _wl0() -> Workload:
     # 4 ch @ 50 GHz, 128 OOK bits at 10 Gb/s, 30 ps FWHM, 1 mW, N=2^14, 4 spans (200 km);
@@ -232,7 +275,10 @@ WORKLOADS = {"0": _wl0, "1": _wl1, "2": _wl2, "4": _wl4}
 
 
 def workload(key: str) -> Workload:
-    """Named workload by index ("0", "1", "2", "4") or by name."""
+    """Named workload by index ("0", "1", "2", "4"), by name, or from a JSON
+    file (a path ending in ".json", see :func:`load_workload`)."""
+    if key.endswith(".json"):
+        return load_workload(key)
     if key in WORKLOADS:
         return WORKLOADS[key]()
     for f in WORKLOADS.values():
