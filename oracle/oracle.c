@@ -139,6 +139,19 @@ static long n_amps(const fmap* m, double za, double zb) {
     return kb > ka ? kb - ka : 0;
 }
 
+/* 1 if an amplifier z_k = k z_a (k >= 1) lies strictly inside (za, zb):
+ * more than n_amps' tolerance away from both ends.  The MPA applies the
+ * lumped gain only at an interval end (step 7), so such an interval is
+ * rejected. */
+static int amp_inside(const fmap* m, double za, double zb) {
+    if (m->z_a <= 0.0) return 0;
+    double tol = 1e-9 * m->z_a;
+    long first = (long)floor((za + tol) / m->z_a) + 1; /* smallest k with k z_a > za + tol */
+    long last = (long)ceil((zb - tol) / m->z_a) - 1;   /* largest k with k z_a < zb - tol */
+    if (first < 1) first = 1;
+    return last >= first;
+}
+
 /* int_za^zb G without the lumped amplifiers: -gamma (zb - za) plus the
  * distributed gain of the segments (G of Eq. (1) between the z_k). */
 static double int_G(const fmap* m, double za, double zb) {
@@ -270,7 +283,7 @@ int oracle_mpa(const double* seg_rows, int n_seg, double gamma, double z_a, int 
     /* amplifiers may only sit at interval ends */
     for (long q = 0; q < n_int; q++) {
         double a = z_from + L * (double)q, b = z_from + L * (double)(q + 1);
-        if (n_amps(&m, a, b - 1e-6 * L) != 0) return 2;
+        if (amp_inside(&m, a, b)) return 2;
     }
     if (threads_used) {
         *threads_used = n_threads > 0 ? n_threads : ORACLE_MAX_THREADS();
@@ -558,7 +571,7 @@ static int mpa_grid(const fmap* m, double z_from, double z_to, double L, long* n
     if (fabs(cnt - (double)n) > 1e-9 * (cnt > 1.0 ? cnt : 1.0)) return 2;
     for (long q = 0; q < n; q++) {
         double a = z_from + L * (double)q, b = z_from + L * (double)(q + 1);
-        if (n_amps(m, a, b - 1e-6 * L) != 0) return 2;
+        if (amp_inside(m, a, b)) return 2;
     }
     *n_int = n;
     return 0;

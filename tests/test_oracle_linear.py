@@ -105,6 +105,24 @@ def test_inconsistent_grids_are_rejected():
         oracle.fft(np.ones(12), +1)  # N not a power of two
 
 
+def test_fine_intervals_ending_on_amplifiers_are_accepted():
+    """Intervals much shorter than the tolerance of the amplifier count
+    (L < 1e-3 z_a) that end exactly on amplifiers are valid grids: with
+    sigma = 0 the MPA reproduces the exact linear flow with both lumped
+    gains, while the same fine grid shifted by L/2 (an amplifier strictly
+    inside an interval) is still rejected."""
+    N, T = 64, 100.0
+    g = gamma_from_db_per_km(0.2)
+    fm = FiberMap((Segment(5.0, -1.0, 0.05, 0.0),), g, 50.0, 20)
+    A0 = chirped_gaussian(N, T, 5.0, 1.0)
+    L = 50.0 / 1024
+    out = oracle.mpa(A0, fm, T, 0.0, 100.0, L, 1, 1)
+    ref = closed_form_linear(A0, T, 100.0 * -1.0, 100.0 * 0.05, math.exp(-g * 100.0) * math.exp(2 * 50.0 * g))
+    assert oracle.rel_l2(out, ref) < 1e-12
+    with pytest.raises(ValueError):
+        oracle.mpa(A0, fm, T, 0.5 * L, 100.0 - 0.5 * L, L, 1, 1)
+
+
 def test_distributed_gain_linear_flow_and_energy():
     """A distributed gain g on a segment enters G = g - gamma (Eq. (1)): with
     sigma = 0 both methods give the closed-form flow times exp(int G), and
