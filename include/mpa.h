@@ -24,7 +24,10 @@
  *
  * Errors: every entry point returns an int status (MPA_OK = 0).  Argument
  * and grid checks are synchronous; a CUDA launch or copy failure returns
- * MPA_ERR_CUDA.  Nothing aborts or throws across the ABI.
+ * MPA_ERR_CUDA; a host allocation that fails (plan and batch tables, the
+ * per-interval schedules of a propagation or gradient) returns
+ * MPA_ERR_HOST_MEMORY and leaves no partly built object behind.  Nothing
+ * aborts or throws across the ABI.
  */
 #ifndef MPA_H
 #define MPA_H
@@ -53,7 +56,8 @@ enum {
     MPA_ERR_DIVERGED = 7,      /* the Picard iteration did not contract (mpa_plan_status, mpa_batch_status) */
     MPA_ERR_SCALES = 8,        /* scales outside the weakly nonlinear regime (mpa_plan_check_scales) */
     MPA_ERR_TIMEOUT = 9,       /* a bounded wait of a persistent kernel ran out (mpa_plan_status, mpa_batch_status) */
-    MPA_ERR_BOUNDS = 10        /* debug build: an access outside the checked range was skipped (mpa_plan_status) */
+    MPA_ERR_BOUNDS = 10,       /* debug build: an access outside the checked range was skipped (mpa_plan_status) */
+    MPA_ERR_HOST_MEMORY = 11   /* a host allocation failed (or a table too large for the host was asked for) */
 };
 
 enum { MPA_FP32 = 0, MPA_FP64 = 1 };
@@ -103,8 +107,9 @@ typedef struct {
 typedef struct {
     int64_t N;         /* Fourier modes, power of two */
     double T_ps;       /* time window */
-    double L_km;       /* interval length; must divide the DM period or be a multiple of it */
-    int32_t M;         /* intervals of the z-quadrature per interval (M+1 nodes) */
+    double L_km;       /* interval length; must divide the DM period (at most 2^20 intervals per period,
+                          else MPA_ERR_GRID) or be a multiple of it */
+    int32_t M;         /* intervals of the z-quadrature per interval (M+1 nodes), 1 <= M <= 2^24 */
     int32_t n_iter;    /* n_tot, Picard iterations per interval (>= 1) */
     int32_t precision; /* MPA_FP32 (FFT/nonlinearity in FP32, phase exact, Kahan sums, FP64 state) or MPA_FP64 */
     int32_t schedule;  /* MPA_SCHEDULE_* (0 = AUTO); WAVEFRONT where unsupported is MPA_ERR_INVALID_ARG */
@@ -265,6 +270,8 @@ typedef struct {
 
 typedef struct mpa_batch mpa_batch;
 
+/* L_km and M obey the limits of mpa_plan_params; each link has at most
+ * 2^31 - 1 intervals (MPA_ERR_GRID). */
 MPA_API int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_t M, int32_t n_iter,
                              int32_t precision, mpa_batch** out);
 MPA_API int mpa_batch_workspace_size(const mpa_batch* batch, size_t* bytes);

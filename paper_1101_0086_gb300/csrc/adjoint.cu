@@ -41,14 +41,15 @@ int adj_layout(const mpa_plan* p, double z_from, double z_to, AdjLayout* a) {
     const double L = p->L;
     double qf, ni;
     if (!(z_from >= -1e-12) || !(z_to > z_from) || z_to > p->map.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
-    if (!whole(z_from / L, &qf) || !whole((z_to - z_from) / L, &ni) || ni < 1) return MPA_ERR_GRID;
+    if (!whole(z_from / L, &qf) || !whole((z_to - z_from) / L, &ni) || ni < 1 || ni > kMaxIntervals)
+        return MPA_ERR_GRID;
     a->n_int = (long)ni;
     a->z_from = z_from;
     a->types.assign((size_t)a->n_int, 0);
     a->amps.assign((size_t)a->n_int, 0);
     for (long q = 0; q < a->n_int; ++q) {
         const double z0 = z_from + L * (double)q;
-        if (p->map.amps(z0, z0 + L - 1e-6 * L) != 0) return MPA_ERR_GRID;
+        if (p->map.amp_inside(z0, z0 + L)) return MPA_ERR_GRID;
         int t;
         if (interval_type(p, z0, &t) != MPA_OK) return MPA_ERR_GRID;
         a->types[(size_t)q] = t;
@@ -396,43 +397,49 @@ int mpa_plan_n_segments(const mpa_plan* p, int32_t* n) {
 }
 
 int mpa_adjoint_workspace_size(const mpa_plan* p, double z_from_km, double z_to_km, size_t* bytes) {
-    if (!p || !bytes) return MPA_ERR_INVALID_ARG;
-    AdjLayout a;
-    const int rc = adj_layout(p, z_from_km, z_to_km, &a);
-    if (rc) return rc;
-    *bytes = a.need;
-    return MPA_OK;
+    return abi_call([&]() -> int {
+        if (!p || !bytes) return MPA_ERR_INVALID_ARG;
+        AdjLayout a;
+        const int rc = adj_layout(p, z_from_km, z_to_km, &a);
+        if (rc) return rc;
+        *bytes = a.need;
+        return MPA_OK;
+    });
 }
 
 int mpa_propagate_checkpointed(mpa_plan* p, void* field, double z_from_km, double z_to_km, void* adj_ws,
                                size_t adj_bytes, mpa_stream stream) {
-    mpa::host::EntryRange nv("mpa_propagate_checkpointed", stream);
-    if (!p || !field) return MPA_ERR_INVALID_ARG;
-    if (!p->ws) return MPA_ERR_WORKSPACE;
-    AdjLayout a;
-    int rc = adj_layout(p, z_from_km, z_to_km, &a);
-    if (rc) return rc;
-    if ((rc = check_ws(a, adj_ws, adj_bytes))) return rc;
-    double2* ck = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(adj_ws) + a.off_ck);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    return p->prec == MPA_FP32 ? forward_ckpt<float>(p, field, a, ck, field, st)
-                               : forward_ckpt<double>(p, field, a, ck, field, st);
+    return abi_call([&]() -> int {
+        mpa::host::EntryRange nv("mpa_propagate_checkpointed", stream);
+        if (!p || !field) return MPA_ERR_INVALID_ARG;
+        if (!p->ws) return MPA_ERR_WORKSPACE;
+        AdjLayout a;
+        int rc = adj_layout(p, z_from_km, z_to_km, &a);
+        if (rc) return rc;
+        if ((rc = check_ws(a, adj_ws, adj_bytes))) return rc;
+        double2* ck = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(adj_ws) + a.off_ck);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        return p->prec == MPA_FP32 ? forward_ckpt<float>(p, field, a, ck, field, st)
+                                   : forward_ckpt<double>(p, field, a, ck, field, st);
+    });
 }
 
 int mpa_adjoint(mpa_plan* p, const void* field_in, const void* grad_out, void* grad_in, double z_from_km,
                 double z_to_km, void* adj_ws, size_t adj_bytes, double* grad_sigma, double* grad_beta2,
                 mpa_stream stream) {
-    mpa::host::EntryRange nv("mpa_adjoint", stream);
-    if (!p || !grad_out || !grad_in) return MPA_ERR_INVALID_ARG;
-    if (!p->ws) return MPA_ERR_WORKSPACE;
-    AdjLayout a;
-    int rc = adj_layout(p, z_from_km, z_to_km, &a);
-    if (rc) return rc;
-    if ((rc = check_ws(a, adj_ws, adj_bytes))) return rc;
-    unsigned char* ws = reinterpret_cast<unsigned char*>(adj_ws);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    return p->prec == MPA_FP32 ? adjoint_t<float>(p, field_in, grad_out, grad_in, a, ws, grad_sigma, grad_beta2, st)
-                               : adjoint_t<double>(p, field_in, grad_out, grad_in, a, ws, grad_sigma, grad_beta2, st);
+    return abi_call([&]() -> int {
+        mpa::host::EntryRange nv("mpa_adjoint", stream);
+        if (!p || !grad_out || !grad_in) return MPA_ERR_INVALID_ARG;
+        if (!p->ws) return MPA_ERR_WORKSPACE;
+        AdjLayout a;
+        int rc = adj_layout(p, z_from_km, z_to_km, &a);
+        if (rc) return rc;
+        if ((rc = check_ws(a, adj_ws, adj_bytes))) return rc;
+        unsigned char* ws = reinterpret_cast<unsigned char*>(adj_ws);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        if (p->prec == MPA_FP32) return adjoint_t<float>(p, field_in, grad_out, grad_in, a, ws, grad_sigma, grad_beta2, st);
+        return adjoint_t<double>(p, field_in, grad_out, grad_in, a, ws, grad_sigma, grad_beta2, st);
+    });
 }
 
 }  // extern "C"

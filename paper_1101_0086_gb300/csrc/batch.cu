@@ -9,6 +9,7 @@
 // independent: captured into one CUDA graph they become parallel branches,
 // so small-N groups fill the GPU together.
 #include <algorithm>
+#include <memory>
 #include <new>
 
 #include "host.h"
@@ -218,148 +219,153 @@ extern "C" {
 
 int mpa_batch_create(const mpa_link* links, int32_t n_links, double L_km, int32_t M, int32_t n_iter,
                      int32_t precision, mpa_batch** out) {
-    if (!links || n_links < 1 || !out || !(L_km > 0.0) || M < 1 || n_iter < 1) return MPA_ERR_INVALID_ARG;
-    if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
-    *out = nullptr;
-    mpa_batch* b = new (std::nothrow) mpa_batch();
-    if (!b) return MPA_ERR_INVALID_ARG;
-    b->L = L_km;
-    b->M = M;
-    b->n_iter = n_iter;
-    b->prec = precision;
-    b->csize = precision == MPA_FP32 ? sizeof(float2) : sizeof(double2);
-    b->links.resize((size_t)n_links);
-    auto fail = [&](int rc) {
-        delete b;
-        return rc;
-    };
-    const double dz = L_km / M;
-    for (int i = 0; i < n_links; ++i) {
-        const mpa_link& in = links[i];
-        Link& k = b->links[(size_t)i];
-        int rc = k.map.init(&in.map);
-        if (rc) return fail(rc);
-        if (!in.field || !(in.T_ps > 0.0)) return fail(MPA_ERR_INVALID_ARG);
-        Split sp;
-        rc = split_n(in.N, precision, &sp);
-        if (rc) return fail(rc);
-        k.N = in.N;
-        k.T = in.T_ps;
-        k.z_to = in.z_to_km;
-        k.field = in.field;
-        double r;
-        if (!(in.z_to_km > 0.0) || in.z_to_km > k.map.length * (1 + 1e-12) + 1e-9 || !whole(in.z_to_km / L_km, &r))
-            return fail(MPA_ERR_GRID);
-        k.n_int = (long)r;
-        if (whole(k.map.period / L_km, &r) && r >= 1) k.n_types = (int)r;
-        else if (whole(L_km / k.map.period, &r) && r >= 1) k.n_types = 1;
-        else return fail(MPA_ERR_GRID);
-        for (long q = 0; q < k.n_int; ++q) {
-            const double z0 = L_km * (double)q;
-            if (k.map.amps(z0, z0 + L_km - 1e-6 * L_km) != 0) return fail(MPA_ERR_GRID);
-        }
-    }
-    // groups by N, links longest first
-    std::vector<int> order((size_t)n_links);
-    for (int i = 0; i < n_links; ++i) order[(size_t)i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        const Link &x = b->links[(size_t)a], &y = b->links[(size_t)c];
-        return x.N != y.N ? x.N < y.N : x.n_int > y.n_int;
-    });
-    for (int i : order) {
-        const Link& k = b->links[(size_t)i];
-        if (b->groups.empty() || b->groups.back().sp.N != k.N) {
-            b->groups.emplace_back();
-            split_n(k.N, precision, &b->groups.back().sp);
-            // on-chip node transforms by default where an FP32 spectrum fits a CTA
-            b->groups.back().sp.onchip = precision == MPA_FP32 && onchip_ok(k.N, MPA_FP32) && k.N <= (1ll << 14);
-        }
-        b->groups.back().links.push_back(i);
-    }
-    size_t off = 0;
-    for (auto& g : b->groups) {
-        const int n = (int)g.links.size();
-        const size_t N = (size_t)g.sp.N;
-        // node tables of every link (each interval start within its period)
-        for (int i = 0; i < n; ++i) {
-            Link& k = b->links[(size_t)g.links[(size_t)i]];
-            k.node_base = g.nodes.size();
-            for (int t = 0; t < k.n_types; ++t) {
-                const double u0 = L_km * t;
-                for (int j = 0; j <= M; ++j) {
-                    const double zr = (j == M) ? L_km : dz * j;
-                    NodeC c{};
-                    phase_consts(k.map.integ(u0, u0 + zr, 1), k.map.integ(u0, u0 + zr, 2), k.T, &c);
-                    c.pre = std::exp(k.map.G(u0, u0 + zr));
-                    double sig;
-                    if (j == 0) sig = k.map.side(u0, 3, +1);
-                    else if (j == M) sig = k.map.side(u0 + zr, 3, -1);
-                    else sig = 0.5 * (k.map.side(u0 + zr, 3, -1) + k.map.side(u0 + zr, 3, +1));
-                    c.post = sig * dz / c.pre;
-                    g.nodes.push_back(c);
-                }
-            }
-            g.n_int = std::max(g.n_int, k.n_int);
-        }
-        g.loff.assign((size_t)g.n_int * n, 0);
-        g.gain.assign((size_t)g.n_int * n, 1.0);
-        g.active.assign((size_t)g.n_int, 0);
-        for (long q = 0; q < g.n_int; ++q) {
-            int act = 0;
-            for (int i = 0; i < n; ++i) {
-                const Link& k = b->links[(size_t)g.links[(size_t)i]];
-                if (k.n_int <= q) continue;
-                ++act;
+    return abi_call([&]() -> int {
+        if (!links || n_links < 1 || !out || !(L_km > 0.0) || M < 1 || M > kMaxNodes || n_iter < 1)
+            return MPA_ERR_INVALID_ARG;
+        if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+        *out = nullptr;
+        std::unique_ptr<mpa_batch> b(new mpa_batch());  // released to *out on success
+        b->L = L_km;
+        b->M = M;
+        b->n_iter = n_iter;
+        b->prec = precision;
+        b->csize = precision == MPA_FP32 ? sizeof(float2) : sizeof(double2);
+        b->links.resize((size_t)n_links);
+        auto fail = [](int rc) { return rc; };
+        const double dz = L_km / M;
+        for (int i = 0; i < n_links; ++i) {
+            const mpa_link& in = links[i];
+            Link& k = b->links[(size_t)i];
+            int rc = k.map.init(&in.map);
+            if (rc) return fail(rc);
+            if (!in.field || !(in.T_ps > 0.0)) return fail(MPA_ERR_INVALID_ARG);
+            Split sp;
+            rc = split_n(in.N, precision, &sp);
+            if (rc) return fail(rc);
+            k.N = in.N;
+            k.T = in.T_ps;
+            k.z_to = in.z_to_km;
+            k.field = in.field;
+            double r;
+            if (!(in.z_to_km > 0.0) || in.z_to_km > k.map.length * (1 + 1e-12) + 1e-9 ||
+                !whole(in.z_to_km / L_km, &r) || r > kMaxIntervals)
+                return fail(MPA_ERR_GRID);
+            k.n_int = (long)r;
+            if (whole(k.map.period / L_km, &r) && r >= 1 && r <= kMaxIntervalTypes) k.n_types = (int)r;
+            else if (whole(L_km / k.map.period, &r) && r >= 1) k.n_types = 1;
+            else return fail(MPA_ERR_GRID);
+            for (long q = 0; q < k.n_int; ++q) {
                 const double z0 = L_km * (double)q;
-                int t;
-                if (link_type(k, L_km, z0, &t)) return fail(MPA_ERR_GRID);
-                g.loff[(size_t)q * n + i] = (int)(k.node_base + (size_t)t * (M + 1));
-                g.gain[(size_t)q * n + i] = std::exp((double)k.map.amps(z0, z0 + L_km) * k.map.z_a * k.map.gamma);
+                if (k.map.amp_inside(z0, z0 + L_km)) return fail(MPA_ERR_GRID);
             }
-            g.active[(size_t)q] = act;
         }
-        g.off_psi = off;
-        off = align256(off + (size_t)n * (M + 1) * N * b->csize);
-        g.has_work = wants_work_buffers(N, precision);
-        g.off_work = off;
-        if (g.has_work) off = align256(off + (size_t)n * (M + 1) * N * b->csize);
-        g.off_state = off;
-        off = align256(off + (size_t)n * N * sizeof(double2));
-        g.off_psi0c = precision == MPA_FP32 ? off : g.off_state;
-        if (precision == MPA_FP32) off = align256(off + (size_t)n * N * sizeof(float2));
-        g.off_nodes = off;
-        off = align256(off + g.nodes.size() * sizeof(NodeC));
-        g.off_loff = off;
-        off = align256(off + g.loff.size() * sizeof(int));
-        g.off_gain = off;
-        off = align256(off + g.gain.size() * sizeof(double));
-        g.off_err = off;
-        off = align256(off + sizeof(unsigned int));
-        g.off_conv = off;
-        off = align256(off + (size_t)n * sizeof(ConvState));
-        g.off_dprev = off;
-        if (n_iter > 1) off = align256(off + (size_t)n * N * sizeof(float2));
-        g.link_nint.resize((size_t)n);
-        for (int i = 0; i < n; ++i) g.link_nint[(size_t)i] = (int)b->links[(size_t)g.links[(size_t)i]].n_int;
-        if (precision == MPA_FP32 && g.sp.N <= (1ll << 14) && g.sp.N >= (1ll << KN_LOG_MIN)) {
-            // queue of the persistent kernel: one phase of tasks per link, plus slack
-            const long long rows = KN_TILE_ROWS(g.sp.logN), thr = KN_THREADS(g.sp.logN);
-            const long long nb = (M + 1 + rows - 1) / rows, ns = (long long)N / thr;
-            g.q_cap = (unsigned)((long long)n * (nb > ns ? nb : ns) + 4096);
-            g.off_qtask = off;
-            off = align256(off + (size_t)g.q_cap * sizeof(unsigned long long));
-            g.off_qseq = off;
-            off = align256(off + (size_t)g.q_cap * sizeof(unsigned int));
-            g.off_ctr = off;
-            off = align256(off + (size_t)(3 + n) * sizeof(unsigned int));
-            g.off_nint = off;
-            off = align256(off + (size_t)n * sizeof(int));
-            g.persistent = g.sp.onchip;
+        // groups by N, links longest first
+        std::vector<int> order((size_t)n_links);
+        for (int i = 0; i < n_links; ++i) order[(size_t)i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            const Link &x = b->links[(size_t)a], &y = b->links[(size_t)c];
+            return x.N != y.N ? x.N < y.N : x.n_int > y.n_int;
+        });
+        for (int i : order) {
+            const Link& k = b->links[(size_t)i];
+            if (b->groups.empty() || b->groups.back().sp.N != k.N) {
+                b->groups.emplace_back();
+                split_n(k.N, precision, &b->groups.back().sp);
+                // on-chip node transforms by default where an FP32 spectrum fits a CTA
+                b->groups.back().sp.onchip = precision == MPA_FP32 && onchip_ok(k.N, MPA_FP32) && k.N <= (1ll << 14);
+            }
+            b->groups.back().links.push_back(i);
         }
-    }
-    b->ws_need = off;
-    *out = b;
-    return MPA_OK;
+        size_t off = 0;
+        for (auto& g : b->groups) {
+            const int n = (int)g.links.size();
+            const size_t N = (size_t)g.sp.N;
+            // node tables of every link (each interval start within its period),
+            // allocated at once: a table too large for the host fails here
+            size_t n_nodes = 0;
+            for (int i = 0; i < n; ++i)
+                n_nodes += (size_t)b->links[(size_t)g.links[(size_t)i]].n_types * ((size_t)M + 1);
+            g.nodes.reserve(n_nodes);
+            for (int i = 0; i < n; ++i) {
+                Link& k = b->links[(size_t)g.links[(size_t)i]];
+                k.node_base = g.nodes.size();
+                for (int t = 0; t < k.n_types; ++t) {
+                    const double u0 = L_km * t;
+                    for (int j = 0; j <= M; ++j) {
+                        const double zr = (j == M) ? L_km : dz * j;
+                        NodeC c{};
+                        phase_consts(k.map.integ(u0, u0 + zr, 1), k.map.integ(u0, u0 + zr, 2), k.T, &c);
+                        c.pre = std::exp(k.map.G(u0, u0 + zr));
+                        double sig;
+                        if (j == 0) sig = k.map.side(u0, 3, +1);
+                        else if (j == M) sig = k.map.side(u0 + zr, 3, -1);
+                        else sig = 0.5 * (k.map.side(u0 + zr, 3, -1) + k.map.side(u0 + zr, 3, +1));
+                        c.post = sig * dz / c.pre;
+                        g.nodes.push_back(c);
+                    }
+                }
+                g.n_int = std::max(g.n_int, k.n_int);
+            }
+            g.loff.assign((size_t)g.n_int * n, 0);
+            g.gain.assign((size_t)g.n_int * n, 1.0);
+            g.active.assign((size_t)g.n_int, 0);
+            for (long q = 0; q < g.n_int; ++q) {
+                int act = 0;
+                for (int i = 0; i < n; ++i) {
+                    const Link& k = b->links[(size_t)g.links[(size_t)i]];
+                    if (k.n_int <= q) continue;
+                    ++act;
+                    const double z0 = L_km * (double)q;
+                    int t;
+                    if (link_type(k, L_km, z0, &t)) return fail(MPA_ERR_GRID);
+                    g.loff[(size_t)q * n + i] = (int)(k.node_base + (size_t)t * (M + 1));
+                    g.gain[(size_t)q * n + i] = std::exp((double)k.map.amps(z0, z0 + L_km) * k.map.z_a * k.map.gamma);
+                }
+                g.active[(size_t)q] = act;
+            }
+            g.off_psi = off;
+            off = align256(off + (size_t)n * (M + 1) * N * b->csize);
+            g.has_work = wants_work_buffers(N, precision);
+            g.off_work = off;
+            if (g.has_work) off = align256(off + (size_t)n * (M + 1) * N * b->csize);
+            g.off_state = off;
+            off = align256(off + (size_t)n * N * sizeof(double2));
+            g.off_psi0c = precision == MPA_FP32 ? off : g.off_state;
+            if (precision == MPA_FP32) off = align256(off + (size_t)n * N * sizeof(float2));
+            g.off_nodes = off;
+            off = align256(off + g.nodes.size() * sizeof(NodeC));
+            g.off_loff = off;
+            off = align256(off + g.loff.size() * sizeof(int));
+            g.off_gain = off;
+            off = align256(off + g.gain.size() * sizeof(double));
+            g.off_err = off;
+            off = align256(off + sizeof(unsigned int));
+            g.off_conv = off;
+            off = align256(off + (size_t)n * sizeof(ConvState));
+            g.off_dprev = off;
+            if (n_iter > 1) off = align256(off + (size_t)n * N * sizeof(float2));
+            g.link_nint.resize((size_t)n);
+            for (int i = 0; i < n; ++i) g.link_nint[(size_t)i] = (int)b->links[(size_t)g.links[(size_t)i]].n_int;
+            if (precision == MPA_FP32 && g.sp.N <= (1ll << 14) && g.sp.N >= (1ll << KN_LOG_MIN)) {
+                // queue of the persistent kernel: one phase of tasks per link, plus slack
+                const long long rows = KN_TILE_ROWS(g.sp.logN), thr = KN_THREADS(g.sp.logN);
+                const long long nb = (M + 1 + rows - 1) / rows, ns = (long long)N / thr;
+                g.q_cap = (unsigned)((long long)n * (nb > ns ? nb : ns) + 4096);
+                g.off_qtask = off;
+                off = align256(off + (size_t)g.q_cap * sizeof(unsigned long long));
+                g.off_qseq = off;
+                off = align256(off + (size_t)g.q_cap * sizeof(unsigned int));
+                g.off_ctr = off;
+                off = align256(off + (size_t)(3 + n) * sizeof(unsigned int));
+                g.off_nint = off;
+                off = align256(off + (size_t)n * sizeof(int));
+                g.persistent = g.sp.onchip;
+            }
+        }
+        b->ws_need = off;
+        *out = b.release();
+        return MPA_OK;
+    });
 }
 
 int mpa_batch_workspace_size(const mpa_batch* b, size_t* bytes) {
@@ -375,7 +381,8 @@ int mpa_batch_set_workspace(mpa_batch* b, void* ws, size_t bytes) {
     b->ws = reinterpret_cast<unsigned char*>(ws);
     b->ws_bytes = bytes;
     for (auto& g : b->groups) {
-        MPA_TRY(cudaMemcpy(b->ws + g.off_nodes, g.nodes.data(), g.nodes.size() * sizeof(NodeC), cudaMemcpyHostToDevice));
+        MPA_TRY(cudaMemcpy(b->ws + g.off_nodes, g.nodes.data(), g.nodes.size() * sizeof(NodeC),
+                           cudaMemcpyHostToDevice));
         MPA_TRY(cudaMemcpy(b->ws + g.off_loff, g.loff.data(), g.loff.size() * sizeof(int), cudaMemcpyHostToDevice));
         MPA_TRY(cudaMemcpy(b->ws + g.off_gain, g.gain.data(), g.gain.size() * sizeof(double), cudaMemcpyHostToDevice));
         MPA_TRY(cudaMemset(b->ws + g.off_err, 0, sizeof(unsigned int)));
@@ -388,23 +395,26 @@ int mpa_batch_set_workspace(mpa_batch* b, void* ws, size_t bytes) {
 }
 
 int mpa_batch_status(mpa_batch* b, mpa_stream stream) {
-    if (!b) return MPA_ERR_INVALID_ARG;
-    if (!b->ws) return MPA_ERR_WORKSPACE;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    std::vector<unsigned int> h(b->groups.size(), 0u);
-    for (size_t i = 0; i < b->groups.size(); ++i)
-        MPA_TRY(cudaMemcpyAsync(&h[i], b->ws + b->groups[i].off_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-    MPA_TRY(cudaStreamSynchronize(st));
-    unsigned int all = 0u;
-    for (size_t i = 0; i < b->groups.size(); ++i) {
-        all |= h[i];
-        MPA_TRY(cudaMemsetAsync(b->ws + b->groups[i].off_err, 0, sizeof(unsigned int), st));
-    }
-    return (all & ERR_TIMEOUT) ? MPA_ERR_TIMEOUT
-         : (all & ERR_BOUNDS) ? MPA_ERR_BOUNDS
-         : (all & ERR_NONFINITE) ? MPA_ERR_NONFINITE
-         : (all & ERR_DIVERGED) ? MPA_ERR_DIVERGED
-                                : MPA_OK;
+    return abi_call([&]() -> int {
+        if (!b) return MPA_ERR_INVALID_ARG;
+        if (!b->ws) return MPA_ERR_WORKSPACE;
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        std::vector<unsigned int> h(b->groups.size(), 0u);
+        for (size_t i = 0; i < b->groups.size(); ++i)
+            MPA_TRY(cudaMemcpyAsync(&h[i], b->ws + b->groups[i].off_err, sizeof(unsigned int),
+                                    cudaMemcpyDeviceToHost, st));
+        MPA_TRY(cudaStreamSynchronize(st));
+        unsigned int all = 0u;
+        for (size_t i = 0; i < b->groups.size(); ++i) {
+            all |= h[i];
+            MPA_TRY(cudaMemsetAsync(b->ws + b->groups[i].off_err, 0, sizeof(unsigned int), st));
+        }
+        return (all & ERR_TIMEOUT) ? MPA_ERR_TIMEOUT
+             : (all & ERR_BOUNDS) ? MPA_ERR_BOUNDS
+             : (all & ERR_NONFINITE) ? MPA_ERR_NONFINITE
+             : (all & ERR_DIVERGED) ? MPA_ERR_DIVERGED
+                                    : MPA_OK;
+    });
 }
 
 int mpa_batch_set_persistent(mpa_batch* b, int32_t on) {
@@ -422,52 +432,54 @@ int mpa_batch_set_wait_limit(mpa_batch* b, int64_t polls) {
 }
 
 int mpa_batch_propagate(mpa_batch* b, int32_t use_graph, mpa_stream stream) {
-    EntryRange nv("mpa_batch_propagate", stream);
-    if (!b) return MPA_ERR_INVALID_ARG;
-    if (!b->ws) return MPA_ERR_WORKSPACE;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!use_graph) return run_all(b, st, false);
-    if (!b->graph) {
-        // first call: run once directly (sets kernel attributes), then
-        // capture the same launches, one parallel branch per N group
-        int rc = run_all(b, st, false);
-        if (rc) return rc;
-        MPA_TRY(cudaStreamSynchronize(st));
-        MPA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
-        b->branch.resize(b->groups.size());
-        for (auto& s : b->branch) MPA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-        b->ev.resize(b->groups.size() + 1);
-        for (auto& e : b->ev) MPA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        const bool prof = g_prof_on.exchange(false);
-        MPA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-        rc = run_all(b, b->cap, true);
-        cudaGraph_t graph = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
-        g_prof_on.store(prof);
-        if (rc) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
+    return abi_call([&]() -> int {
+        EntryRange nv("mpa_batch_propagate", stream);
+        if (!b) return MPA_ERR_INVALID_ARG;
+        if (!b->ws) return MPA_ERR_WORKSPACE;
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        if (!use_graph) return run_all(b, st, false);
+        if (!b->graph) {
+            // first call: run once directly (sets kernel attributes), then
+            // capture the same launches, one parallel branch per N group
+            int rc = run_all(b, st, false);
+            if (rc) return rc;
+            MPA_TRY(cudaStreamSynchronize(st));
+            MPA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+            b->branch.resize(b->groups.size());
+            for (auto& s : b->branch) MPA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            b->ev.resize(b->groups.size() + 1);
+            for (auto& e : b->ev) MPA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            const bool prof = g_prof_on.exchange(false);
+            MPA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            rc = run_all(b, b->cap, true);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+            g_prof_on.store(prof);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            MPA_TRY(e);
+            size_t nn = 0;
+            cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> gn(nn);
+            cudaGraphGetNodes(graph, gn.data(), &nn);
+            b->graph_kernels = 0;
+            for (auto& x : gn) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(x, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++b->graph_kernels;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&b->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            MPA_TRY(ei);
+            // the launches recorded while capturing did not run
+            g_launches.fetch_sub(b->graph_kernels, std::memory_order_relaxed);
+            return MPA_OK;  // this call already propagated once
         }
-        MPA_TRY(e);
-        size_t nn = 0;
-        cudaGraphGetNodes(graph, nullptr, &nn);
-        std::vector<cudaGraphNode_t> gn(nn);
-        cudaGraphGetNodes(graph, gn.data(), &nn);
-        b->graph_kernels = 0;
-        for (auto& x : gn) {
-            cudaGraphNodeType ty;
-            if (cudaGraphNodeGetType(x, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++b->graph_kernels;
-        }
-        const cudaError_t ei = cudaGraphInstantiate(&b->graph, graph, 0);
-        cudaGraphDestroy(graph);
-        MPA_TRY(ei);
-        // the launches recorded while capturing did not run
-        g_launches.fetch_sub(b->graph_kernels, std::memory_order_relaxed);
-        return MPA_OK;  // this call already propagated once
-    }
-    MPA_TRY(cudaGraphLaunch(b->graph, st));
-    g_launches.fetch_add(b->graph_kernels, std::memory_order_relaxed);
-    return MPA_OK;
+        MPA_TRY(cudaGraphLaunch(b->graph, st));
+        g_launches.fetch_add(b->graph_kernels, std::memory_order_relaxed);
+        return MPA_OK;
+    });
 }
 
 int mpa_batch_autotune(mpa_batch* b, mpa_stream stream) {

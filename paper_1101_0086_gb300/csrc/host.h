@@ -5,6 +5,8 @@
 
 #include <cmath>
 #include <cstdlib>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -42,7 +44,31 @@ int cuda_fail(cudaError_t e);
         if (_e != cudaSuccess) return ::mpa::host::cuda_fail(_e); \
     } while (0)
 
+// Body of a C entry point: no C++ exception may cross the C ABI, so a host
+// allocation that fails (or a container size beyond what the host can hold)
+// becomes MPA_ERR_HOST_MEMORY and any other exception MPA_ERR_INVALID_ARG.
+// Objects the body owns must be held by RAII (std::unique_ptr, containers)
+// so that nothing leaks on that path.
+template <class F> int abi_call(F&& body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return MPA_ERR_HOST_MEMORY;
+    } catch (const std::length_error&) {
+        return MPA_ERR_HOST_MEMORY;
+    } catch (...) {
+        return MPA_ERR_INVALID_ARG;
+    }
+}
+
 inline constexpr double kPi = 3.14159265358979323846264338327950288;
+// largest node count parameter M of a plan or batch (every size computed
+// from M + 1 stays far inside 64 bits and M + 1 inside 32)
+inline constexpr int kMaxNodes = 1 << 24;
+// most distinct interval starts within one period (period / L), and most
+// intervals of one link; larger counts are reported as MPA_ERR_GRID
+inline constexpr double kMaxIntervalTypes = (double)(1 << 20);
+inline constexpr double kMaxIntervals = 2147483647.0;
 // default polls of each bounded wait of a persistent kernel (a few seconds
 // at most; a wait normally ends within microseconds)
 inline constexpr long long kSpinLimit = 1ll << 22;
@@ -114,6 +140,17 @@ struct HostMap {
         long ka = (long)std::floor((za + tol) / z_a), kb = (long)std::floor((zb + tol) / z_a);
         if (ka < 0) ka = 0;
         return kb > ka ? kb - ka : 0;
+    }
+    // whether an amplifier z_k = k z_a (k >= 1) lies strictly inside
+    // (za, zb), i.e. more than the tolerance of amps() away from both ends
+    // (lumped gain is applied only at interval ends)
+    bool amp_inside(double za, double zb) const {
+        if (!(z_a > 0.0)) return false;
+        const double tol = 1e-9 * z_a;
+        long ka = (long)std::floor((za + tol) / z_a);        // k z_a > za + tol  <=>  k > ka
+        const long kb = (long)std::ceil((zb - tol) / z_a) - 1;  // k z_a < zb - tol  <=>  k <= kb
+        if (ka < 0) ka = 0;
+        return kb > ka;
     }
 };
 

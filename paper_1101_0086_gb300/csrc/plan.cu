@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -284,13 +285,13 @@ int propagate_t(mpa_plan* p, void* field, double z_from, double z_to, cudaStream
     const double L = p->L;
     double qf, ni;
     if (!(z_from >= -1e-12) || !(z_to >= z_from) || z_to > p->map.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
-    if (!whole(z_from / L, &qf) || !whole((z_to - z_from) / L, &ni)) return MPA_ERR_GRID;
+    if (!whole(z_from / L, &qf) || !whole((z_to - z_from) / L, &ni) || ni > kMaxIntervals) return MPA_ERR_GRID;
     const long n_int = (long)ni;
     std::vector<int> types((size_t)n_int);
     std::vector<long> amps((size_t)n_int);
     for (long q = 0; q < n_int; ++q) {
         const double z0 = z_from + L * (double)q;
-        if (p->map.amps(z0, z0 + L - 1e-6 * L) != 0) return MPA_ERR_GRID;
+        if (p->map.amp_inside(z0, z0 + L)) return MPA_ERR_GRID;
         int t;
         if (interval_type(p, z0, &t) != MPA_OK) return MPA_ERR_GRID;
         types[(size_t)q] = t;
@@ -320,7 +321,7 @@ template <typename T>
 int interval_t(mpa_plan* p, const void* psi0, void* psiM, double z0, cudaStream_t st) {
     double q;
     if (!whole(z0 / p->L, &q) || z0 < -1e-12 || z0 + p->L > p->map.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
-    if (p->map.amps(z0, z0 + p->L - 1e-6 * p->L) != 0) return MPA_ERR_GRID;
+    if (p->map.amp_inside(z0, z0 + p->L)) return MPA_ERR_GRID;
     int t;
     if (interval_type(p, z0, &t) != MPA_OK) return MPA_ERR_GRID;
     double2* state = reinterpret_cast<double2*>(p->ws + p->off_state);
@@ -336,7 +337,7 @@ int ss_t(const HostMap& m, const Split& s, double T_ps, double dz, void* field, 
          void* ws, cudaStream_t st) {
     double kk;
     if (!(z_from >= -1e-12) || !(z_to > z_from) || z_to > m.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
-    if (!whole((z_to - z_from) / dz, &kk) || kk < 1) return MPA_ERR_GRID;
+    if (!whole((z_to - z_from) / dz, &kk) || kk < 1 || kk > kMaxIntervals) return MPA_ERR_GRID;
     const long K = (long)kk;
     cx<T>* f = reinterpret_cast<cx<T>*>(field);
     cx<T>* w = reinterpret_cast<cx<T>*>(ws);
@@ -384,106 +385,105 @@ int ss_t(const HostMap& m, const Split& s, double T_ps, double dz, void* field, 
 extern "C" {
 
 int mpa_plan_create(const mpa_fiber_map* map, const mpa_plan_params* prm, mpa_plan** out) {
-    if (!map || !prm || !out) return MPA_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (prm->precision != MPA_FP32 && prm->precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
-    if (!(prm->T_ps > 0.0) || !(prm->L_km > 0.0) || prm->M < 1 || prm->n_iter < 1) return MPA_ERR_INVALID_ARG;
-    if (prm->schedule < MPA_SCHEDULE_AUTO || prm->schedule > MPA_SCHEDULE_WAVEFRONT) return MPA_ERR_INVALID_ARG;
-    mpa_plan* p = new (std::nothrow) mpa_plan();
-    if (!p) return MPA_ERR_INVALID_ARG;
-    int rc = p->map.init(map);
-    if (rc == MPA_OK) rc = split_n(prm->N, prm->precision, &p->sp);
-    if (rc != MPA_OK) {
-        delete p;
-        return rc;
-    }
-    // FP32 plans whose spectra fit one CTA use the on-chip node transform by
-    // default (1.75x the three passes on the 2^14-mode link); the cluster
-    // form (2^15, 2^16) and FP64 plans are chosen by set_split(0) or tuning
-    p->sp.onchip = prm->precision == MPA_FP32 && prm->schedule != MPA_SCHEDULE_WAVEFRONT && onchip_ok(prm->N, MPA_FP32) &&
-                   prm->N <= (1ll << 14);
-    p->T = prm->T_ps;
-    p->L = prm->L_km;
-    p->M = prm->M;
-    p->n_iter = prm->n_iter;
-    p->prec = prm->precision;
-    double r;
-    if (whole(p->map.period / p->L, &r) && r >= 1) p->n_types = (int)r;
-    else if (whole(p->L / p->map.period, &r) && r >= 1) p->n_types = 1;
-    else {
-        delete p;
-        return MPA_ERR_GRID;
-    }
-    // per-node constants of Eq. (6) for each interval start u0 = t L in the period
-    const int M = p->M;
-    const double dz = p->L / M;
-    p->nodes.resize((size_t)p->n_types * (M + 1));
-    for (int t = 0; t < p->n_types; ++t) {
-        const double u0 = p->L * t;
-        for (int j = 0; j <= M; ++j) {
-            const double zr = (j == M) ? p->L : dz * j;
-            NodeC& c = p->nodes[(size_t)t * (M + 1) + j];
-            phase_consts(p->map.integ(u0, u0 + zr, 1), p->map.integ(u0, u0 + zr, 2), p->T, &c);
-            c.pre = std::exp(p->map.G(u0, u0 + zr));
-            double sig;
-            if (j == 0) sig = p->map.side(u0, 3, +1);
-            else if (j == M) sig = p->map.side(u0 + zr, 3, -1);
-            else sig = 0.5 * (p->map.side(u0 + zr, 3, -1) + p->map.side(u0 + zr, 3, +1));
-            c.post = sig * dz / c.pre;
+    return abi_call([&]() -> int {
+        if (!map || !prm || !out) return MPA_ERR_INVALID_ARG;
+        *out = nullptr;
+        if (prm->precision != MPA_FP32 && prm->precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+        if (!(prm->T_ps > 0.0) || !(prm->L_km > 0.0) || prm->M < 1 || prm->M > kMaxNodes || prm->n_iter < 1)
+            return MPA_ERR_INVALID_ARG;
+        if (prm->schedule < MPA_SCHEDULE_AUTO || prm->schedule > MPA_SCHEDULE_WAVEFRONT) return MPA_ERR_INVALID_ARG;
+        std::unique_ptr<mpa_plan> p(new mpa_plan());  // released to *out on success
+        int rc = p->map.init(map);
+        if (rc == MPA_OK) rc = split_n(prm->N, prm->precision, &p->sp);
+        if (rc != MPA_OK) return rc;
+        // FP32 plans whose spectra fit one CTA use the on-chip node transform by
+        // default (1.75x the three passes on the 2^14-mode link); the cluster
+        // form (2^15, 2^16) and FP64 plans are chosen by set_split(0) or tuning
+        p->sp.onchip = prm->precision == MPA_FP32 && prm->schedule != MPA_SCHEDULE_WAVEFRONT &&
+                       onchip_ok(prm->N, MPA_FP32) && prm->N <= (1ll << 14);
+        p->T = prm->T_ps;
+        p->L = prm->L_km;
+        p->M = prm->M;
+        p->n_iter = prm->n_iter;
+        p->prec = prm->precision;
+        double r;
+        if (whole(p->map.period / p->L, &r) && r >= 1) {
+            if (r > kMaxIntervalTypes) return MPA_ERR_GRID;
+            p->n_types = (int)r;
+        } else if (whole(p->L / p->map.period, &r) && r >= 1) {
+            p->n_types = 1;
+        } else {
+            return MPA_ERR_GRID;
         }
-    }
-    p->csize = p->prec == MPA_FP32 ? sizeof(float2) : sizeof(double2);
-    const size_t N = (size_t)p->sp.N;
-    // schedule: the wavefront needs FP32 and whole column tiles per node
-    // (column length >= 128 keeps its shared memory within the 227 KB limit)
-    p->wf = prm->schedule == MPA_SCHEDULE_WAVEFRONT && p->prec == MPA_FP32 && p->n_iter <= 8 && p->sp.logN2 >= 7 &&
-            p->sp.N1 >= kcw_tile_cols(p->sp.logN2) && p->sp.N1 % kcw_tile_cols(p->sp.logN2) == 0;
-    if (prm->schedule == MPA_SCHEDULE_WAVEFRONT && !p->wf) {
-        delete p;
-        return MPA_ERR_INVALID_ARG;
-    }
-    if (p->wf) {
-        // B nodes per block: about 256 MiB of node buffers over the n_iter slots
-        const size_t per = (size_t)p->n_iter * N * sizeof(float2);
-        long b = (long)((256ull << 20) / per);
-        b = b < 1 ? 1 : b > 16 ? 16 : b;
-        p->B = (int)(b < M ? b : M);
-        const size_t S = (size_t)p->n_iter;
-        p->off_work = 0;
-        p->off_y0 = align256(p->off_work + S * (size_t)p->B * N * sizeof(float2));
-        p->off_R = align256(p->off_y0 + N * sizeof(float2));
-        p->off_C = align256(p->off_R + S * N * sizeof(float2));
-        p->off_D = align256(p->off_C + S * N * sizeof(float2));
-        p->off_state = align256(p->off_D + N * sizeof(double2));
+        // per-node constants of Eq. (6) for each interval start u0 = t L in the period
+        const int M = p->M;
+        const double dz = p->L / M;
+        p->nodes.resize((size_t)p->n_types * (M + 1));
+        for (int t = 0; t < p->n_types; ++t) {
+            const double u0 = p->L * t;
+            for (int j = 0; j <= M; ++j) {
+                const double zr = (j == M) ? p->L : dz * j;
+                NodeC& c = p->nodes[(size_t)t * (M + 1) + j];
+                phase_consts(p->map.integ(u0, u0 + zr, 1), p->map.integ(u0, u0 + zr, 2), p->T, &c);
+                c.pre = std::exp(p->map.G(u0, u0 + zr));
+                double sig;
+                if (j == 0) sig = p->map.side(u0, 3, +1);
+                else if (j == M) sig = p->map.side(u0 + zr, 3, -1);
+                else sig = 0.5 * (p->map.side(u0 + zr, 3, -1) + p->map.side(u0 + zr, 3, +1));
+                c.post = sig * dz / c.pre;
+            }
+        }
+        p->csize = p->prec == MPA_FP32 ? sizeof(float2) : sizeof(double2);
+        const size_t N = (size_t)p->sp.N;
+        // schedule: the wavefront needs FP32 and whole column tiles per node
+        // (column length >= 128 keeps its shared memory within the 227 KB limit)
+        p->wf = prm->schedule == MPA_SCHEDULE_WAVEFRONT && p->prec == MPA_FP32 && p->n_iter <= 8 && p->sp.logN2 >= 7 &&
+                p->sp.N1 >= kcw_tile_cols(p->sp.logN2) && p->sp.N1 % kcw_tile_cols(p->sp.logN2) == 0;
+        if (prm->schedule == MPA_SCHEDULE_WAVEFRONT && !p->wf) return MPA_ERR_INVALID_ARG;
+        if (p->wf) {
+            // B nodes per block: about 256 MiB of node buffers over the n_iter slots
+            const size_t per = (size_t)p->n_iter * N * sizeof(float2);
+            long b = (long)((256ull << 20) / per);
+            b = b < 1 ? 1 : b > 16 ? 16 : b;
+            p->B = (int)(b < M ? b : M);
+            const size_t S = (size_t)p->n_iter;
+            p->off_work = 0;
+            p->off_y0 = align256(p->off_work + S * (size_t)p->B * N * sizeof(float2));
+            p->off_R = align256(p->off_y0 + N * sizeof(float2));
+            p->off_C = align256(p->off_R + S * N * sizeof(float2));
+            p->off_D = align256(p->off_C + S * N * sizeof(float2));
+            p->off_state = align256(p->off_D + N * sizeof(double2));
+            p->off_psi0c = align256(p->off_state + N * sizeof(double2));
+            p->off_psi = p->off_work;  // scratch of the entry/exit transforms
+            p->off_nodes = align256(p->off_psi0c + N * sizeof(float2));
+            p->off_toff = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
+            p->off_gains = align256(p->off_toff + (size_t)p->n_types * sizeof(int));
+            p->off_err = align256(p->off_gains + kMaxAmpsPerInterval * sizeof(double));
+            p->off_conv = align256(p->off_err + sizeof(unsigned int));
+            p->off_dprev = align256(p->off_conv + sizeof(ConvState));
+            p->ws_need = align256(p->off_dprev);  // the wavefront schedule has no increment check
+            *out = p.release();
+            return MPA_OK;
+        }
+        p->off_psi = 0;
+        p->has_work = wants_work_buffers(p->sp.N, p->prec);
+        p->off_work2 = align256(p->off_psi + (size_t)(M + 1) * N * p->csize);
+        p->off_state = p->has_work ? align256(p->off_work2 + (size_t)(M + 1) * N * p->csize) : p->off_work2;
         p->off_psi0c = align256(p->off_state + N * sizeof(double2));
-        p->off_psi = p->off_work;  // scratch of the entry/exit transforms
-        p->off_nodes = align256(p->off_psi0c + N * sizeof(float2));
+        const size_t psi0c_bytes = p->prec == MPA_FP32 ? N * sizeof(float2) : 0;
+        if (p->prec == MPA_FP64) p->off_psi0c = p->off_state;  // the FP64 state is its own working copy
+        const size_t after_psi0c =
+            p->prec == MPA_FP32 ? p->off_psi0c + psi0c_bytes : p->off_state + N * sizeof(double2);
+        p->off_nodes = align256(after_psi0c);
         p->off_toff = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
         p->off_gains = align256(p->off_toff + (size_t)p->n_types * sizeof(int));
         p->off_err = align256(p->off_gains + kMaxAmpsPerInterval * sizeof(double));
         p->off_conv = align256(p->off_err + sizeof(unsigned int));
         p->off_dprev = align256(p->off_conv + sizeof(ConvState));
-        p->ws_need = align256(p->off_dprev);  // the wavefront schedule has no increment check
-        *out = p;
+        p->ws_need = align256(p->off_dprev + (p->n_iter > 1 ? N * sizeof(float2) : 0));
+        *out = p.release();
         return MPA_OK;
-    }
-    p->off_psi = 0;
-    p->has_work = wants_work_buffers(p->sp.N, p->prec);
-    p->off_work2 = align256(p->off_psi + (size_t)(M + 1) * N * p->csize);
-    p->off_state = p->has_work ? align256(p->off_work2 + (size_t)(M + 1) * N * p->csize) : p->off_work2;
-    p->off_psi0c = align256(p->off_state + N * sizeof(double2));
-    const size_t psi0c_bytes = p->prec == MPA_FP32 ? N * sizeof(float2) : 0;
-    if (p->prec == MPA_FP64) p->off_psi0c = p->off_state;  // the FP64 state is its own working copy
-    const size_t after_psi0c = p->prec == MPA_FP32 ? p->off_psi0c + psi0c_bytes : p->off_state + N * sizeof(double2);
-    p->off_nodes = align256(after_psi0c);
-    p->off_toff = align256(p->off_nodes + p->nodes.size() * sizeof(NodeC));
-    p->off_gains = align256(p->off_toff + (size_t)p->n_types * sizeof(int));
-    p->off_err = align256(p->off_gains + kMaxAmpsPerInterval * sizeof(double));
-    p->off_conv = align256(p->off_err + sizeof(unsigned int));
-    p->off_dprev = align256(p->off_conv + sizeof(ConvState));
-    p->ws_need = align256(p->off_dprev + (p->n_iter > 1 ? N * sizeof(float2) : 0));
-    *out = p;
-    return MPA_OK;
+    });
 }
 
 int mpa_plan_workspace_size(const mpa_plan* p, size_t* bytes) {
@@ -493,21 +493,23 @@ int mpa_plan_workspace_size(const mpa_plan* p, size_t* bytes) {
 }
 
 int mpa_plan_set_workspace(mpa_plan* p, void* ws, size_t bytes) {
-    if (!p || !ws) return MPA_ERR_INVALID_ARG;
-    if (bytes < p->ws_need || ((uintptr_t)ws & 255u) != 0) return MPA_ERR_WORKSPACE;
-    p->ws = reinterpret_cast<unsigned char*>(ws);
-    p->ws_bytes = bytes;
-    MPA_TRY(cudaMemcpy(p->ws + p->off_nodes, p->nodes.data(), p->nodes.size() * sizeof(NodeC),
-                       cudaMemcpyHostToDevice));
-    std::vector<int> toff((size_t)p->n_types);
-    for (int t = 0; t < p->n_types; ++t) toff[(size_t)t] = t * (p->M + 1);
-    MPA_TRY(cudaMemcpy(p->ws + p->off_toff, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice));
-    double gains[kMaxAmpsPerInterval];
-    for (int a = 0; a < kMaxAmpsPerInterval; ++a) gains[a] = std::exp((double)a * p->map.z_a * p->map.gamma);
-    MPA_TRY(cudaMemcpy(p->ws + p->off_gains, gains, sizeof(gains), cudaMemcpyHostToDevice));
-    MPA_TRY(cudaMemset(p->ws + p->off_err, 0, sizeof(unsigned int)));
-    MPA_TRY(cudaMemset(p->ws + p->off_conv, 0, sizeof(ConvState)));
-    return MPA_OK;
+    return abi_call([&]() -> int {
+        if (!p || !ws) return MPA_ERR_INVALID_ARG;
+        if (bytes < p->ws_need || ((uintptr_t)ws & 255u) != 0) return MPA_ERR_WORKSPACE;
+        p->ws = reinterpret_cast<unsigned char*>(ws);
+        p->ws_bytes = bytes;
+        MPA_TRY(cudaMemcpy(p->ws + p->off_nodes, p->nodes.data(), p->nodes.size() * sizeof(NodeC),
+                           cudaMemcpyHostToDevice));
+        std::vector<int> toff((size_t)p->n_types);
+        for (int t = 0; t < p->n_types; ++t) toff[(size_t)t] = t * (p->M + 1);
+        MPA_TRY(cudaMemcpy(p->ws + p->off_toff, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice));
+        double gains[kMaxAmpsPerInterval];
+        for (int a = 0; a < kMaxAmpsPerInterval; ++a) gains[a] = std::exp((double)a * p->map.z_a * p->map.gamma);
+        MPA_TRY(cudaMemcpy(p->ws + p->off_gains, gains, sizeof(gains), cudaMemcpyHostToDevice));
+        MPA_TRY(cudaMemset(p->ws + p->off_err, 0, sizeof(unsigned int)));
+        MPA_TRY(cudaMemset(p->ws + p->off_conv, 0, sizeof(ConvState)));
+        return MPA_OK;
+    });
 }
 
 }  // extern "C"
@@ -607,12 +609,14 @@ int mpa_plan_autotune(mpa_plan* p, mpa_stream stream, int32_t* log2_n2) {
 }
 
 int mpa_propagate(mpa_plan* p, void* field, double z_from_km, double z_to_km, mpa_stream stream) {
-    EntryRange nv("mpa_propagate", stream);
-    if (!p || !field) return MPA_ERR_INVALID_ARG;
-    if (!p->ws) return MPA_ERR_WORKSPACE;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    return p->prec == MPA_FP32 ? propagate_t<float>(p, field, z_from_km, z_to_km, st)
-                               : propagate_t<double>(p, field, z_from_km, z_to_km, st);
+    return abi_call([&]() -> int {
+        EntryRange nv("mpa_propagate", stream);
+        if (!p || !field) return MPA_ERR_INVALID_ARG;
+        if (!p->ws) return MPA_ERR_WORKSPACE;
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        return p->prec == MPA_FP32 ? propagate_t<float>(p, field, z_from_km, z_to_km, st)
+                                   : propagate_t<double>(p, field, z_from_km, z_to_km, st);
+    });
 }
 
 int mpa_interval(mpa_plan* p, const void* psi0, void* psiM, double z0_km, mpa_stream stream) {
@@ -688,21 +692,23 @@ int ss_workspace_size(int64_t N, int32_t precision, size_t* bytes) {
 
 int ss_propagate(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision, void* field,
                  double z_from_km, double z_to_km, void* workspace, size_t ws_bytes, mpa_stream stream) {
-    EntryRange nv("ss_propagate", stream);
-    if (!map || !field || !workspace || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
-    if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
-    HostMap m;
-    int rc = m.init(map);
-    if (rc) return rc;
-    Split s;
-    rc = split_n(N, precision, &s);
-    if (rc) return rc;
-    size_t need = 0;
-    ss_workspace_size(N, precision, &need);
-    if (ws_bytes < need) return MPA_ERR_WORKSPACE;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    return precision == MPA_FP32 ? ss_t<float>(m, s, T_ps, dz_km, field, z_from_km, z_to_km, workspace, st)
-                                 : ss_t<double>(m, s, T_ps, dz_km, field, z_from_km, z_to_km, workspace, st);
+    return abi_call([&]() -> int {
+        EntryRange nv("ss_propagate", stream);
+        if (!map || !field || !workspace || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
+        if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+        HostMap m;
+        int rc = m.init(map);
+        if (rc) return rc;
+        Split s;
+        rc = split_n(N, precision, &s);
+        if (rc) return rc;
+        size_t need = 0;
+        ss_workspace_size(N, precision, &need);
+        if (ws_bytes < need) return MPA_ERR_WORKSPACE;
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        return precision == MPA_FP32 ? ss_t<float>(m, s, T_ps, dz_km, field, z_from_km, z_to_km, workspace, st)
+                                     : ss_t<double>(m, s, T_ps, dz_km, field, z_from_km, z_to_km, workspace, st);
+    });
 }
 
 int mpa_fft(int64_t N, int32_t precision, int32_t sign, void* data, void* workspace, size_t ws_bytes,
@@ -745,6 +751,7 @@ const char* mpa_status_string(int status) {
         case MPA_ERR_SCALES: return "scales outside the weak-nonlinearity regime of the method";
         case MPA_ERR_TIMEOUT: return "a bounded wait of a persistent kernel ran out (results incomplete)";
         case MPA_ERR_BOUNDS: return "debug build: an access outside the checked buffer range was skipped";
+        case MPA_ERR_HOST_MEMORY: return "host memory allocation failed";
     }
     return "unknown status";
 }

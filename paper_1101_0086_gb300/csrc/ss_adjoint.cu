@@ -35,7 +35,7 @@ int ss_layout(const HostMap& m, const Split& s, int prec, double dz, double z_fr
               SSAdj* a) {
     double kk;
     if (!(z_from >= -1e-12) || !(z_to > z_from) || z_to > m.length * (1 + 1e-12) + 1e-9) return MPA_ERR_GRID;
-    if (!whole((z_to - z_from) / dz, &kk) || kk < 1) return MPA_ERR_GRID;
+    if (!whole((z_to - z_from) / dz, &kk) || kk < 1 || kk > kMaxIntervals) return MPA_ERR_GRID;
     if (s.logN < 13) return MPA_ERR_UNSUPPORTED_N;
     a->K = (long)kk;
     a->Kc = ckpt_steps > 0 ? ckpt_steps : (long)std::ceil(std::sqrt((double)a->K));
@@ -240,40 +240,44 @@ extern "C" {
 
 int ss_adjoint_workspace_size(const mpa_fiber_map* map, int64_t N, int32_t precision, double dz_km, double z_from_km,
                               double z_to_km, int32_t ckpt_steps, size_t* bytes) {
-    if (!map || !bytes || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
-    if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
-    HostMap m;
-    int rc = m.init(map);
-    if (rc) return rc;
-    Split s;
-    if ((rc = split_n(N, precision, &s))) return rc;
-    SSAdj a;
-    if ((rc = ss_layout(m, s, precision, dz_km, z_from_km, z_to_km, ckpt_steps, &a))) return rc;
-    *bytes = a.need;
-    return MPA_OK;
+    return abi_call([&]() -> int {
+        if (!map || !bytes || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
+        if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+        HostMap m;
+        int rc = m.init(map);
+        if (rc) return rc;
+        Split s;
+        if ((rc = split_n(N, precision, &s))) return rc;
+        SSAdj a;
+        if ((rc = ss_layout(m, s, precision, dz_km, z_from_km, z_to_km, ckpt_steps, &a))) return rc;
+        *bytes = a.need;
+        return MPA_OK;
+    });
 }
 
 int ss_adjoint(const mpa_fiber_map* map, int64_t N, double T_ps, double dz_km, int32_t precision, const void* field_in,
                const void* grad_out, void* grad_in, double z_from_km, double z_to_km, int32_t ckpt_steps,
                void* workspace, size_t ws_bytes, double* grad_sigma, double* grad_beta2, mpa_stream stream) {
-    mpa::host::EntryRange nv("ss_adjoint", stream);
-    if (!map || !field_in || !grad_out || !grad_in || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
-    if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
-    HostMap m;
-    int rc = m.init(map);
-    if (rc) return rc;
-    Split s;
-    if ((rc = split_n(N, precision, &s))) return rc;
-    SSAdj a;
-    if ((rc = ss_layout(m, s, precision, dz_km, z_from_km, z_to_km, ckpt_steps, &a))) return rc;
-    if (!workspace || ws_bytes < a.need || ((uintptr_t)workspace & 255u) != 0) return MPA_ERR_WORKSPACE;
-    unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    return precision == MPA_FP32
-               ? ss_adjoint_t<float>(m, s, T_ps, dz_km, field_in, grad_out, grad_in, z_from_km, z_to_km, a, ws,
-                                     grad_sigma, grad_beta2, st)
-               : ss_adjoint_t<double>(m, s, T_ps, dz_km, field_in, grad_out, grad_in, z_from_km, z_to_km, a, ws,
-                                      grad_sigma, grad_beta2, st);
+    return abi_call([&]() -> int {
+        mpa::host::EntryRange nv("ss_adjoint", stream);
+        if (!map || !field_in || !grad_out || !grad_in || !(T_ps > 0.0) || !(dz_km > 0.0)) return MPA_ERR_INVALID_ARG;
+        if (precision != MPA_FP32 && precision != MPA_FP64) return MPA_ERR_INVALID_ARG;
+        HostMap m;
+        int rc = m.init(map);
+        if (rc) return rc;
+        Split s;
+        if ((rc = split_n(N, precision, &s))) return rc;
+        SSAdj a;
+        if ((rc = ss_layout(m, s, precision, dz_km, z_from_km, z_to_km, ckpt_steps, &a))) return rc;
+        if (!workspace || ws_bytes < a.need || ((uintptr_t)workspace & 255u) != 0) return MPA_ERR_WORKSPACE;
+        unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        return precision == MPA_FP32
+                   ? ss_adjoint_t<float>(m, s, T_ps, dz_km, field_in, grad_out, grad_in, z_from_km, z_to_km, a, ws,
+                                         grad_sigma, grad_beta2, st)
+                   : ss_adjoint_t<double>(m, s, T_ps, dz_km, field_in, grad_out, grad_in, z_from_km, z_to_km, a, ws,
+                                          grad_sigma, grad_beta2, st);
+    });
 }
 
 }  // extern "C"

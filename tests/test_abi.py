@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_status_strings(L):
-    for s in range(0, 11):
+    for s in range(0, 12):
         assert L.mpa_status_string(s) and L.mpa_status_string(s) != b"unknown status"
     assert L.mpa_status_string(99) == b"unknown status"
 
@@ -169,6 +169,37 @@ def test_plan_validation_is_host_only(L):
     bad = FiberMap((Segment(-1.0, 0.0, 0.0, 0.0),), 0.0, 0.0, 1)
     assert _plan(L, bad, 1 << 14, 12800.0, 50.0, 10, 3)[0] == 1
     rc, h = _plan(L, fib, 1 << 14, 12800.0, 100.0, 10, 3)  # L a multiple of the period
+    assert rc == 0
+    L.mpa_plan_destroy(h)
+
+
+def test_size_limits_and_host_allocation_failures_are_statuses(L):
+    """M above 2^24 and more than 2^20 interval starts per period are
+    refused before any allocation; a node table the host cannot hold comes
+    back as MPA_ERR_HOST_MEMORY (11) instead of a C++ exception crossing the
+    C ABI (which would end the process)."""
+    fib = dm_map(4)
+    assert _plan(L, fib, 1 << 14, 12800.0, 50.0, (1 << 24) + 1, 2)[0] == 1
+    assert _plan(L, fib, 1 << 14, 12800.0, 50.0 / (1 << 21), 4, 2)[0] == 5
+    # 2^20 interval starts x (2^24 + 1) nodes x 48 bytes: about 8e14 bytes of node constants
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0 / (1 << 20), 1 << 24, 2)
+    assert rc == 11 and not h.value
+    assert L.mpa_status_string(11) == b"host memory allocation failed"
+    # the same through the batch: one link of 2^14 modes over the whole map
+    fm, segs = mpa._fiber_struct(fib)
+    links = (mpa._Link * 1)()
+    links[0] = mpa._Link(fm, 1 << 14, 12800.0, fib.length_km, ctypes.c_void_p(256))
+    L.mpa_batch_create.argtypes = [ctypes.POINTER(mpa._Link), ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]
+    b = ctypes.c_void_p()
+    assert L.mpa_batch_create(links, 1, 50.0, (1 << 24) + 1, 2, 0, ctypes.byref(b)) == 1
+    assert L.mpa_batch_create(links, 1, 50.0 / (1 << 21), 4, 2, 0, ctypes.byref(b)) == 5
+    assert L.mpa_batch_create(links, 1, 50.0 / (1 << 20), 1 << 24, 2, 0, ctypes.byref(b)) == 11 and not b.value
+    # intervals far below the amplifier spacing that end on the amplifiers are a valid grid
+    assert L.mpa_batch_create(links, 1, 50.0 / (1 << 10), 1, 2, 0, ctypes.byref(b)) == 0 and b.value
+    L.mpa_batch_destroy(b)
+    # a plan of ordinary size still works after the failures
+    rc, h = _plan(L, fib, 1 << 14, 12800.0, 50.0, 800, 3)
     assert rc == 0
     L.mpa_plan_destroy(h)
 

@@ -97,6 +97,21 @@ def test_propagate_matches_oracle_across_amplifiers(M, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_fine_intervals_ending_on_amplifiers(M, prec):
+    # L = z_a / 1024, below the tolerance of the amplifier count: 2048
+    # intervals, two of which end on an amplifier, are a valid grid
+    fib = small_map()
+    N, T = 1 << 10, 800.0
+    A0 = wdm_field(N, T, 2, 50.0, 16, 30.0, 10.0, "qpsk", seed=7)
+    L = 10.0 / 1024
+    ref = oracle.mpa(A0, fib, T, 0.0, 20.0, L, 2, 2)
+    plan = M.Plan(fib, N, T, L, 2, 2, precision=prec)
+    got = host(plan.propagate(dev(A0, prec), 0.0, 20.0))
+    assert oracle.rel_l2(got, ref) < TOL[prec]
+    assert plan.status()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_linear_limit_is_exact(M, prec):
     # sigma = 0: psi is constant (text after Eq. (2)); the result is the exact
     # linear flow, computed here with numpy's FFT
