@@ -179,10 +179,40 @@ def _stream(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _field_ptr(t: torch.Tensor, dtype: torch.dtype, n: int, what: str) -> ctypes.c_void_p:
+def _resolve(device) -> torch.device:
+    """The CUDA device a call runs on, with its index ("cuda" = the current one)."""
+    d = torch.device(device)
+    if d.type == "cuda" and d.index is None:
+        d = torch.device("cuda", torch.cuda.current_device())
+    return d
+
+
+def _on_device(device: torch.device, what: str) -> None:
+    """The library launches on the current CUDA device, which must be the one
+    the call's buffers live on (another device's pointers would be read as
+    this device's)."""
+    cur = torch.cuda.current_device()
+    if device.type != "cuda" or device.index != cur:
+        raise ValueError(f"{what}: the buffers are on {device} but the current CUDA device is cuda:{cur}; "
+                         f"call it under torch.cuda.device({device.index})")
+
+
+def _field_ptr(t: torch.Tensor, dtype: torch.dtype, n: int, what: str, device=None) -> ctypes.c_void_p:
     if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
         raise ValueError(f"{what}: expected a contiguous CUDA {dtype} tensor of {n} elements")
+    if device is not None and t.device != device:
+        raise ValueError(f"{what}: the tensor is on {t.device}, the call's buffers on {device}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _ws_ptr(ws: torch.Tensor, device, what: str) -> ctypes.c_void_p:
+    """A workspace: a contiguous CUDA uint8 tensor on the call's device (the
+    library checks its size)."""
+    if not getattr(ws, "is_cuda", False) or ws.dtype != torch.uint8 or not ws.is_contiguous():
+        raise ValueError(f"{what}: the workspace must be a contiguous CUDA uint8 tensor")
+    if ws.device != device:
+        raise ValueError(f"{what}: the workspace is on {ws.device}, the call's buffers on {device}")
+    return ctypes.c_void_p(ws.data_ptr())
 
 
 class Plan:
@@ -205,21 +235,24 @@ class Plan:
         _check(L.mpa_plan_workspace_size(h, ctypes.byref(nbytes)), "mpa_plan_workspace_size")
         self.workspace_bytes = int(nbytes.value)
         if workspace is None:
-            workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+            workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=_resolve(device))
         self.workspace = workspace
-        _check(L.mpa_plan_set_workspace(h, ctypes.c_void_p(workspace.data_ptr()), workspace.numel()),
+        self.device = workspace.device
+        _check(L.mpa_plan_set_workspace(h, _ws_ptr(workspace, self.device, "Plan"), workspace.numel()),
                "mpa_plan_set_workspace")
         self._split = min(max((self.N.bit_length() - 1) // 2, 4), 11)  # split_n's default column length
 
     def propagate(self, field: torch.Tensor, z_from_km: float, z_to_km: float, stream=None) -> torch.Tensor:
         """In-place MPA propagation of the time-domain field (``mpa_propagate``)."""
-        ptr = _field_ptr(field, self.dtype, self.N, "propagate")
+        ptr = _field_ptr(field, self.dtype, self.N, "propagate", self.device)
+        _on_device(self.device, "propagate")
         _check(lib().mpa_propagate(self._h, ptr, float(z_from_km), float(z_to_km), _stream(stream)), "mpa_propagate")
         return field
 
     def interval(self, psi0: torch.Tensor, z0_km: float, stream=None) -> torch.Tensor:
         """psi^{(n_iter)} at the last node of one interval (``mpa_interval``)."""
-        p0 = _field_ptr(psi0, torch.complex128, self.N, "interval")
+        p0 = _field_ptr(psi0, torch.complex128, self.N, "interval", self.device)
+        _on_device(self.device, "interval")
         out = torch.empty_like(psi0)
         _check(lib().mpa_interval(self._h, p0, ctypes.c_void_p(out.data_ptr()), float(z0_km), _stream(stream)),
                "mpa_interval")
@@ -229,6 +262,7 @@ class Plan:
         """``mpa_plan_autotune``: time every admissible four-step split on the
         GPU and keep the fastest; returns log2 of the chosen column length."""
         l2 = ctypes.c_int32()
+        _on_device(self.device, "autotune")
         _check(lib().mpa_plan_autotune(self._h, _stream(stream), ctypes.byref(l2)), "mpa_plan_autotune")
         self._split = int(l2.value)
         return int(l2.value)
@@ -268,9 +302,11 @@ class Plan:
         """``mpa_propagate`` that also keeps the interval checkpoints in the
         adjoint workspace (returned) for a later :meth:`adjoint` without the input."""
         ws = self._adj_ws(z_from_km, z_to_km, adj_workspace)
-        ptr = _field_ptr(field, self.dtype, self.N, "propagate_checkpointed")
-        _check(lib().mpa_propagate_checkpointed(self._h, ptr, float(z_from_km), float(z_to_km),
-                                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+        ptr = _field_ptr(field, self.dtype, self.N, "propagate_checkpointed", self.device)
+        wp = _ws_ptr(ws, self.device, "propagate_checkpointed")
+        _on_device(self.device, "propagate_checkpointed")
+        _check(lib().mpa_propagate_checkpointed(self._h, ptr, float(z_from_km), float(z_to_km), wp, ws.numel(),
+                                                _stream(stream)),
                "mpa_propagate_checkpointed")
         return ws
 
@@ -286,8 +322,10 @@ class Plan:
         if field_in is None and adj_workspace is None:
             raise ValueError("adjoint: give field_in or the workspace of propagate_checkpointed")
         ws = self._adj_ws(z_from_km, z_to_km, adj_workspace)
-        go = _field_ptr(grad_out, self.dtype, self.N, "adjoint grad_out")
-        fi = _field_ptr(field_in, self.dtype, self.N, "adjoint field_in") if field_in is not None else None
+        go = _field_ptr(grad_out, self.dtype, self.N, "adjoint grad_out", self.device)
+        fi = _field_ptr(field_in, self.dtype, self.N, "adjoint field_in", self.device) if field_in is not None else None
+        wp = _ws_ptr(ws, self.device, "adjoint")
+        _on_device(self.device, "adjoint")
         gi = torch.empty_like(grad_out)
         gs = gb = None
         ps = pb = None
@@ -297,7 +335,7 @@ class Plan:
             ps = gs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             pb = gb.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         _check(lib().mpa_adjoint(self._h, fi, go, ctypes.c_void_p(gi.data_ptr()), float(z_from_km), float(z_to_km),
-                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), ps, pb, _stream(stream)), "mpa_adjoint")
+                                 wp, ws.numel(), ps, pb, _stream(stream)), "mpa_adjoint")
         return gi, gs, gb
 
     def status(self, stream=None) -> bool:
@@ -438,10 +476,11 @@ class Batch:
         L = lib()
         self.prec = _prec(precision)
         self.dtype = _cdtype(self.prec)
+        self.device = _resolve(device)
         keep = []
         arr = (_Link * len(links))()
         for i, (fiber, T_ps, z_to, field) in enumerate(links):
-            ptr = _field_ptr(field, self.dtype, field.numel(), "Batch")
+            ptr = _field_ptr(field, self.dtype, field.numel(), "Batch", self.device)
             fm, segs = _fiber_struct(fiber)
             keep.append(segs)
             arr[i] = _Link(fm, field.numel(), float(T_ps), float(z_to), ptr)
@@ -453,15 +492,17 @@ class Batch:
         self._h = h
         n = ctypes.c_size_t()
         _check(L.mpa_batch_workspace_size(h, ctypes.byref(n)), "mpa_batch_workspace_size")
-        self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=device)
+        self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=self.device)
         _check(L.mpa_batch_set_workspace(h, ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel()),
                "mpa_batch_set_workspace")
 
     def autotune(self, stream=None) -> None:
         """``mpa_batch_autotune``: per-group four-step split by timing."""
+        _on_device(self.device, "Batch.autotune")
         _check(lib().mpa_batch_autotune(self._h, _stream(stream)), "mpa_batch_autotune")
 
     def propagate(self, use_graph: bool = True, stream=None) -> None:
+        _on_device(self.device, "Batch.propagate")
         _check(lib().mpa_batch_propagate(self._h, 1 if use_graph else 0, _stream(stream)), "mpa_batch_propagate")
 
     def status_code(self, stream=None) -> int:
@@ -509,10 +550,11 @@ def ss_propagate(field: torch.Tensor, fiber, T_ps: float, dz_km: float, z_from_k
     need = ss_workspace_bytes(N, prec)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=field.device)
+    wp = _ws_ptr(workspace, field.device, "ss_propagate")
+    _on_device(field.device, "ss_propagate")
     fm, segs = _fiber_struct(fiber)
     _check(lib().ss_propagate(ctypes.byref(fm), N, float(T_ps), float(dz_km), prec, ptr, float(z_from_km),
-                              float(z_to_km), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
-                              _stream(stream)), "ss_propagate")
+                              float(z_to_km), wp, workspace.numel(), _stream(stream)), "ss_propagate")
     return field
 
 
@@ -533,7 +575,9 @@ def ss_adjoint(field_in: torch.Tensor, grad_out: torch.Tensor, fiber, T_ps: floa
                                            int(ckpt_steps), ctypes.byref(n)), "ss_adjoint_workspace_size")
         workspace = torch.empty(int(n.value), dtype=torch.uint8, device=field_in.device)
     fi = _field_ptr(field_in, _cdtype(prec), N, "ss_adjoint field_in")
-    go = _field_ptr(grad_out, _cdtype(prec), N, "ss_adjoint grad_out")
+    go = _field_ptr(grad_out, _cdtype(prec), N, "ss_adjoint grad_out", field_in.device)
+    wp = _ws_ptr(workspace, field_in.device, "ss_adjoint")
+    _on_device(field_in.device, "ss_adjoint")
     gi = torch.empty_like(grad_out)
     gs = gb = ps = pb = None
     if params:
@@ -542,8 +586,8 @@ def ss_adjoint(field_in: torch.Tensor, grad_out: torch.Tensor, fiber, T_ps: floa
         ps = gs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         pb = gb.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     _check(L.ss_adjoint(ctypes.byref(fm), N, float(T_ps), float(dz_km), prec, fi, go, ctypes.c_void_p(gi.data_ptr()),
-                        float(z_from_km), float(z_to_km), int(ckpt_steps), ctypes.c_void_p(workspace.data_ptr()),
-                        workspace.numel(), ps, pb, _stream(stream)), "ss_adjoint")
+                        float(z_from_km), float(z_to_km), int(ckpt_steps), wp, workspace.numel(), ps, pb,
+                        _stream(stream)), "ss_adjoint")
     return gi, gs, gb
 
 
@@ -555,8 +599,9 @@ def fft(data: torch.Tensor, sign: int, workspace: Optional[torch.Tensor] = None,
     need = ss_workspace_bytes(N, prec)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=data.device)
-    _check(lib().mpa_fft(N, prec, int(sign), ptr, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
-                         _stream(stream)), "mpa_fft")
+    wp = _ws_ptr(workspace, data.device, "fft")
+    _on_device(data.device, "fft")
+    _check(lib().mpa_fft(N, prec, int(sign), ptr, wp, workspace.numel(), _stream(stream)), "mpa_fft")
     return data
 
 
@@ -567,6 +612,7 @@ def fft_noalloc(data: torch.Tensor, sign: int, stream=None) -> torch.Tensor:
     prec = _prec(data.dtype)
     N = data.numel()
     ptr = _field_ptr(data, _cdtype(prec), N, "fft_noalloc")
+    _on_device(data.device, "fft_noalloc")
     _check(lib().mpa_fft_noalloc(N, prec, int(sign), ptr, _stream(stream)), "mpa_fft_noalloc")
     return data
 
