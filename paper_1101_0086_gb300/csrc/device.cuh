@@ -214,7 +214,7 @@ struct NodeC {
     double post; // MPA: sigma(z_j) dz / pre (weight of V_j in Eq. (6))
 };
 
-// frac(k'^2 a + k'^3 b) as an unsigned Q0.64 number of turns (error < 3 ulp).
+// frac(k'^2 a + k'^3 b) as an unsigned Q0.64 number of turns (within 2 ulp).
 // frac(k'^3 b) = frac(k' frac(k'^2 b)) since k'^3 b - k' frac(k'^2 b) is an
 // integer multiple of k'.
 __device__ __forceinline__ unsigned long long phase_q64(long long kp, const NodeC& c) {
@@ -316,8 +316,8 @@ __device__ __forceinline__ void sincos_kerr(float phi, float* s, float* c) {
 // Exact phases theta(k'_0 + s D), s = -R/2 .. R/2-1, produced in s order
 // by finite differences in Q0.64 arithmetic: theta is a cubic in s, so
 // after four direct evaluations every further value costs three 64-bit
-// additions (each direct value carries < 3 ulp of 2^-64; the accumulated
-// error stays below 2^-50 turns).
+// additions (each direct value is within 2 ulp of 2^-64; over 32 values
+// the cubic extrapolation keeps the error below 2^-48 turns).
 struct PhaseRun {
     unsigned long long t0, t1, t2, t3, d1, d2, d3;
     int n;
@@ -347,8 +347,8 @@ struct PhaseRun {
 // Phases of the R elements k'_s = k'_0 + s D, s = -R/2 .. R/2-1 of one
 // butterfly by exact finite differences in Q0.64 arithmetic: theta is a
 // cubic in s, so after four direct evaluations every further value costs
-// three 64-bit additions (the direct values carry < 3 ulp of 2^-64 each, so
-// the accumulated error stays below 2^-50 turns).  th[r] receives the phase
+// three 64-bit additions (the direct values are within 2 ulp of 2^-64, so
+// over 32 values the error stays below 2^-48 turns).  th[r] receives the phase
 // of element r, where s = r for r < R/2 and s = r - R for r >= R/2.
 template <int R>
 __device__ __forceinline__ void phase_run(long long k0, long long D, const NodeC& c, unsigned long long (&th)[R]) {
