@@ -250,7 +250,7 @@ template <> __device__ __forceinline__ double2 expi_turns<double>(unsigned long 
 // Taylor series through x^8 and x^9 (truncation below 2.5e-8 and 1.8e-9),
 // and rotate by i^q.
 __device__ __forceinline__ float2 expi_turns_poly(unsigned long long th) {
-    const unsigned long long q = (th + (1ull << 61)) >> 62;  // 0..4
+    const unsigned long long q = (th + (1ull << 61)) >> 62;  // 0..3 (the sum wraps at 2^64)
     // residual in units of 2^-32 turn (|d| <= 2^29; the dropped bits are < 2^-32 turn)
     const int d = (int)((long long)(th - (q << 62)) >> 32);
     const float x = __int2float_rn(d) * 1.4629180792671596e-09f;  // 2 pi 2^-32
@@ -283,8 +283,8 @@ __device__ __forceinline__ float2 expi_turns_poly(unsigned long long th) {
 // (sin, cos) of a Kerr phase phi = sigma |A|^2 dz of the split-step.  These
 // phases are small (about 1e-3 rad on the benchmark links), so for
 // |phi| <= 1/16 the Taylor series of cos and sin are used: through phi^8 and
-// phi^9 in FP64 (the first dropped terms are below 2.5e-19 and 2.3e-20
-// relative) and through phi^4 and phi^5 in FP32 (below 8e-11 and 1.2e-11);
+// phi^9 in FP64 (the first dropped terms are below 2.6e-19 and 2.3e-20
+// relative) and through phi^4 and phi^5 in FP32 (below 8.3e-11 and 1.2e-11);
 // larger phases take the library's sincos.  The FP64 series costs ten
 // multiply-adds instead of a full-range evaluation on a GPU whose FP64
 // rate is a small fraction of its FP32 rate.

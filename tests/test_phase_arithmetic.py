@@ -145,3 +145,29 @@ def test_quarter_turn_split_and_series(seed):
     # the series' first dropped terms at |x| = pi/4
     assert (math.pi / 4) ** 10 / math.factorial(10) < 2.5e-8
     assert (math.pi / 4) ** 11 / math.factorial(11) < 1.8e-9
+
+
+def _series(mp, x, last_cos, last_sin):
+    c = sum((-1) ** k * x ** (2 * k) / mp.factorial(2 * k) for k in range(last_cos // 2 + 1))
+    s = sum((-1) ** k * x ** (2 * k + 1) / mp.factorial(2 * k + 1) for k in range(last_sin // 2 + 1))
+    return c, s
+
+
+def test_series_truncation_bounds():
+    """The truncation errors stated for the phase series (|x| <= pi/4, through
+    x^8 and x^9) and for the split-step's Kerr series (|phi| <= 1/16, through
+    phi^8/phi^9 in FP64 and phi^4/phi^5 in FP32; sin relative), at 200-bit
+    precision."""
+    mp = pytest.importorskip("mpmath").mp
+    mp.prec = 200
+    cases = [(mp.pi / 4, 8, 9, 2.5e-8, 1.8e-9, False),
+             (mp.mpf(1) / 16, 8, 9, 2.6e-19, 2.3e-20, True),
+             (mp.mpf(1) / 16, 4, 5, 8.3e-11, 1.2e-11, True)]
+    for xmax, lc, ls, bound_c, bound_s, rel_sin in cases:
+        worst_c = worst_s = mp.mpf(0)
+        for i in range(1, 257):
+            x = xmax * i / 256
+            c, s = _series(mp, x, lc, ls)
+            worst_c = max(worst_c, abs(c - mp.cos(x)))
+            worst_s = max(worst_s, abs(s - mp.sin(x)) / (mp.sin(x) if rel_sin else 1))
+        assert worst_c < bound_c and worst_s < bound_s, (xmax, lc, worst_c, worst_s)
