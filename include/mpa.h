@@ -102,6 +102,12 @@ typedef struct {
     int32_t n_periods;
 } mpa_fiber_map;
 
+/* gamma_per_km of a fiber whose POWER loss is db_per_km dB/km: G = -gamma in
+ * Eq. (1) acts on the amplitude, so |A|^2 decays as exp(-2 gamma z) =
+ * 10^(-db_per_km z / 10), i.e. gamma = db_per_km ln(10) / 20.  Host only;
+ * never fails (NaN in, NaN out). */
+MPA_API double mpa_gamma_from_db_per_km(double db_per_km);
+
 /* MPA discretisation (MPA steps 1-7 and Eq. (6)): intervals of length L_km,
  * each with M+1 equally spaced nodes and n_iter Picard iterations. */
 typedef struct {

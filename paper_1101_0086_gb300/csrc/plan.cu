@@ -738,6 +738,8 @@ int mpa_fft(int64_t N, int32_t precision, int32_t sign, void* data, void* worksp
     return MPA_OK;
 }
 
+double mpa_gamma_from_db_per_km(double db_per_km) { return db_per_km * std::log(10.0) / 20.0; }
+
 const char* mpa_status_string(int status) {
     switch (status) {
         case MPA_OK: return "ok";

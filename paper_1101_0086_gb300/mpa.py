@@ -62,7 +62,7 @@ EXPORTS = ("mpa_plan_create", "mpa_plan_workspace_size", "mpa_plan_set_workspace
            "ss_adjoint_workspace_size", "ss_adjoint", "mpa_plan_autotune", "mpa_plan_set_split",
            "mpa_batch_autotune", "mpa_plan_contraction", "mpa_plan_check_scales", "mpa_batch_status",
            "mpa_debug_fail_launch", "mpa_alu_peak", "mpa_batch_set_persistent", "mpa_batch_set_wait_limit",
-           "mpa_last_timing", "mpa_debug_bounds_checked", "mpa_debug_set_bounds")
+           "mpa_last_timing", "mpa_debug_bounds_checked", "mpa_debug_set_bounds", "mpa_gamma_from_db_per_km")
 
 
 def library_path() -> str:
@@ -128,6 +128,8 @@ def lib() -> ctypes.CDLL:
         L.mpa_debug_fail_launch.argtypes = [i64, i32]
         L.mpa_last_timing.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_char_p)]
         L.mpa_debug_bounds_checked.restype = i32
+        L.mpa_gamma_from_db_per_km.argtypes = [dbl]
+        L.mpa_gamma_from_db_per_km.restype = dbl
         L.mpa_debug_set_bounds.argtypes = [vp, ctypes.c_size_t, ctypes.c_size_t]
         L.mpa_alu_peak.argtypes = [i32, ctypes.POINTER(dbl), vp]
         L.mpa_batch_set_persistent.argtypes = [vp, i32]
@@ -642,6 +644,12 @@ def profile_read() -> dict:
             out[name.decode()] = (float(ms.value), int(n.value), float(b.value))
         k += 1
     return out
+
+
+def gamma_from_db_per_km(db_per_km: float) -> float:
+    """``mpa_gamma_from_db_per_km``: the amplitude loss coefficient gamma of
+    Eq. (1) for a power loss in dB/km."""
+    return float(lib().mpa_gamma_from_db_per_km(float(db_per_km)))
 
 
 def debug_bounds_checked() -> bool:

@@ -33,7 +33,7 @@ int main(void) {
     memset(&map, 0, sizeof map);
     map.segments = span;
     map.n_segments = 2;
-    map.gamma_per_km = 0.02302585092994046; /* 0.2 dB/km */
+    map.gamma_per_km = mpa_gamma_from_db_per_km(0.2);
     map.z_a_km = 50.0;
     map.n_periods = 40;
 
@@ -77,6 +77,7 @@ int main(void) {
     EXPECT(ss_workspace_size((int64_t)1 << 20, MPA_FP64, &ss) == MPA_OK && ss == ((size_t)1 << 20) * 16,
            "split-step workspace");
     EXPECT(strcmp(mpa_status_string(MPA_ERR_GRID), "z-grid inconsistent with the fiber map") == 0, "status string");
+    EXPECT(map.gamma_per_km > 0.0230258509299 && map.gamma_per_km < 0.0230258509300, "0.2 dB/km as gamma");
 
     if (failures) return 1;
     printf("C client: %d checks passed\n", checks);

@@ -204,6 +204,15 @@ def test_size_limits_and_host_allocation_failures_are_statuses(L):
     L.mpa_plan_destroy(h)
 
 
+def test_gamma_from_db_per_km(L):
+    """The dB/km helper of the ABI: |A|^2 falls by the stated dB over 1 km."""
+    from paper_1101_0086_gb300.workloads import gamma_from_db_per_km
+    for db in (0.0, 0.2, 0.35, 1.0):
+        g = mpa.gamma_from_db_per_km(db)
+        assert g == pytest.approx(gamma_from_db_per_km(db), rel=1e-15, abs=0.0)
+        assert 10 * math.log10(math.exp(2 * g)) == pytest.approx(db, rel=1e-13, abs=1e-15)
+
+
 def test_ss_workspace_size(L):
     n = ctypes.c_size_t()
     assert L.ss_workspace_size(1 << 20, 0, ctypes.byref(n)) == 0 and n.value == (1 << 20) * 8
