@@ -560,6 +560,14 @@ def ss_propagate(field: torch.Tensor, fiber, T_ps: float, dz_km: float, z_from_k
     return field
 
 
+def propagate(field: torch.Tensor, plan: "Plan", z_from_km: float, z_to_km: float, stream=None) -> torch.Tensor:
+    """Module-level form of :meth:`Plan.propagate` (``mpa_propagate``)."""
+    return plan.propagate(field, z_from_km, z_to_km, stream)
+
+
+ss = ss_propagate  # the split-step of Eq. (4) under its short name
+
+
 def ss_adjoint(field_in: torch.Tensor, grad_out: torch.Tensor, fiber, T_ps: float, dz_km: float, z_from_km: float,
                z_to_km: float, ckpt_steps: int = 0, workspace: Optional[torch.Tensor] = None, params: bool = True,
                stream=None):

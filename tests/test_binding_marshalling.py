@@ -116,6 +116,14 @@ def test_plan_calls_reach_the_library_with_their_buffers(fake):
     assert fake.calls[-1][0] == "mpa_plan_autotune"
 
 
+def test_module_level_forms(fake):
+    plan = make_plan()
+    f = FakeCuda(N, torch.complex64)
+    assert mpa.propagate(f, plan, 0.0, 5.0) is f and fake.calls[-1][0] == "mpa_propagate"
+    x = FakeCuda(N, torch.complex128)
+    assert mpa.ss(x, dm_map(4), 800.0, 0.05, 0.0, 1.0) is x and fake.calls[-1][0] == "ss_propagate"
+
+
 def test_plan_refuses_buffers_of_another_device_or_kind(fake):
     plan = make_plan()
     n_calls = len(fake.calls)
