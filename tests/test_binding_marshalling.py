@@ -7,8 +7,6 @@ pointers and sizes it was given. A field, gradient or workspace on another
 device, a host or non-byte workspace, or a call made while another CUDA
 device is current must be refused before any C call is made.
 """
-import ctypes
-
 import pytest
 import torch
 
@@ -55,9 +53,6 @@ class FakeLib:
                 args[-1]._obj.value = 8
             return 0
         return fn
-
-    def names(self):
-        return [c[0] for c in self.calls]
 
 
 @pytest.fixture
