@@ -194,6 +194,29 @@ def issue_roofline(warp_inst: float, launch_s: float, sm_mhz: float, n_sm: int =
             "peak": round(peak, 1), "frac": round(ach / peak, 4), "sm_mhz": sm_mhz}
 
 
+# bytes of one level's node spectra that stay resident in the GB300's 129 MB L2
+L2_RESIDENT_BYTES = 120e6
+
+
+def l2_resident_roofline(line: dict, level_bytes: float) -> dict:
+    """When one level's node spectra fit in L2 (the small links), the
+    dominant kernel is bound by instruction issue, not by HBM: its issue view
+    (warp instructions per second against 152 SMs x 4 schedulers x the
+    sampled SM clock) becomes the roofline, "alu", with the HBM figures kept
+    beside it.  Larger levels, or a line without the issue view, are
+    returned unchanged."""
+    if level_bytes > L2_RESIDENT_BYTES or "issue" not in line:
+        return line
+    iss = line["issue"]
+    return {"bound": "alu", "achieved": iss["achieved"], "peak": iss["peak"], "unit": iss["unit"], "frac": iss["frac"],
+            "traffic": line.get("traffic"), "kernel": line["kernel"],
+            "peak_source": "issue limit: 152 SMs x 4 warp schedulers x 1 instruction per cycle at the sampled SM clock",
+            "working_set": f"one level of node spectra, {level_bytes / 1e6:.0f} MB, resident in L2",
+            "hbm": {k: line[k] for k in ("achieved", "peak", "unit", "frac", "algorithmic_bytes_per_launch",
+                                         "peak_source")},
+            "issue": iss}
+
+
 def max_over_ranks(t: float, dist=None, device="cpu") -> float:
     """The job's time: the largest per-rank time (each rank times its own
     replica; the barrier before and after the timed region aligns them)."""
@@ -450,6 +473,7 @@ def run_mpa(args, world, rank, local):
     roofline, (dom_ms, dom_n) = hbm_roofline(r["prof"], peak, peak_src, rec)
     if rec.get("warp_instructions_per_launch") and ck.get("sm_mhz"):
         roofline["issue"] = issue_roofline(rec["warp_instructions_per_launch"], dom_ms / 1e3 / dom_n, ck["sm_mhz"])
+    roofline = l2_resident_roofline(roofline, (w.mpa_M + 1) * N * 8.0)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,

@@ -67,6 +67,22 @@ def test_roofline_helpers():
     assert bench.ncu_traffic("no_such_kernel", "w", "s") is None
 
 
+def test_l2_resident_levels_report_the_issue_roofline():
+    """A level whose node spectra fit in L2 reports the issue view as its
+    roofline ("alu") and keeps the HBM figures beside it; a larger level,
+    or a line without the issue view, keeps the HBM roofline."""
+    prof = {"kn_mpa": (10.0, 100, 1.75e10), "scan": (2.0, 100, 1e9)}
+    hbm, _ = bench.hbm_roofline(prof, 6786.9, "measured", {"dram_bytes_per_launch": 1.49e8})
+    hbm["issue"] = bench.issue_roofline(74.9e6, 10.0e-3 / 100, 2070.0)
+    small = bench.l2_resident_roofline(hbm, 801 * (1 << 14) * 8.0)
+    assert small["bound"] == "alu" and small["kernel"] == "kn_mpa"
+    assert small["frac"] == hbm["issue"]["frac"] and small["peak"] == pytest.approx(152 * 4 * 2.07, abs=0.1)
+    assert small["hbm"]["frac"] == hbm["frac"] and small["traffic"] == 1.49e8
+    assert bench.l2_resident_roofline(hbm, 126 * (1 << 20) * 8.0) is hbm
+    plain, _ = bench.hbm_roofline(prof, 6786.9, "measured")
+    assert bench.l2_resident_roofline(plain, 1e6) is plain
+
+
 def test_clock_samples_are_parsed():
     """The clocks record: median SM clock of the loaded samples, the maximum
     clock, and every throttle reason that was active in any sample."""
