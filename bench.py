@@ -659,6 +659,20 @@ def run_batch(args, world, rank, local):
     launches = mpa.kernel_launches() - l0
     ck = clocks.stop()
     value = units * args.steps / t
+    # kernel table and roofline from one more step outside the timed region:
+    # the same launches without the graph, each bracketed by CUDA events
+    reset()
+    torch.cuda.synchronize()
+    mpa.profile(True)
+    batch.propagate(False, stream)
+    torch.cuda.synchronize()
+    prof = mpa.profile_read()
+    mpa.profile(False)
+    tot = sum(x[0] for x in prof.values())
+    kern = {k: {"ms_total": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4),
+                "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1)} for k, v in prof.items()}
+    peak, peak_src = peaks()
+    roof = hbm_roofline(prof, peak, peak_src)[0] if prof else None
     # sequential per-link loop on every 8th link (same plans as a user would make)
     sub = specs[::8]
     plans = [mpa.Plan(s.fiber, s.N, s.T_ps, L, Mn, nit, "fp32") for s in sub]
@@ -684,7 +698,9 @@ def run_batch(args, world, rank, local):
                        "L_km": L, "M": Mn, "n_iter": nit, "method": "MPA FP32, batched links, CUDA graph",
                        "l2": "inputs reset between steps (working set > L2)"},
             "sequential_subset": {"value": seq, "unit": UNIT, "links": len(sub)},
-            "batch_over_sequential": value / seq, "clocks": ck, "gpu_launches": launches}
+            "batch_over_sequential": value / seq, "clocks": ck, "gpu_launches": launches,
+            "kernels": kern, "roofline": roof,
+            "kernels_from": "one untimed step of the same launches without the graph, CUDA events per launch"}
     print(json.dumps(line), flush=True)
     return 0
 
