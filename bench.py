@@ -242,8 +242,9 @@ def dist_env():
 
 # ----------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
-    """The FP64 CPU oracle on the host cores: each step is one 5-km interval of
-    the same link (M = 142, n_tot of the workload) at N = 2^20."""
+    """The FP64 CPU oracle on the host cores: each step is one MPA interval
+    (L, M and n_tot of the workload: 5 km, M = 125, n_tot = 2 on the 2^20
+    link) of the same link at its full N."""
     if rank != 0:
         return 0
     import numpy as np
